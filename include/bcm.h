@@ -1,0 +1,178 @@
+/*
+ * libbcm -- exact top-k closeness centrality on one GPU.
+ *
+ * Method: Borassi, Crescenzi, Marino, "Fast and Simple Computation of Top-k
+ * Closeness Centralities" (arXiv 1507.01490), called BCM below.
+ *
+ *   closeness   c(v) = (r(v)-1)^2 / ((n-1) f(v))                 (Section 1)
+ *               r(v) = |R(v)|, the vertices reachable from v (v included);
+ *               f(v) = sum of d(v,w) over R(v), the farness.
+ *   ranking     by c(v) descending, equal values by vertex id ascending;
+ *               r(v) = 1 gives c(v) = 0.
+ *   BCM         Algorithm 1: vertices in decreasing degree order (outdeg on
+ *               digraphs, equal degrees by id), each one's BFS cut by
+ *               BFSCut (Algorithm 2) once Lemma 1's farness lower bound
+ *               (Lemma 2's for digraphs, with the alpha/omega bounds of
+ *               Section 2.3) shows it cannot enter the current top-k.
+ *
+ * Results are exact: farness is an integer, every comparison is done in
+ * 128-bit integer arithmetic, and the top-k is the one the textbook
+ * algorithm (one BFS per vertex) returns.
+ *
+ * Conventions
+ *   - Graphs are CSR: row_ptr[n+1] (uint64), col[m] (uint32).  Undirected
+ *     graphs store both arcs of every edge (m counts arcs).  Self-loops and
+ *     repeated arcs are accepted; they change no distance.  Supported sizes:
+ *     n < 2^30 and m < 2^32.
+ *   - The caller owns every array it passes; the library copies inputs and
+ *     writes outputs into caller-allocated memory.  Output pointers are host
+ *     memory unless BCM_OUT_DEVICE is set (then they are device memory on the
+ *     current device).
+ *   - Calls are synchronous: they return after the work on the graph's
+ *     stream has finished, unless the name ends in _async.
+ *   - Every function returns a bcm_status; on failure bcm_last_error()
+ *     returns a message for the calling thread.  No C++ exception crosses
+ *     this interface.
+ *   - A handle must not be used by two threads at once.
+ *   - Every wait inside a kernel (grid barrier, top-k lock) has a time
+ *     limit; when one runs out the call returns BCM_ERR_TIMEOUT and the
+ *     CUDA context stays usable.
+ */
+#ifndef BCM_H
+#define BCM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bcm_graph* bcm_graph_t;
+
+typedef enum {
+    BCM_OK = 0,
+    BCM_ERR_INVALID = 1,        /* bad argument or malformed CSR */
+    BCM_ERR_NOT_SYMMETRIC = 2,  /* undirected graph whose arcs are not paired */
+    BCM_ERR_OOM = 3,            /* device memory exhausted */
+    BCM_ERR_CUDA = 4,           /* a CUDA call failed (message has the CUDA error) */
+    BCM_ERR_TIMEOUT = 5,        /* a bounded in-kernel wait ran out */
+    BCM_ERR_UNSUPPORTED = 6     /* size or option outside the supported range */
+} bcm_status;
+
+/* bcm_options.flags */
+#define BCM_OUT_DEVICE    0x1u  /* output pointers are device memory */
+#define BCM_NO_FOOTNOTE   0x2u  /* undirected: bound gamma_{d+1} by sum of deg(u), not deg(u)-1
+                                   (the footnote of Section 2.2 tightens; results are the same) */
+#define BCM_PLAIN         0x4u  /* bcm_topk: one source per kernel launch (comparison baseline) */
+#define BCM_NO_SEED       0x8u  /* bcm_topk: skip the grid-wide first wave */
+#define BCM_CHECK_SYMMETRIC 0x10u /* bcm_graph_create: verify undirected arcs are paired */
+
+typedef struct {
+    uint32_t lanes;           /* sources per wave: 64, 128 or 256; 0 = library default */
+    uint32_t flags;           /* BCM_* flags above */
+    uint32_t blocks;          /* CTAs of the wave kernel; 0 = all that fit on the GPU */
+    uint32_t threads;         /* threads per CTA: 256, 512 or 1024; 0 = default (512) */
+    uint64_t wait_limit_ns;   /* limit of every in-kernel wait; 0 = default (20 s) */
+} bcm_options;
+
+typedef struct {
+    uint64_t m_vis;           /* arcs scanned, counted once per source scanning them
+                                 (Section 3.1's visited arcs) */
+    uint64_t visits;          /* (source, vertex) pairs reached */
+    uint64_t completed;       /* sources whose BFS ran to the end */
+    uint64_t cut;             /* sources stopped by the bound */
+    uint64_t waves;           /* waves (groups of sources expanded together) */
+    uint64_t levels;          /* BFS levels expanded, summed over waves */
+    uint64_t max_level;       /* deepest level expanded */
+    uint64_t frontier_words;  /* (vertex, 64-lane word) frontier entries expanded */
+    uint64_t arc_words;       /* (arc, frontier word) pairs scanned */
+    uint64_t new_words;       /* frontier words created */
+    uint64_t cleared_words;   /* words reset between waves */
+    uint64_t launches;        /* kernels this call launched */
+    double   kernel_ms;       /* device time of the BFS kernels (CUDA events) */
+    double   preprocess_ms;   /* device time of preprocessing done by this call */
+    double   total_ms;        /* wall time of the call */
+} bcm_stats;
+
+/*
+ * bcm_graph_create -- copy a CSR graph to the device and validate it.
+ *   row_ptr, col : CSR arrays (host memory, or device memory if
+ *                  ptr_on_device != 0).  Not retained.
+ *   n, m         : vertex and arc counts.
+ *   directed     : 0 = undirected (both arcs of each edge present), 1 = directed.
+ *   stream       : cudaStream_t used for all work on this graph (NULL = legacy default).
+ *   flags        : BCM_CHECK_SYMMETRIC or 0.
+ *   out          : receives the handle; release it with bcm_graph_destroy.
+ * Errors: BCM_ERR_INVALID (NULL pointer, row_ptr not monotone from 0 to m,
+ * a column >= n), BCM_ERR_NOT_SYMMETRIC, BCM_ERR_UNSUPPORTED (n >= 2^30 or
+ * m >= 2^32), BCM_ERR_OOM, BCM_ERR_CUDA.  Preprocessing (Algorithm 1's
+ * PreProcessing and the degree order) runs lazily on first use.
+ */
+bcm_status bcm_graph_create(const uint64_t* row_ptr, const uint32_t* col, uint32_t n, uint64_t m,
+                            int directed, int ptr_on_device, void* stream, uint32_t flags,
+                            bcm_graph_t* out);
+
+/* bcm_graph_destroy -- free the handle and its device memory (NULL is a no-op). */
+bcm_status bcm_graph_destroy(bcm_graph_t g);
+
+/*
+ * bcm_preprocess -- run PreProcessing now (Algorithm 1, first line):
+ *   undirected: r(v) = size of v's connected component (Section 2.2);
+ *   directed:   SCCs, the weighted SCC DAG and alpha(v) <= r(v) <= omega(v)
+ *               (Section 2.3), omega held at n;
+ * and the processing order (degree descending, id ascending; Section 2.1).
+ * Idempotent.  Any output pointer may be NULL; when given, each receives n
+ * uint32 values (host memory unless out_on_device):
+ *   order : vertex ids in processing order;
+ *   x_lo  : r(v) (undirected) or alpha(v);  x_hi : r(v) or omega(v).
+ */
+bcm_status bcm_preprocess(bcm_graph_t g, uint32_t* order, uint32_t* x_lo, uint32_t* x_hi,
+                          int out_on_device);
+
+/*
+ * bcm_scc_bounds -- Section 1.3 / 2.3 for a directed graph: comp[v] (SCC
+ * label in [0, n_scc), labels ordered by smallest member id), alpha[v],
+ * omega[v] (n uint32 each) and the SCC count.  Any pointer may be NULL.
+ * Undirected graphs: components play the role of SCCs and
+ * alpha = omega = r.  Host memory unless out_on_device.
+ */
+bcm_status bcm_scc_bounds(bcm_graph_t g, uint32_t* comp, uint32_t* alpha, uint32_t* omega,
+                          uint32_t* n_scc, int out_on_device);
+
+/*
+ * bcm_topk -- the k most central vertices (Algorithm 1).
+ *   k      : 1 <= k <= 1024.  min(k, n) entries are written.
+ *   opt    : NULL for defaults.
+ *   ids, farness, reach : min(k, n) entries each, best first: vertex id,
+ *            f(v) (uint64) and r(v) (uint32).
+ *   stats  : NULL or receives counters and timings.
+ * Errors: BCM_ERR_INVALID (k outside 1..1024, NULL outputs),
+ * BCM_ERR_TIMEOUT, BCM_ERR_OOM, BCM_ERR_CUDA.
+ */
+bcm_status bcm_topk(bcm_graph_t g, uint32_t k, const bcm_options* opt, uint32_t* ids,
+                    uint64_t* farness, uint32_t* reach, bcm_stats* stats);
+
+/*
+ * bcm_farness_all -- f(v) and r(v) of every vertex by a complete BFS from
+ * each one (the textbook algorithm of Section 2.1, no cut), n entries each,
+ * indexed by vertex id.  opt may be NULL.
+ */
+bcm_status bcm_farness_all(bcm_graph_t g, const bcm_options* opt, uint64_t* farness, uint32_t* reach,
+                           bcm_stats* stats);
+
+/* Thread-local message for the last failing call ("" if none). */
+const char* bcm_last_error(void);
+
+/* Kernels launched by this library in this process so far. */
+uint64_t bcm_launch_count(void);
+
+/* Device bytes a bcm_topk / bcm_farness_all run on this graph holds with
+ * these options (graph copy excluded); 0 on bad arguments. */
+uint64_t bcm_workspace_bytes(bcm_graph_t g, const bcm_options* opt);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BCM_H */

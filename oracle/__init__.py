@@ -77,6 +77,8 @@ def _get():
         lib.oracle_bound_trace.restype = ctypes.c_int64
         lib.oracle_bound_trace.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_uint32,
                                            ctypes.c_int, ctypes.c_uint64, _i64p, ctypes.c_uint64]
+        lib.oracle_order.restype = None
+        lib.oracle_order.argtypes = [ctypes.c_uint32, _u64p, _u32p]
         lib.oracle_bcm.restype = ctypes.c_int64
         lib.oracle_bcm.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int, ctypes.c_uint32,
                                    ctypes.c_int, ctypes.c_int, _u32p, _u64p, _u32p,
@@ -167,6 +169,14 @@ def alpha_omega(g):
     if nc < 0:
         raise MemoryError("oracle_alpha_omega failed")
     return comp[:g.n], al[:g.n], om[:g.n], int(nc)
+
+
+def order(g):
+    """Algorithm 1's processing order: degree descending, ids ascending on ties."""
+    rp, _ = _csr(g)
+    out = np.zeros(max(g.n, 1), np.uint32)
+    _get().oracle_order(g.n, _p(rp, _u64p), _p(out, _u32p))
+    return out[:g.n]
 
 
 def bound_trace(g, v, x, mode=GT_TABLE1):

@@ -446,6 +446,13 @@ static int cmp_order(const void *pa, const void *pb, void *pc) {
     return a < b ? -1 : (a > b);
 }
 
+/* Algorithm 1's processing order: decreasing degree (outdeg on digraphs),
+ * equal degrees by increasing id. */
+void oracle_order(uint32_t n, const uint64_t *row_ptr, uint32_t *order) {
+    for (uint32_t v = 0; v < n; ++v) order[v] = v;
+    qsort_r(order, n, sizeof(uint32_t), cmp_order, (void *)row_ptr);
+}
+
 /* Algorithm 1: preprocessing, vertices in decreasing order of degree
  * (outdeg on digraphs; equal degrees by increasing id), BFSCut(v, x_k) each,
  * the k-th best kept in a size-k rank-ordered buffer.

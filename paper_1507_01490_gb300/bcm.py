@@ -1,0 +1,233 @@
+"""Python binding of the C-ABI in ``include/bcm.h`` (ctypes, argument
+marshalling only: every step of the computation runs in ``libbcm.so``'s CUDA
+kernels).
+
+Functions keep the C names.  Array arguments may be numpy arrays (host
+memory) or torch CUDA tensors (device memory, passed by ``data_ptr()``); plain
+integers are taken as raw addresses.  A non-OK status raises ``BcmError``
+carrying the status and ``bcm_last_error()``.
+
+``BcmGraph`` is a small convenience wrapper over the same calls.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+BCM_OK, BCM_ERR_INVALID, BCM_ERR_NOT_SYMMETRIC, BCM_ERR_OOM, BCM_ERR_CUDA, BCM_ERR_TIMEOUT, \
+    BCM_ERR_UNSUPPORTED = range(7)
+STATUS_NAMES = {0: "BCM_OK", 1: "BCM_ERR_INVALID", 2: "BCM_ERR_NOT_SYMMETRIC", 3: "BCM_ERR_OOM",
+                4: "BCM_ERR_CUDA", 5: "BCM_ERR_TIMEOUT", 6: "BCM_ERR_UNSUPPORTED"}
+
+BCM_OUT_DEVICE = 0x1
+BCM_NO_FOOTNOTE = 0x2
+BCM_PLAIN = 0x4
+BCM_NO_SEED = 0x8
+BCM_CHECK_SYMMETRIC = 0x10
+
+# every symbol include/bcm.h declares
+EXPORTS = ["bcm_graph_create", "bcm_graph_destroy", "bcm_preprocess", "bcm_scc_bounds", "bcm_topk",
+           "bcm_farness_all", "bcm_last_error", "bcm_launch_count", "bcm_workspace_bytes"]
+
+
+class bcm_options(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("blocks", ctypes.c_uint32),
+                ("threads", ctypes.c_uint32), ("wait_limit_ns", ctypes.c_uint64)]
+
+
+class bcm_stats(ctypes.Structure):
+    _fields_ = [("m_vis", ctypes.c_uint64), ("visits", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("cut", ctypes.c_uint64), ("waves", ctypes.c_uint64), ("levels", ctypes.c_uint64),
+                ("max_level", ctypes.c_uint64), ("frontier_words", ctypes.c_uint64),
+                ("arc_words", ctypes.c_uint64), ("new_words", ctypes.c_uint64),
+                ("cleared_words", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("kernel_ms", ctypes.c_double), ("preprocess_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class BcmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+_lib = None
+LIB_PATH = os.path.join(_build.LIB_DIR, "libbcm.so")
+
+
+def load():
+    """The loaded libbcm.so.  Raises if the CUDA library has not been built:
+    there is no other implementation to fall back to."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libbcm.so is not built (run __graft_entry__.build() or "
+                           "python -m paper_1507_01490_gb300._build)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    sig = {
+        "bcm_graph_create": (i32, [vp, vp, u32, u64, i32, i32, vp, u32, ctypes.POINTER(vp)]),
+        "bcm_graph_destroy": (i32, [vp]),
+        "bcm_preprocess": (i32, [vp, vp, vp, vp, i32]),
+        "bcm_scc_bounds": (i32, [vp, vp, vp, vp, vp, i32]),
+        "bcm_topk": (i32, [vp, u32, ctypes.POINTER(bcm_options), vp, vp, vp, ctypes.POINTER(bcm_stats)]),
+        "bcm_farness_all": (i32, [vp, ctypes.POINTER(bcm_options), vp, vp, ctypes.POINTER(bcm_stats)]),
+        "bcm_last_error": (ctypes.c_char_p, []),
+        "bcm_launch_count": (u64, []),
+        "bcm_workspace_bytes": (u64, [vp, ctypes.POINTER(bcm_options)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError("cannot pass %r" % type(a))
+
+
+def _check(st):
+    if st != BCM_OK:
+        raise BcmError(st, bcm_last_error())
+
+
+def bcm_last_error() -> str:
+    return load().bcm_last_error().decode()
+
+
+def bcm_launch_count() -> int:
+    return int(load().bcm_launch_count())
+
+
+def make_options(lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0) -> bcm_options:
+    return bcm_options(lanes, flags, blocks, threads, wait_limit_ns)
+
+
+def bcm_graph_create(row_ptr, col, n, m, directed, ptr_on_device=False, stream=None, flags=0):
+    h = ctypes.c_void_p()
+    _check(load().bcm_graph_create(_ptr(row_ptr), _ptr(col), n, m, int(bool(directed)),
+                                   int(bool(ptr_on_device)), _ptr(stream) if stream is not None else None,
+                                   flags, ctypes.byref(h)))
+    return h
+
+
+def bcm_graph_destroy(h):
+    _check(load().bcm_graph_destroy(h))
+
+
+def bcm_preprocess(h, order=None, x_lo=None, x_hi=None, out_on_device=False):
+    _check(load().bcm_preprocess(h, _ptr(order), _ptr(x_lo), _ptr(x_hi), int(bool(out_on_device))))
+
+
+def bcm_scc_bounds(h, comp=None, alpha=None, omega=None, out_on_device=False):
+    """Returns n_scc; fills comp/alpha/omega (n uint32 each) when given."""
+    n_scc = ctypes.c_uint32(0)
+    if out_on_device:   # the count goes to a host variable either way
+        _check(load().bcm_scc_bounds(h, _ptr(comp), _ptr(alpha), _ptr(omega), None, 1))
+        _check(load().bcm_scc_bounds(h, None, None, None, ctypes.addressof(n_scc), 0))
+    else:
+        _check(load().bcm_scc_bounds(h, _ptr(comp), _ptr(alpha), _ptr(omega), ctypes.addressof(n_scc), 0))
+    return int(n_scc.value)
+
+
+def bcm_topk(h, k, options, ids, farness, reach, stats=None):
+    _check(load().bcm_topk(h, k, ctypes.byref(options) if options is not None else None, _ptr(ids),
+                           _ptr(farness), _ptr(reach), ctypes.byref(stats) if stats is not None else None))
+
+
+def bcm_farness_all(h, options, farness, reach, stats=None):
+    _check(load().bcm_farness_all(h, ctypes.byref(options) if options is not None else None, _ptr(farness),
+                                  _ptr(reach), ctypes.byref(stats) if stats is not None else None))
+
+
+def bcm_workspace_bytes(h, options=None) -> int:
+    return int(load().bcm_workspace_bytes(h, ctypes.byref(options) if options is not None else None))
+
+
+class BcmGraph:
+    """A graph handle: ``BcmGraph(row_ptr, col, n, directed)`` with host numpy
+    arrays, or torch CUDA tensors and ``on_device=True``."""
+
+    def __init__(self, row_ptr, col, n, directed, on_device=False, stream=None, flags=0):
+        m = int(col.shape[0]) if hasattr(col, "shape") else int(len(col))
+        self.n, self.m, self.directed = int(n), m, bool(directed)
+        if not on_device:
+            row_ptr = np.ascontiguousarray(row_ptr, dtype=np.uint64)
+            col = np.ascontiguousarray(col, dtype=np.uint32)
+            if col.size == 0:
+                col = np.zeros(1, np.uint32)
+        self.h = bcm_graph_create(row_ptr, col, self.n, m, directed, on_device, stream, flags)
+
+    @classmethod
+    def from_graph(cls, g, **kw):
+        return cls(g.row_ptr, g.col, g.n, g.directed, **kw)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            bcm_graph_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def preprocess(self):
+        order = np.zeros(max(self.n, 1), np.uint32)
+        lo = np.zeros(max(self.n, 1), np.uint32)
+        hi = np.zeros(max(self.n, 1), np.uint32)
+        bcm_preprocess(self.h, order, lo, hi)
+        return order[:self.n], lo[:self.n], hi[:self.n]
+
+    def scc_bounds(self):
+        comp = np.zeros(max(self.n, 1), np.uint32)
+        al = np.zeros(max(self.n, 1), np.uint32)
+        om = np.zeros(max(self.n, 1), np.uint32)
+        nc = bcm_scc_bounds(self.h, comp, al, om)
+        return comp[:self.n], al[:self.n], om[:self.n], nc
+
+    def topk(self, k, lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0):
+        kk = max(min(k, self.n), 1)
+        ids = np.zeros(kk, np.uint32)
+        far = np.zeros(kk, np.uint64)
+        reach = np.zeros(kk, np.uint32)
+        st = bcm_stats()
+        bcm_topk(self.h, k, make_options(lanes, flags, blocks, threads, wait_limit_ns), ids, far, reach, st)
+        kk = min(k, self.n)
+        return ids[:kk], far[:kk], reach[:kk], st.as_dict()
+
+    def farness_all(self, lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0):
+        far = np.zeros(max(self.n, 1), np.uint64)
+        reach = np.zeros(max(self.n, 1), np.uint32)
+        st = bcm_stats()
+        bcm_farness_all(self.h, make_options(lanes, flags, blocks, threads, wait_limit_ns), far, reach, st)
+        return far[:self.n], reach[:self.n], st.as_dict()

@@ -1,0 +1,658 @@
+// The C-ABI of include/bcm.h: graph handles, preprocessing, the wave
+// kernels' workspace and launch sequence, and error reporting.
+#include <atomic>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "bcm.h"
+#include "internal.h"
+
+namespace bcm {
+
+static std::atomic<uint64_t> g_launches{0};
+void note_launch(int count) { g_launches.fetch_add((uint64_t)count, std::memory_order_relaxed); }
+
+static thread_local std::string t_err;
+
+static bcm_status fail(bcm_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return st;
+}
+
+static bcm_status cuda_fail(cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(BCM_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return fail(BCM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CU(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// ---------------------------------------------------------- workspaces
+// The slot region of the wave kernels is large (36 n W bytes per CTA) and
+// must start zeroed; every successful run leaves it zeroed again.  Clean
+// regions are kept here for reuse instead of being freed and re-zeroed.
+struct Region { int dev; void* ptr; size_t bytes; };
+static std::mutex g_region_mu;
+static std::vector<Region> g_regions;
+
+static bcm_status region_acquire(size_t bytes, cudaStream_t s, Region* out) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lk(g_region_mu);
+        int best = -1;
+        for (size_t i = 0; i < g_regions.size(); ++i)
+            if (g_regions[i].dev == dev && g_regions[i].bytes >= bytes &&
+                (best < 0 || g_regions[i].bytes < g_regions[best].bytes))
+                best = (int)i;
+        if (best >= 0) {
+            *out = g_regions[best];
+            g_regions.erase(g_regions.begin() + best);
+            return BCM_OK;
+        }
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        // drop cached regions of this device and retry once
+        std::vector<Region> drop;
+        {
+            std::lock_guard<std::mutex> lk(g_region_mu);
+            for (size_t i = 0; i < g_regions.size();)
+                if (g_regions[i].dev == dev) { drop.push_back(g_regions[i]); g_regions.erase(g_regions.begin() + i); }
+                else ++i;
+        }
+        cudaGetLastError();
+        for (auto& r : drop) cudaFree(r.ptr);
+        e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
+    }
+    CU(cudaMemsetAsync(p, 0, bytes, s), "workspace clear");
+    *out = Region{dev, p, bytes};
+    return BCM_OK;
+}
+
+static void region_release(Region& r, bool clean) {
+    if (!r.ptr) return;
+    if (clean) {
+        std::lock_guard<std::mutex> lk(g_region_mu);
+        g_regions.push_back(r);
+    } else {
+        cudaFree(r.ptr);
+    }
+    r.ptr = nullptr;
+    r.bytes = 0;
+}
+
+// Small per-run state of the wave kernels (all zeroed before a run).
+struct Aux {
+    uint32_t topk_id[1024];
+    u64 topk_f[1024];
+    uint32_t topk_r[1024];
+    uint32_t topk_count;
+    uint32_t lock;
+    uint32_t head;
+    int err;
+    Threshold thr;
+    unsigned long long stats[ST_COUNT];
+    GridBarrier bar;
+    uint32_t gcnt[1024];
+    uint32_t glist_n[2];
+    uint32_t glog_n;
+};
+
+}  // namespace bcm
+
+using namespace bcm;
+
+struct bcm_graph {
+    uint32_t n = 0;
+    uint64_t m = 0;
+    int directed = 0;
+    cudaStream_t stream = nullptr;
+    int dev = 0;
+    uint32_t* d_rp = nullptr;
+    uint32_t* d_col = nullptr;
+    uint32_t* d_order = nullptr;
+    uint32_t* d_xlo = nullptr;
+    uint32_t* d_xhi = nullptr;
+    uint32_t* d_comp = nullptr;    // component / SCC label, smallest-member order
+    uint32_t n_comp = 0;
+    bool preprocessed = false;
+    Aux* d_aux = nullptr;
+    uint32_t* d_plain = nullptr;   // stamps [n], two vertex queues [2n]
+    unsigned long long* d_far = nullptr;   // exhaustive outputs [n]
+    uint32_t* d_reach = nullptr;
+    Region slots{0, nullptr, 0};
+    int sms = 0;
+};
+
+namespace {
+
+constexpr uint64_t kDefaultLimitNs = 20ull * 1000 * 1000 * 1000;
+
+struct Cfg {
+    int W, threads, blocks, seed_W, seed_blocks;
+    uint64_t limit_ns;
+    uint32_t flags;
+};
+
+bcm_status resolve(bcm_graph* g, const bcm_options* opt, Cfg* c) {
+    bcm_options o{};
+    if (opt) o = *opt;
+    c->flags = o.flags;
+    uint32_t lanes = o.lanes ? o.lanes : 64;
+    if (lanes != 64 && lanes != 128 && lanes != 256)
+        return fail(BCM_ERR_UNSUPPORTED, "lanes must be 64, 128 or 256 (got %u)", lanes);
+    c->W = (int)(lanes / 64);
+    c->threads = o.threads ? (int)o.threads : 512;
+    if (c->threads != 256 && c->threads != 512 && c->threads != 1024)
+        return fail(BCM_ERR_UNSUPPORTED, "threads must be 256, 512 or 1024 (got %u)", o.threads);
+    if (c->threads < 64 * c->W)
+        return fail(BCM_ERR_UNSUPPORTED, "threads (%d) must be >= lanes (%u)", c->threads, lanes);
+    int per = cta_blocks_per_sm(c->W, c->threads);
+    if (per < 1) return fail(BCM_ERR_CUDA, "wave kernel does not fit on an SM");
+    int maxb = per * g->sms;
+    c->blocks = o.blocks ? (int)o.blocks : maxb;
+    if (c->blocks > maxb) c->blocks = maxb;
+    c->limit_ns = o.wait_limit_ns ? o.wait_limit_ns : kDefaultLimitNs;
+    c->seed_W = 1;
+    c->seed_blocks = 0;
+    return BCM_OK;
+}
+
+size_t region_bytes(bcm_graph* g, const Cfg& c) {
+    size_t a = (size_t)c.blocks * slot_bytes(g->n, c.W);
+    size_t b = slot_bytes(g->n, 4);
+    return a > b ? a : b;
+}
+
+bcm_status ensure_aux(bcm_graph* g) {
+    if (g->d_aux) return BCM_OK;
+    CU(cudaMalloc(&g->d_aux, sizeof(Aux)), "aux allocation");
+    return BCM_OK;
+}
+
+bcm_status ensure_slots(bcm_graph* g, size_t bytes) {
+    if (g->slots.ptr && g->slots.bytes >= bytes) return BCM_OK;
+    region_release(g->slots, true);
+    return region_acquire(bytes, g->stream, &g->slots);
+}
+
+bcm_status check_dev_err(int err) {
+    if (err == 0) return BCM_OK;
+    if (err & (DEV_ERR_BARRIER_TIMEOUT | DEV_ERR_LOCK_TIMEOUT))
+        return fail(BCM_ERR_TIMEOUT, "an in-kernel wait ran past its limit (device error bits 0x%x)", err);
+    if (err & DEV_ERR_INVALID_CSR) return fail(BCM_ERR_INVALID, "malformed CSR (device check 0x%x)", err);
+    return fail(BCM_ERR_CUDA, "device error bits 0x%x", err);
+}
+
+double ms_since(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// ------------------------------------------------------ preprocessing
+bcm_status preprocess(bcm_graph* g, double* ms) {
+    if (g->preprocessed) return BCM_OK;
+    cudaStream_t s = g->stream;
+    const uint32_t n = g->n;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0), "event");
+    CU(cudaEventCreate(&e1), "event");
+    CU(cudaEventRecord(e0, s), "event record");
+    size_t nb = ((size_t)n * sizeof(uint32_t) + 255) & ~(size_t)255;
+    size_t scratch = 2 * nb + degree_order_scratch_bytes(n) + scan_scratch_bytes((size_t)n + 1) + 1024;
+    if (g->directed) {
+        size_t sc = scc_scratch_bytes(n, g->m);
+        if (sc > scratch) scratch = sc;
+    }
+    if (!g->d_order) {
+        CU(cudaMalloc(&g->d_order, nb * 4), "preprocess allocation");
+        g->d_xlo = (uint32_t*)((char*)g->d_order + nb);
+        g->d_xhi = (uint32_t*)((char*)g->d_order + 2 * nb);
+        g->d_comp = (uint32_t*)((char*)g->d_order + 3 * nb);
+    }
+    char* d_scr = nullptr;
+    CU(cudaMalloc(&d_scr, scratch), "preprocess scratch");
+    int* d_err = (int*)(d_scr + scratch - 256);
+    bcm_status st = BCM_OK;
+    int herr = 0;
+    do {
+        if (cudaMemsetAsync(d_err, 0, sizeof(int), s) != cudaSuccess) { st = fail(BCM_ERR_CUDA, "memset"); break; }
+        if (n == 0) break;
+        if (!g->directed) {
+            uint32_t* parent = g->d_comp;
+            uint32_t* size = (uint32_t*)d_scr;
+            if (launch_cc_reach(g->d_rp, g->d_col, n, parent, size, g->d_xlo, g->d_xhi, d_err, s)) {
+                st = fail(BCM_ERR_CUDA, "component kernels: %s", cudaGetErrorString(cudaGetLastError()));
+                break;
+            }
+            // labels: rank of the component's smallest vertex among all such
+            uint32_t* flags = size;   // reuse: size no longer needed after reach
+            uint32_t* total = (uint32_t*)(d_scr + scratch - 512);
+            if (launch_root_flags(parent, n, flags, s) ||
+                exclusive_scan_u32(flags, flags, n, total, d_scr + nb, s) ||
+                launch_relabel(parent, flags, n, s)) {
+                st = fail(BCM_ERR_CUDA, "component labels");
+                break;
+            }
+            if (cudaMemcpyAsync(&g->n_comp, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+                st = fail(BCM_ERR_CUDA, "copy");
+                break;
+            }
+        } else {
+            uint32_t nscc = 0;
+            int rc = launch_scc_bounds(g->d_rp, g->d_col, n, g->m, g->d_comp, g->d_xlo, g->d_xhi, &nscc, d_scr,
+                                       scratch - 1024, d_err, s);
+            if (rc == -2) { st = fail(BCM_ERR_UNSUPPORTED, "directed preprocessing is not available"); break; }
+            if (rc) { st = fail(BCM_ERR_CUDA, "SCC kernels: %s", cudaGetErrorString(cudaGetLastError())); break; }
+            g->n_comp = nscc;
+        }
+        if (launch_degree_order(g->d_rp, n, g->d_order, d_scr, scratch - 1024, s)) {
+            st = fail(BCM_ERR_CUDA, "degree order: %s", cudaGetErrorString(cudaGetLastError()));
+            break;
+        }
+        if (cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+            st = fail(BCM_ERR_CUDA, "copy");
+            break;
+        }
+    } while (0);
+    cudaEventRecord(e1, s);
+    cudaError_t se = cudaStreamSynchronize(s);
+    cudaFree(d_scr);
+    float t = 0;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != BCM_OK) return st;
+    if (se != cudaSuccess) return cuda_fail(se, "preprocessing");
+    if (herr) return check_dev_err(herr);
+    g->preprocessed = true;
+    if (ms) *ms += t;
+    return BCM_OK;
+}
+
+WaveParams base_params(bcm_graph* g, const Cfg& c) {
+    WaveParams p;
+    memset(&p, 0, sizeof(p));
+    p.g.n = g->n;
+    p.g.m = g->m;
+    p.g.rp = g->d_rp;
+    p.g.col = g->d_col;
+    p.g.order = g->d_order;
+    p.g.xlo = g->d_xlo;
+    p.g.xhi = g->d_xhi;
+    p.footnote = (!g->directed && !(c.flags & BCM_NO_FOOTNOTE)) ? 1u : 0u;
+    Aux* a = g->d_aux;
+    p.head = &a->head;
+    p.n_end = g->n;
+    p.topk.id = a->topk_id;
+    p.topk.f = a->topk_f;
+    p.topk.r = a->topk_r;
+    p.topk.count = &a->topk_count;
+    p.topk.lock = &a->lock;
+    p.topk.thr = &a->thr;
+    p.slot_base = (char*)g->slots.ptr;
+    p.slot_stride = slot_bytes(g->n, c.W);
+    p.stats = a->stats;
+    p.err = &a->err;
+    p.lock_limit_ns = c.limit_ns;
+    p.barrier_limit_ns = c.limit_ns;
+    p.bar = &a->bar;
+    p.gcnt = a->gcnt;
+    p.glist_n = a->glist_n;
+    p.glog_n = &a->glog_n;
+    return p;
+}
+
+void fill_stats(bcm_stats* s, const unsigned long long* st, uint64_t launches, double kms, double pms, double tms) {
+    if (!s) return;
+    s->m_vis = st[ST_MVIS];
+    s->visits = st[ST_DISC];
+    s->completed = st[ST_COMPLETED];
+    s->cut = st[ST_CUT];
+    s->waves = st[ST_WAVES];
+    s->levels = st[ST_LEVELS];
+    s->max_level = st[ST_MAXLEVEL];
+    s->frontier_words = st[ST_ENTRIES];
+    s->arc_words = st[ST_ARCWORDS];
+    s->new_words = st[ST_DISCWORDS];
+    s->cleared_words = st[ST_CLEARED];
+    s->launches = launches;
+    s->kernel_ms = kms;
+    s->preprocess_ms = pms;
+    s->total_ms = tms;
+}
+
+// Runs the wave kernels.  exhaustive: every source, no cut; else top-k.
+bcm_status run_waves(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, unsigned long long* stats_out,
+                     double* kernel_ms) {
+    cudaStream_t s = g->stream;
+    bcm_status st = ensure_aux(g);
+    if (st) return st;
+    const bool plain = !exhaustive && (c.flags & BCM_PLAIN);
+    if (!plain) {
+        st = ensure_slots(g, region_bytes(g, c));
+        if (st) return st;
+    }
+    CU(cudaMemsetAsync(g->d_aux, 0, sizeof(Aux), s), "aux clear");
+    if (exhaustive && !g->d_far) {
+        CU(cudaMalloc(&g->d_far, (size_t)g->n * sizeof(uint64_t) + 256), "output allocation");
+        CU(cudaMalloc(&g->d_reach, (size_t)g->n * sizeof(uint32_t) + 256), "output allocation");
+    }
+    WaveParams p = base_params(g, c);
+    p.exhaustive = exhaustive ? 1u : 0u;
+    p.topk.k = k;
+    p.out_far = g->d_far;
+    p.out_reach = g->d_reach;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0), "event");
+    CU(cudaEventCreate(&e1), "event");
+    CU(cudaEventRecord(e0, s), "event record");
+    int rc = 0;
+    if (plain) {
+        if (!g->d_plain) CU(cudaMalloc(&g->d_plain, (size_t)g->n * 3 * sizeof(uint32_t) + 256), "plain buffers");
+        CU(cudaMemsetAsync(g->d_plain, 0, (size_t)g->n * sizeof(uint32_t), s), "stamp clear");
+        int blocks = max_coop_blocks(1, 1, 256);
+        int want = g->sms;   // one 256-thread CTA per SM
+        if (blocks > want) blocks = want;
+        for (uint32_t it = 0; it < g->n && rc == 0; ++it)
+            rc = launch_plain_source(p, it, g->d_plain, g->d_plain + g->n, blocks, 256, s);
+    } else {
+        uint32_t head0 = 0;
+        if (!exhaustive && !(c.flags & BCM_NO_SEED) && g->n > 0) {
+            int sw = (int)((k + 63) / 64);
+            sw = sw <= 1 ? 1 : (sw <= 2 ? 2 : 4);
+            p.seed_lanes = (uint32_t)(64 * sw) < g->n ? (uint32_t)(64 * sw) : g->n;
+            int blocks = max_coop_blocks(0, sw, 512);
+            if (blocks > g->sms) blocks = g->sms;
+            rc = launch_seed_wave(p, sw, blocks, 512, s);
+            head0 = p.seed_lanes;
+        }
+        if (rc == 0 && head0 < g->n) {
+            if (head0) {
+                if (cudaMemcpyAsync(&g->d_aux->head, &head0, sizeof(uint32_t), cudaMemcpyHostToDevice, s) != cudaSuccess)
+                    rc = -1;
+            }
+            if (rc == 0) rc = launch_cta_waves(p, c.W, c.blocks, c.threads, s);
+        }
+    }
+    cudaEventRecord(e1, s);
+    if (rc) {
+        cudaStreamSynchronize(s);
+        return fail(BCM_ERR_CUDA, "wave kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    int herr = 0;
+    CU(cudaMemcpyAsync(&herr, &g->d_aux->err, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+    CU(cudaMemcpyAsync(stats_out, g->d_aux->stats, sizeof(unsigned long long) * ST_COUNT, cudaMemcpyDeviceToHost, s),
+       "copy");
+    cudaError_t se = cudaStreamSynchronize(s);
+    float t = 0;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (se != cudaSuccess) return cuda_fail(se, "wave kernels");
+    *kernel_ms = t;
+    if (herr) {
+        // a timed-out run may leave words set: do not reuse the region
+        region_release(g->slots, false);
+        return check_dev_err(herr);
+    }
+    return BCM_OK;
+}
+
+bcm_status copy_out(void* dst, const void* src, size_t bytes, bool dev, cudaStream_t s) {
+    CU(cudaMemcpyAsync(dst, src, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s), "output copy");
+    return BCM_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------ symmetric-pairs check
+namespace bcm {
+__global__ void k_check_symmetric(const uint32_t* rp, const uint32_t* col, uint32_t n, int* bad) {
+    size_t warp = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5;
+    size_t nw = ((size_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t lane = threadIdx.x & 31;
+    for (size_t u = warp; u < n; u += nw) {
+        for (uint32_t e = rp[u] + lane; e < rp[u + 1]; e += 32) {
+            uint32_t w = col[e];
+            if (e + 1 < rp[u + 1] && col[e + 1] < w) { atomicOr(bad, 2); continue; }   // rows must be sorted
+            uint32_t lo = rp[w], hi = rp[w + 1];
+            while (lo < hi) {
+                uint32_t mid = lo + (hi - lo) / 2;
+                if (col[mid] < u) lo = mid + 1; else hi = mid;
+            }
+            if (lo >= rp[w + 1] || col[lo] != u) atomicOr(bad, 1);
+        }
+    }
+}
+
+__global__ void k_root_flags(const uint32_t* parent, uint32_t n, uint32_t* flags) {
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += stride)
+        flags[v] = parent[v] == v ? 1u : 0u;
+}
+
+__global__ void k_relabel(uint32_t* parent, const uint32_t* rank, uint32_t n) {
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += stride)
+        parent[v] = rank[parent[v]];
+}
+
+int launch_root_flags(const uint32_t* parent, uint32_t n, uint32_t* flags, cudaStream_t s) {
+    k_root_flags<<<(n + 255) / 256 < 4864 ? (n + 255) / 256 : 4864, 256, 0, s>>>(parent, n, flags);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// parent[v] holds a root id; rank[root] its label.  Roots are relabelled
+// last, after every vertex read them, by a second pass.
+int launch_relabel(uint32_t* parent, const uint32_t* rank, uint32_t n, cudaStream_t s) {
+    // rank[] is the exclusive scan of the root flags; parent[v] = rank[parent[v]]
+    // is safe in one pass because rank is a separate array.
+    k_relabel<<<(n + 255) / 256 < 4864 ? (n + 255) / 256 : 4864, 256, 0, s>>>(parent, rank, n);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace bcm
+
+// ================================================================= C-ABI
+extern "C" {
+
+const char* bcm_last_error(void) { return t_err.c_str(); }
+
+uint64_t bcm_launch_count(void) { return g_launches.load(); }
+
+bcm_status bcm_graph_create(const uint64_t* row_ptr, const uint32_t* col, uint32_t n, uint64_t m, int directed,
+                            int ptr_on_device, void* stream, uint32_t flags, bcm_graph_t* out) {
+    t_err.clear();
+    if (!out) return fail(BCM_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!row_ptr || (m > 0 && !col)) return fail(BCM_ERR_INVALID, "row_ptr/col is NULL");
+    if (n >= (1u << 30)) return fail(BCM_ERR_UNSUPPORTED, "n = %u: at most 2^30 - 1 vertices", n);
+    if (m >= (1ull << 32)) return fail(BCM_ERR_UNSUPPORTED, "m = %llu: fewer than 2^32 arcs", (unsigned long long)m);
+    bcm_graph* g = new (std::nothrow) bcm_graph();
+    if (!g) return fail(BCM_ERR_OOM, "host allocation");
+    g->n = n;
+    g->m = m;
+    g->directed = directed ? 1 : 0;
+    g->stream = (cudaStream_t)stream;
+    cudaGetDevice(&g->dev);
+    cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->dev);
+    cudaStream_t s = g->stream;
+    bcm_status st = BCM_OK;
+    uint64_t* d_rp64 = nullptr;
+    int* d_err = nullptr;
+    do {
+        cudaError_t e;
+        if ((e = cudaMalloc(&g->d_rp, ((size_t)n + 1) * sizeof(uint32_t))) != cudaSuccess) { st = cuda_fail(e, "graph allocation"); break; }
+        if ((e = cudaMalloc(&g->d_col, (m ? m : 1) * sizeof(uint32_t))) != cudaSuccess) { st = cuda_fail(e, "graph allocation"); break; }
+        if ((e = cudaMalloc(&d_rp64, ((size_t)n + 1) * sizeof(uint64_t) + sizeof(int) * 2)) != cudaSuccess) { st = cuda_fail(e, "graph allocation"); break; }
+        d_err = (int*)(d_rp64 + n + 1);
+        cudaMemcpyKind kind = ptr_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        if ((e = cudaMemcpyAsync(d_rp64, row_ptr, ((size_t)n + 1) * sizeof(uint64_t), kind, s)) != cudaSuccess) { st = cuda_fail(e, "row_ptr copy"); break; }
+        if (m && (e = cudaMemcpyAsync(g->d_col, col, m * sizeof(uint32_t), kind, s)) != cudaSuccess) { st = cuda_fail(e, "col copy"); break; }
+        if ((e = cudaMemsetAsync(d_err, 0, 2 * sizeof(int), s)) != cudaSuccess) { st = cuda_fail(e, "memset"); break; }
+        if (launch_validate(d_rp64, g->d_col, n, m, d_err, s) || launch_narrow_offsets(d_rp64, g->d_rp, n, s)) {
+            st = fail(BCM_ERR_CUDA, "validation kernels: %s", cudaGetErrorString(cudaGetLastError()));
+            break;
+        }
+        int herr[2] = {0, 0};
+        if ((e = cudaMemcpyAsync(herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) { st = cuda_fail(e, "copy"); break; }
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { st = cuda_fail(e, "graph upload"); break; }
+        if (herr[0]) { st = fail(BCM_ERR_INVALID, "malformed CSR: row_ptr must rise from 0 to m and every col < n"); break; }
+        if (!directed && (flags & BCM_CHECK_SYMMETRIC) && n > 0) {
+            if ((e = cudaMemsetAsync(d_err + 1, 0, sizeof(int), s)) != cudaSuccess) { st = cuda_fail(e, "memset"); break; }
+            unsigned blocks = (unsigned)(((size_t)n * 32 + 255) / 256);
+            if (blocks > 4864) blocks = 4864;
+            k_check_symmetric<<<blocks, 256, 0, s>>>(g->d_rp, g->d_col, n, d_err + 1);
+            note_launch();
+            if ((e = cudaMemcpyAsync(&herr[1], d_err + 1, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) { st = cuda_fail(e, "copy"); break; }
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { st = cuda_fail(e, "symmetry check"); break; }
+            if (herr[1] & 2) { st = fail(BCM_ERR_INVALID, "the symmetry check needs every row sorted"); break; }
+            if (herr[1] & 1) { st = fail(BCM_ERR_NOT_SYMMETRIC, "undirected graph has an arc (u,w) without (w,u)"); break; }
+        }
+    } while (0);
+    if (d_rp64) cudaFree(d_rp64);
+    if (st != BCM_OK) {
+        bcm_graph_destroy(g);
+        return st;
+    }
+    *out = g;
+    return BCM_OK;
+}
+
+bcm_status bcm_graph_destroy(bcm_graph_t g) {
+    if (!g) return BCM_OK;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(g->d_rp);
+    cudaFree(g->d_col);
+    cudaFree(g->d_order);
+    cudaFree(g->d_aux);
+    cudaFree(g->d_plain);
+    cudaFree(g->d_far);
+    cudaFree(g->d_reach);
+    region_release(g->slots, true);
+    delete g;
+    return BCM_OK;
+}
+
+bcm_status bcm_preprocess(bcm_graph_t g, uint32_t* order, uint32_t* x_lo, uint32_t* x_hi, int out_on_device) {
+    t_err.clear();
+    if (!g) return fail(BCM_ERR_INVALID, "graph is NULL");
+    bcm_status st = preprocess(g, nullptr);
+    if (st) return st;
+    size_t b = (size_t)g->n * sizeof(uint32_t);
+    if (b) {
+        if (order && (st = copy_out(order, g->d_order, b, out_on_device, g->stream))) return st;
+        if (x_lo && (st = copy_out(x_lo, g->d_xlo, b, out_on_device, g->stream))) return st;
+        if (x_hi && (st = copy_out(x_hi, g->d_xhi, b, out_on_device, g->stream))) return st;
+    }
+    CU(cudaStreamSynchronize(g->stream), "copy");
+    return BCM_OK;
+}
+
+bcm_status bcm_scc_bounds(bcm_graph_t g, uint32_t* comp, uint32_t* alpha, uint32_t* omega, uint32_t* n_scc,
+                          int out_on_device) {
+    t_err.clear();
+    if (!g) return fail(BCM_ERR_INVALID, "graph is NULL");
+    bcm_status st = preprocess(g, nullptr);
+    if (st) return st;
+    size_t b = (size_t)g->n * sizeof(uint32_t);
+    if (b) {
+        if (comp && (st = copy_out(comp, g->d_comp, b, out_on_device, g->stream))) return st;
+        if (alpha && (st = copy_out(alpha, g->d_xlo, b, out_on_device, g->stream))) return st;
+        if (omega && (st = copy_out(omega, g->d_xhi, b, out_on_device, g->stream))) return st;
+    }
+    CU(cudaStreamSynchronize(g->stream), "copy");
+    if (n_scc) {
+        if (out_on_device) CU(cudaMemcpy(n_scc, &g->n_comp, sizeof(uint32_t), cudaMemcpyHostToDevice), "copy");
+        else *n_scc = g->n_comp;
+    }
+    return BCM_OK;
+}
+
+bcm_status bcm_topk(bcm_graph_t g, uint32_t k, const bcm_options* opt, uint32_t* ids, uint64_t* farness,
+                    uint32_t* reach, bcm_stats* stats) {
+    t_err.clear();
+    auto t0 = std::chrono::steady_clock::now();
+    uint64_t l0 = g_launches.load();
+    if (!g) return fail(BCM_ERR_INVALID, "graph is NULL");
+    if (k < 1 || k > 1024) return fail(BCM_ERR_INVALID, "k = %u: must be in 1..1024", k);
+    if (!ids || !farness || !reach) return fail(BCM_ERR_INVALID, "output pointer is NULL");
+    double pms = 0, kms = 0;
+    bcm_status st = preprocess(g, &pms);
+    if (st) return st;
+    Cfg c;
+    if ((st = resolve(g, opt, &c))) return st;
+    unsigned long long sv[ST_COUNT] = {0};
+    uint32_t kk = k < g->n ? k : g->n;
+    if (g->n > 0) {
+        if ((st = run_waves(g, c, k, false, sv, &kms))) return st;
+        bool dev = (c.flags & BCM_OUT_DEVICE) != 0;
+        Aux* a = g->d_aux;
+        if ((st = copy_out(ids, a->topk_id, kk * sizeof(uint32_t), dev, g->stream))) return st;
+        if ((st = copy_out(farness, a->topk_f, kk * sizeof(uint64_t), dev, g->stream))) return st;
+        if ((st = copy_out(reach, a->topk_r, kk * sizeof(uint32_t), dev, g->stream))) return st;
+        uint32_t cnt = 0;
+        CU(cudaMemcpyAsync(&cnt, &a->topk_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream), "copy");
+        CU(cudaStreamSynchronize(g->stream), "copy");
+        if (cnt != kk) return fail(BCM_ERR_CUDA, "top-k holds %u entries, expected %u", cnt, kk);
+    }
+    fill_stats(stats, sv, g_launches.load() - l0, kms, pms, ms_since(t0));
+    return BCM_OK;
+}
+
+bcm_status bcm_farness_all(bcm_graph_t g, const bcm_options* opt, uint64_t* farness, uint32_t* reach,
+                           bcm_stats* stats) {
+    t_err.clear();
+    auto t0 = std::chrono::steady_clock::now();
+    uint64_t l0 = g_launches.load();
+    if (!g) return fail(BCM_ERR_INVALID, "graph is NULL");
+    if (!farness || !reach) return fail(BCM_ERR_INVALID, "output pointer is NULL");
+    double pms = 0, kms = 0;
+    bcm_status st = preprocess(g, &pms);
+    if (st) return st;
+    Cfg c;
+    if ((st = resolve(g, opt, &c))) return st;
+    unsigned long long sv[ST_COUNT] = {0};
+    if (g->n > 0) {
+        if ((st = run_waves(g, c, 0, true, sv, &kms))) return st;
+        bool dev = (c.flags & BCM_OUT_DEVICE) != 0;
+        if ((st = copy_out(farness, g->d_far, (size_t)g->n * sizeof(uint64_t), dev, g->stream))) return st;
+        if ((st = copy_out(reach, g->d_reach, (size_t)g->n * sizeof(uint32_t), dev, g->stream))) return st;
+        CU(cudaStreamSynchronize(g->stream), "copy");
+    }
+    fill_stats(stats, sv, g_launches.load() - l0, kms, pms, ms_since(t0));
+    return BCM_OK;
+}
+
+uint64_t bcm_workspace_bytes(bcm_graph_t g, const bcm_options* opt) {
+    if (!g) return 0;
+    Cfg c;
+    if (resolve(g, opt, &c)) return 0;
+    return (uint64_t)region_bytes(g, c) + sizeof(Aux) + (uint64_t)g->n * 12;
+}
+
+}  // extern "C"

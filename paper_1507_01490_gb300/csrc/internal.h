@@ -1,0 +1,112 @@
+// Internal interfaces between the library's translation units (not part of
+// the C-ABI).  Kernels are launched only through the functions declared here.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace bcm {
+
+// Counters accumulated by the wave kernels, in this order.
+enum Stat {
+    ST_MVIS = 0,        // arcs scanned, counted per source (Section 3.1's m_vis)
+    ST_DISC,            // (source, vertex) discoveries
+    ST_COMPLETED,       // sources whose BFS ran to the end
+    ST_CUT,             // sources stopped by the bound
+    ST_WAVES,           // waves run
+    ST_LEVELS,          // levels expanded, summed over waves
+    ST_MAXLEVEL,        // deepest level reached
+    ST_ENTRIES,         // frontier words expanded (level >= 1)
+    ST_ARCWORDS,        // (arc, frontier word) pairs scanned
+    ST_DISCWORDS,       // frontier words created (first discovery in a level)
+    ST_CLEARED,         // vertex words cleared at wave ends
+    ST_COUNT
+};
+
+// The graph as the kernels see it.  Offsets are narrowed to 32 bits (m < 2^32).
+struct GraphDev {
+    uint32_t n;
+    uint64_t m;
+    const uint32_t* rp;      // [n+1]
+    const uint32_t* col;     // [m]
+    const uint32_t* order;   // [n] vertices by (degree desc, id asc)
+    const uint32_t* xlo;     // [n] r(v) (undirected) or alpha(v)
+    const uint32_t* xhi;     // [n] r(v) (undirected) or omega(v)
+};
+
+// Per-slot working memory of one MS-BFS wave with W words (64W sources) per
+// vertex.  Word index of (vertex v, word g) is v*W + g.
+inline size_t slot_bytes(uint32_t n, int W) {
+    size_t nw = (size_t)n * W;
+    size_t b = nw * (3 * sizeof(uint64_t) + 3 * sizeof(uint32_t));
+    return (b + 255) & ~(size_t)255;
+}
+
+struct WaveParams {
+    GraphDev g;
+    uint32_t footnote;       // undirected: gamma~ uses deg(u)-1 for d >= 1
+    uint32_t exhaustive;     // 1: no cut, write farness/reach of every source
+    uint32_t* head;          // next position in `order` (atomic)
+    uint32_t n_end;          // sources are order[*head .. n_end)
+    TopK topk;
+    unsigned long long* out_far;   // exhaustive outputs, indexed by vertex id
+    uint32_t* out_reach;
+    char* slot_base;
+    size_t slot_stride;
+    unsigned long long* stats;   // [ST_COUNT]
+    int* err;
+    unsigned long long lock_limit_ns;
+    unsigned long long barrier_limit_ns;
+    // grid-wide (seed / plain) kernels only
+    GridBarrier* bar;
+    uint32_t* gcnt;          // [2][2][256] per-lane level counters (gamma, degree sum)
+    uint32_t* glist_n;       // [2] frontier list sizes
+    uint32_t* glog_n;        // [1] cleared-word log size
+    uint32_t seed_lanes;     // sources taken by the seed wave
+};
+
+// ---- preproc.cu
+int launch_validate(const uint64_t* rp64, const uint32_t* col, uint32_t n, uint64_t m, int* err,
+                    cudaStream_t s);
+int launch_narrow_offsets(const uint64_t* rp64, uint32_t* rp32, uint32_t n, cudaStream_t s);
+int launch_cc_reach(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t* parent,
+                    uint32_t* size, uint32_t* xlo, uint32_t* xhi, int* err, cudaStream_t s);
+int launch_degree_order(const uint32_t* rp, uint32_t n, uint32_t* order, void* scratch,
+                        size_t scratch_bytes, cudaStream_t s);
+size_t degree_order_scratch_bytes(uint32_t n);
+// stable LSD radix sort of (key, value) pairs on the low `bits` of the key
+size_t radix_scratch_bytes(size_t count);
+int radix_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
+                         size_t count, int bits, void* scratch, cudaStream_t s, bool* result_in_tmp);
+int radix_sort_u64(uint64_t* keys, uint64_t* keys_tmp, size_t count, int bits, void* scratch,
+                   cudaStream_t s, bool* result_in_tmp);
+// exclusive scan of u32 counts into u32 offsets (out may alias in); returns total via *total_dev
+size_t scan_scratch_bytes(size_t count);
+int exclusive_scan_u32(const uint32_t* in, uint32_t* out, size_t count, uint32_t* total_dev,
+                       void* scratch, cudaStream_t s);
+
+// component labels: flags[v] = (parent[v] == v); parent[v] = rank[parent[v]]
+int launch_root_flags(const uint32_t* parent, uint32_t n, uint32_t* flags, cudaStream_t s);
+int launch_relabel(uint32_t* parent, const uint32_t* rank, uint32_t n, cudaStream_t s);
+
+// ---- scc.cu
+struct SccResult { uint32_t n_scc; };
+size_t scc_scratch_bytes(uint32_t n, uint64_t m);
+int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, uint32_t n, uint64_t m,
+                      uint32_t* comp, uint32_t* xlo, uint32_t* xhi, uint32_t* n_scc_host,
+                      void* scratch, size_t scratch_bytes, int* err, cudaStream_t s);
+
+// ---- msbfs.cu
+int launch_seed_wave(const WaveParams& p, int W, int blocks, int threads, cudaStream_t s);
+int launch_cta_waves(const WaveParams& p, int W, int blocks, int threads, cudaStream_t s);
+int launch_plain_source(const WaveParams& p, uint32_t it, uint32_t* stamp, uint32_t* lists,
+                        int blocks, int threads, cudaStream_t s);
+int max_coop_blocks(int kind, int W, int threads);   // kind 0 seed, 1 plain
+int cta_blocks_per_sm(int W, int threads);
+
+// launch bookkeeping (api.cu)
+void note_launch(int count = 1);
+
+}  // namespace bcm

@@ -1,0 +1,398 @@
+// Preprocessing kernels (Algorithm 1's PreProcessing and the degree order):
+//   * CSR validation and 64->32-bit offset narrowing,
+//   * connected components for r(v) on undirected graphs (Section 2.2),
+//   * the processing order: decreasing degree, ties by increasing id
+//     (Section 2.1), as a stable LSD radix sort on the degree key,
+//   * scan and radix-sort primitives also used by the SCC pass.
+#include <cstdio>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace bcm {
+
+static inline int blocks_for(size_t n, int threads, int cap = 152 * 32) {
+    size_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > (size_t)cap) b = cap;
+    return (int)b;
+}
+
+// ------------------------------------------------------------ validation
+__global__ void k_validate(const uint64_t* rp, const uint32_t* col, uint32_t n, uint64_t m, int* err) {
+    size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    if (tid == 0 && (rp[0] != 0 || rp[n] != m)) atomicOr(err, DEV_ERR_INVALID_CSR);
+    for (size_t i = tid; i < n; i += stride)
+        if (rp[i] > rp[i + 1]) atomicOr(err, DEV_ERR_INVALID_CSR);
+    for (size_t e = tid; e < m; e += stride)
+        if (col[e] >= n) atomicOr(err, DEV_ERR_INVALID_CSR);
+}
+
+int launch_validate(const uint64_t* rp64, const uint32_t* col, uint32_t n, uint64_t m, int* err,
+                    cudaStream_t s) {
+    k_validate<<<blocks_for(m > n ? m : n, 256), 256, 0, s>>>(rp64, col, n, m, err);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+__global__ void k_narrow(const uint64_t* rp64, uint32_t* rp32, size_t cnt) {
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < cnt; i += stride)
+        rp32[i] = (uint32_t)rp64[i];
+}
+
+int launch_narrow_offsets(const uint64_t* rp64, uint32_t* rp32, uint32_t n, cudaStream_t s) {
+    k_narrow<<<blocks_for((size_t)n + 1, 256), 256, 0, s>>>(rp64, rp32, (size_t)n + 1);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ------------------------------------------------- connected components
+// Union-find with roots hooked under smaller roots, so every parent pointer
+// points to a smaller id and each component's root is its smallest vertex.
+__device__ __forceinline__ uint32_t uf_find(uint32_t* parent, uint32_t x) {
+    for (;;) {
+        uint32_t p = vload(&parent[x]);
+        if (p == x) return x;
+        uint32_t gp = vload(&parent[p]);
+        if (gp != p) vstore(&parent[x], gp);   // path halving; gp is still an ancestor
+        x = gp;
+    }
+}
+
+__global__ void k_uf_init(uint32_t* parent, uint32_t* size, uint32_t n) {
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += stride) {
+        parent[v] = (uint32_t)v;
+        size[v] = 0;
+    }
+}
+
+// One warp per vertex u; its arcs to larger ids are united with u.
+__global__ void k_uf_hook(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t* parent, int* err) {
+    const uint32_t lane = threadIdx.x & 31;
+    size_t warp = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5;
+    size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
+    for (size_t u = warp; u < n; u += nwarps) {
+        uint32_t beg = rp[u], end = rp[u + 1];
+        for (uint32_t e = beg + lane; e < end; e += 32) {
+            uint32_t w = col[e];
+            if (w <= u) continue;
+            uint32_t a = (uint32_t)u, b = w;
+            for (int it = 0;; ++it) {
+                if (it > (1 << 20)) { atomicOr(err, DEV_ERR_RETRY_LIMIT); break; }
+                a = uf_find(parent, a);
+                b = uf_find(parent, b);
+                if (a == b) break;
+                uint32_t hi = a > b ? a : b, lo = a > b ? b : a;
+                if (atomicCAS(&parent[hi], hi, lo) == hi) break;
+            }
+        }
+    }
+}
+
+__global__ void k_uf_compress_count(uint32_t* parent, uint32_t* size, uint32_t n) {
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += stride) {
+        uint32_t r = uf_find(parent, (uint32_t)v);
+        atomicAdd(&size[r], 1u);
+    }
+}
+
+__global__ void k_uf_reach(uint32_t* parent, const uint32_t* size, uint32_t n, uint32_t* xlo, uint32_t* xhi) {
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += stride) {
+        uint32_t r = uf_find(parent, (uint32_t)v);
+        parent[v] = r;
+        uint32_t sz = size[r];
+        xlo[v] = sz;
+        xhi[v] = sz;
+    }
+}
+
+int launch_cc_reach(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t* parent,
+                    uint32_t* size, uint32_t* xlo, uint32_t* xhi, int* err, cudaStream_t s) {
+    if (n == 0) return 0;
+    int b = blocks_for(n, 256);
+    k_uf_init<<<b, 256, 0, s>>>(parent, size, n);
+    k_uf_hook<<<blocks_for((size_t)n * 32, 256), 256, 0, s>>>(rp, col, n, parent, err);
+    k_uf_compress_count<<<b, 256, 0, s>>>(parent, size, n);
+    k_uf_reach<<<b, 256, 0, s>>>(parent, size, n, xlo, xhi);
+    note_launch(4);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ------------------------------------------------------------------ scan
+// Exclusive scan in tiles of SCAN_TILE: tile sums, a one-block scan of the
+// sums (chunked, any length), then each tile rescans with its offset.
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_total;
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += t;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t nw = blockDim.x >> 5;
+        uint32_t x = lane < nw ? s_warp[lane] : 0;
+        uint32_t xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= (uint32_t)o) xi += t;
+        }
+        if (lane < nw) s_warp[lane] = xi - x;
+        if (lane == nw - 1) s_total = xi;
+    }
+    __syncthreads();
+    uint32_t res = s_warp[wid] + incl - v;
+    *total = s_total;
+    __syncthreads();
+    return res;
+}
+
+__global__ void k_scan_tiles(const uint32_t* in, size_t count, uint32_t* tile_sum) {
+    size_t base = (size_t)blockIdx.x * SCAN_TILE + (size_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i)
+        if (base + i < count) s += in[base + i];
+    uint32_t tot;
+    block_exclusive_scan(s, &tot);
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(uint32_t* sums, size_t nt, uint32_t* total) {
+    __shared__ uint32_t s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (size_t c = 0; c < nt; c += SCAN_TILE) {
+        size_t base = c + (size_t)threadIdx.x * SCAN_ITEMS;
+        uint32_t v[SCAN_ITEMS], s = 0;
+#pragma unroll
+        for (int i = 0; i < SCAN_ITEMS; ++i) {
+            v[i] = (base + i < nt) ? sums[base + i] : 0;
+            s += v[i];
+        }
+        uint32_t tot;
+        uint32_t off = block_exclusive_scan(s, &tot) + s_carry;
+#pragma unroll
+        for (int i = 0; i < SCAN_ITEMS; ++i) {
+            if (base + i < nt) sums[base + i] = off;
+            off += v[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total) *total = s_carry;
+}
+
+__global__ void k_scan_apply(const uint32_t* in, uint32_t* out, size_t count, const uint32_t* tile_off) {
+    size_t base = (size_t)blockIdx.x * SCAN_TILE + (size_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t v[SCAN_ITEMS], s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        v[i] = (base + i < count) ? in[base + i] : 0;
+        s += v[i];
+    }
+    uint32_t tot;
+    uint32_t off = block_exclusive_scan(s, &tot) + tile_off[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        if (base + i < count) out[base + i] = off;
+        off += v[i];
+    }
+}
+
+size_t scan_scratch_bytes(size_t count) {
+    size_t nt = (count + SCAN_TILE - 1) / SCAN_TILE;
+    return ((nt + 1) * sizeof(uint32_t) + 255) & ~(size_t)255;
+}
+
+int exclusive_scan_u32(const uint32_t* in, uint32_t* out, size_t count, uint32_t* total_dev,
+                       void* scratch, cudaStream_t s) {
+    if (count == 0) {
+        if (total_dev) cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), s);
+        return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    }
+    size_t nt = (count + SCAN_TILE - 1) / SCAN_TILE;
+    uint32_t* sums = (uint32_t*)scratch;
+    k_scan_tiles<<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, count, sums);
+    k_scan_sums<<<1, SCAN_THREADS, 0, s>>>(sums, nt, total_dev);
+    k_scan_apply<<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, out, count, sums);
+    note_launch(3);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ------------------------------------------------------------ radix sort
+// Stable LSD radix sort, 8-bit digits, tiles of RADIX_TILE elements.  Per
+// pass: per-tile digit histograms (digit-major), one exclusive scan, then a
+// stable scatter in which element order inside a tile is (round, warp, lane).
+constexpr int RADIX_THREADS = 256;
+constexpr int RADIX_ITEMS = 8;
+constexpr int RADIX_TILE = RADIX_THREADS * RADIX_ITEMS;
+
+template <typename K>
+__global__ void k_radix_hist(const K* keys, size_t count, int shift, uint32_t* hist, uint32_t ntiles) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    size_t base = (size_t)blockIdx.x * RADIX_TILE;
+#pragma unroll
+    for (int r = 0; r < RADIX_ITEMS; ++r) {
+        size_t i = base + (size_t)r * RADIX_THREADS + threadIdx.x;
+        if (i < count) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+template <typename K, bool HAS_V>
+__global__ void k_radix_scatter(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, size_t count,
+                                int shift, const uint32_t* offs, uint32_t ntiles) {
+    __shared__ uint32_t s_run[256];
+    __shared__ uint32_t s_w[RADIX_THREADS / 32][256];
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    s_run[threadIdx.x] = offs[(size_t)threadIdx.x * ntiles + blockIdx.x];
+    size_t base = (size_t)blockIdx.x * RADIX_TILE;
+    for (int r = 0; r < RADIX_ITEMS; ++r) {
+        for (int w = 0; w < RADIX_THREADS / 32; ++w) s_w[w][threadIdx.x] = 0;
+        __syncthreads();
+        size_t i = base + (size_t)r * RADIX_THREADS + threadIdx.x;
+        bool valid = i < count;
+        K key = valid ? kin[i] : (K)0;
+        uint32_t val = (HAS_V && valid) ? vin[i] : 0u;
+        uint32_t dg = valid ? ((uint32_t)(key >> shift) & 255u) : 256u;
+        uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        uint32_t rank = __popc(peers & lanemask_lt());
+        if (valid && rank == 0) s_w[wid][dg] = __popc(peers);
+        __syncthreads();
+        {   // per digit: prefix over warps, then advance the running offset
+            uint32_t d = threadIdx.x, run = s_run[d];
+            for (int w = 0; w < RADIX_THREADS / 32; ++w) {
+                uint32_t c = s_w[w][d];
+                s_w[w][d] = run;
+                run += c;
+            }
+            s_run[d] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = s_w[wid][dg] + rank;
+            kout[pos] = key;
+            if (HAS_V) vout[pos] = val;
+        }
+        __syncthreads();
+    }
+}
+
+size_t radix_scratch_bytes(size_t count) {
+    size_t nt = (count + RADIX_TILE - 1) / RADIX_TILE;
+    if (nt == 0) nt = 1;
+    return 256 * nt * sizeof(uint32_t) + scan_scratch_bytes(256 * nt) + 256;
+}
+
+template <typename K, bool HAS_V>
+static int radix_sort_impl(K* keys, uint32_t* vals, K* ktmp, uint32_t* vtmp, size_t count, int bits,
+                           void* scratch, cudaStream_t s, bool* in_tmp) {
+    *in_tmp = false;
+    if (count <= 1 || bits <= 0) return 0;
+    uint32_t ntiles = (uint32_t)((count + RADIX_TILE - 1) / RADIX_TILE);
+    uint32_t* hist = (uint32_t*)scratch;
+    void* scan_scr = (char*)scratch + ((256 * (size_t)ntiles * sizeof(uint32_t) + 255) & ~(size_t)255);
+    K* ka = keys; K* kb = ktmp;
+    uint32_t* va = vals; uint32_t* vb = vtmp;
+    for (int shift = 0; shift < bits; shift += 8) {
+        k_radix_hist<K><<<ntiles, RADIX_THREADS, 0, s>>>(ka, count, shift, hist, ntiles);
+        note_launch();
+        if (exclusive_scan_u32(hist, hist, 256 * (size_t)ntiles, nullptr, scan_scr, s)) return -1;
+        k_radix_scatter<K, HAS_V><<<ntiles, RADIX_THREADS, 0, s>>>(ka, va, kb, vb, count, shift, hist, ntiles);
+        note_launch();
+        K* t = ka; ka = kb; kb = t;
+        uint32_t* tv = va; va = vb; vb = tv;
+        *in_tmp = !*in_tmp;
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int radix_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
+                         size_t count, int bits, void* scratch, cudaStream_t s, bool* result_in_tmp) {
+    return radix_sort_impl<uint32_t, true>(keys, vals, keys_tmp, vals_tmp, count, bits, scratch, s,
+                                           result_in_tmp);
+}
+
+int radix_sort_u64(uint64_t* keys, uint64_t* keys_tmp, size_t count, int bits, void* scratch,
+                   cudaStream_t s, bool* result_in_tmp) {
+    return radix_sort_impl<uint64_t, false>((uint64_t*)keys, nullptr, (uint64_t*)keys_tmp, nullptr,
+                                            count, bits, scratch, s, result_in_tmp);
+}
+
+// ---------------------------------------------------------- degree order
+__global__ void k_max_degree(const uint32_t* rp, uint32_t n, uint32_t* out) {
+    uint32_t best = 0;
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += stride) {
+        uint32_t d = rp[v + 1] - rp[v];
+        best = d > best ? d : best;
+    }
+    for (int o = 16; o; o >>= 1) {
+        uint32_t t = __shfl_xor_sync(0xffffffffu, best, o);
+        best = t > best ? t : best;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(out, best);
+}
+
+__global__ void k_degree_keys(const uint32_t* rp, uint32_t n, const uint32_t* maxdeg, uint32_t* keys,
+                              uint32_t* vals) {
+    uint32_t md = *maxdeg;
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += stride) {
+        keys[v] = md - (rp[v + 1] - rp[v]);   // larger degree -> smaller key
+        vals[v] = (uint32_t)v;                 // ids ascending: ties keep id order
+    }
+}
+
+size_t degree_order_scratch_bytes(uint32_t n) {
+    size_t a = ((size_t)n * sizeof(uint32_t) + 255) & ~(size_t)255;
+    return 3 * a + radix_scratch_bytes(n) + 256;
+}
+
+// order[] = vertices by (degree desc, id asc); degree = CSR row length.
+int launch_degree_order(const uint32_t* rp, uint32_t n, uint32_t* order, void* scratch,
+                        size_t scratch_bytes, cudaStream_t s) {
+    if (n == 0) return 0;
+    if (scratch_bytes < degree_order_scratch_bytes(n)) return -1;
+    size_t a = ((size_t)n * sizeof(uint32_t) + 255) & ~(size_t)255;
+    char* p = (char*)scratch;
+    uint32_t* keys = (uint32_t*)p;
+    uint32_t* ktmp = (uint32_t*)(p + a);
+    uint32_t* vtmp = (uint32_t*)(p + 2 * a);
+    uint32_t* d_max = (uint32_t*)(p + 3 * a);
+    void* rscr = p + 3 * a + 256;
+    cudaMemsetAsync(d_max, 0, sizeof(uint32_t), s);
+    k_max_degree<<<blocks_for(n, 256), 256, 0, s>>>(rp, n, d_max);
+    k_degree_keys<<<blocks_for(n, 256), 256, 0, s>>>(rp, n, d_max, keys, order);
+    note_launch(2);
+    uint32_t maxdeg = 0;
+    if (cudaMemcpyAsync(&maxdeg, d_max, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return -1;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+    int bits = 0;
+    while (bits < 32 && (maxdeg >> bits)) ++bits;
+    bool in_tmp = false;
+    if (radix_sort_pairs_u32(keys, order, ktmp, vtmp, n, bits, rscr, s, &in_tmp)) return -1;
+    if (in_tmp) cudaMemcpyAsync(order, vtmp, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace bcm

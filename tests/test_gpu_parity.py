@@ -1,0 +1,204 @@
+"""CUDA path vs the oracle, element by element, through the C-ABI.
+
+Integer outputs, so the bar is bit-exact: top-k ids, farness and reach; the
+farness/reach of every vertex; the processing order; r(v) or alpha/omega.
+Sizes here are ones the oracle finishes in seconds; full-size workloads are
+in test_gpu_fullsize.py.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+LANES = [64, 128, 256]
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    from paper_1507_01490_gb300 import _build, bcm
+    _build.build_cuda()
+    bcm.load()
+    return bcm
+
+
+def undirected_graphs(gen):
+    gs = [gen.path(9), gen.star(12), gen.cycle(11), gen.complete(7), gen.grid(5, 6), gen.empty(4),
+          gen.path(1), gen.path(2),
+          gen.disjoint_union(gen.cycle(5), gen.cycle(5), gen.empty(1), gen.cycle(5)),
+          gen.relabel(gen.cycle(12), seed=3), gen.relabel(gen.grid(4, 4), seed=5),
+          gen.ba(200, 2, seed=11), gen.grid_lcc(12, 12, 0.1, seed=2),
+          gen.with_self_loops_and_repeats(gen.grid(4, 5), seed=1),
+          gen.star(300), gen.grid(17, 19)]
+    for s in range(6):
+        gs.append(gen.gnp(60 + 37 * s, 0.02 + 0.01 * (s % 4), seed=100 + s, directed=False))
+    gs.append(gen.chung_lu(3000, 6.0, 2.3, seed=4))
+    return gs
+
+
+def _partition(labels):
+    groups = {}
+    for v, c in enumerate(np.asarray(labels).tolist()):
+        groups.setdefault(c, []).append(v)
+    return sorted(tuple(x) for x in groups.values())
+
+
+def test_preprocess_order_and_reach(B, gen, orc):
+    for g in undirected_graphs(gen):
+        with B.BcmGraph.from_graph(g) as h:
+            order, lo, hi = h.preprocess()
+            comp, al, om, nc = h.scc_bounds()
+        assert np.array_equal(order, orc.order(g)), g.name
+        f, r = orc.farness_all(g)
+        assert np.array_equal(lo, r) and np.array_equal(hi, r), g.name
+        # undirected: the components are the SCCs of the symmetric digraph
+        assert _partition(comp) == _partition(orc.scc(g)[0]), g.name
+        assert nc == orc.scc(g)[1]
+        # labels are numbered in order of each component's smallest member
+        firsts = {}
+        for v, c in enumerate(comp.tolist()):
+            firsts.setdefault(c, v)
+        assert sorted(firsts, key=firsts.get) == list(range(nc)), g.name
+
+
+@pytest.mark.parametrize("lanes", LANES)
+def test_farness_all_small(B, gen, orc, lanes):
+    for g in undirected_graphs(gen):
+        f, r = orc.farness_all(g)
+        with B.BcmGraph.from_graph(g) as h:
+            gf, gr, st = h.farness_all(lanes=lanes)
+        assert np.array_equal(gf, f) and np.array_equal(gr, r), (g.name, lanes)
+
+
+@pytest.mark.parametrize("lanes,threads", [(64, 256), (64, 512), (128, 512), (256, 256), (256, 1024)])
+def test_topk_small(B, gen, orc, lanes, threads):
+    for g in undirected_graphs(gen):
+        f, r = orc.farness_all(g)
+        with B.BcmGraph.from_graph(g) as h:
+            for k in sorted({1, 2, 3, 10, 100, g.n, g.n + 4} - {0}):
+                ids, gf, gr, st = h.topk(k, lanes=lanes, threads=threads)
+                exp = orc.topk(f, r, k)
+                assert np.array_equal(ids, exp), (g.name, k, lanes)
+                assert np.array_equal(gf, f[exp]) and np.array_equal(gr, r[exp]), (g.name, k)
+                assert st["completed"] + st["cut"] == g.n, (g.name, k, st)
+
+
+def test_topk_without_seed_and_footnote(B, gen, orc):
+    for g in undirected_graphs(gen)[::3]:
+        f, r = orc.farness_all(g)
+        with B.BcmGraph.from_graph(g) as h:
+            for k in (1, 5, 40):
+                for flags in (B.BCM_NO_SEED, B.BCM_NO_FOOTNOTE, B.BCM_NO_SEED | B.BCM_NO_FOOTNOTE):
+                    ids, gf, gr, st = h.topk(k, flags=flags)
+                    assert np.array_equal(ids, orc.topk(f, r, k)), (g.name, k, flags)
+
+
+def test_plain_equals_oracle_bcm(B, gen, orc):
+    """One source per launch follows the oracle's Algorithm 1 step for step:
+    same top-k and the same arcs scanned, completions and cuts."""
+    for g in undirected_graphs(gen)[:14] + [gen.ba(400, 3, seed=5)]:
+        with B.BcmGraph.from_graph(g) as h:
+            for k in (1, 3, 10):
+                ids, gf, gr, st = h.topk(k, flags=B.BCM_PLAIN)
+                oi, of, orr, ost = orc.bcm(g, k, early_test=True)
+                assert np.array_equal(ids, oi) and np.array_equal(gf, of) and np.array_equal(gr, orr), (g.name, k)
+                assert st["m_vis"] == ost["m_vis"], (g.name, k, st["m_vis"], ost["m_vis"])
+                assert st["completed"] == ost["completed"] and st["cut"] == ost["cut"], (g.name, k)
+
+
+@pytest.mark.parametrize("k", [1, 10, 100])
+def test_workload_ba2000(B, gen, orc, k):
+    g = gen.workload("ba2000")
+    f, r = orc.farness_all(g)
+    exp = orc.topk(f, r, k)
+    with B.BcmGraph.from_graph(g) as h:
+        for lanes in LANES:
+            ids, gf, gr, st = h.topk(k, lanes=lanes)
+            assert np.array_equal(ids, exp) and np.array_equal(gf, f[exp]) and np.array_equal(gr, r[exp])
+        if k <= 10:
+            ids, gf, gr, st = h.topk(k, flags=B.BCM_PLAIN)
+            assert np.array_equal(ids, exp)
+            assert st["m_vis"] == orc.bcm(g, k)[3]["m_vis"]
+        gf, gr, _ = h.farness_all()
+        assert np.array_equal(gf, f) and np.array_equal(gr, r)
+
+
+@pytest.mark.parametrize("lanes", LANES)
+def test_chunglu_16k(B, gen, orc, lanes):
+    g = gen.chung_lu(1 << 14, 10.0, 2.3, seed=2)
+    f, r = orc.farness_all(g)
+    with B.BcmGraph.from_graph(g) as h:
+        for k in (1, 10, 100):
+            ids, gf, gr, st = h.topk(k, lanes=lanes)
+            exp = orc.topk(f, r, k)
+            assert np.array_equal(ids, exp) and np.array_equal(gf, f[exp]) and np.array_equal(gr, r[exp])
+        gf, gr, _ = h.farness_all(lanes=lanes)
+        assert np.array_equal(gf, f) and np.array_equal(gr, r)
+
+
+def test_device_outputs(B, gen, orc):
+    import torch
+    g = gen.grid_lcc(40, 40, 0.05, seed=9)
+    f, r = orc.farness_all(g)
+    exp = orc.topk(f, r, 7)
+    rp = torch.from_numpy(g.row_ptr.view(np.int64)).cuda()
+    col = torch.from_numpy(g.col.view(np.int32)).cuda()
+    h = B.bcm_graph_create(rp, col, g.n, g.m, False, ptr_on_device=True)
+    try:
+        ids = torch.zeros(7, dtype=torch.int32, device="cuda")
+        far = torch.zeros(7, dtype=torch.int64, device="cuda")
+        reach = torch.zeros(7, dtype=torch.int32, device="cuda")
+        B.bcm_topk(h, 7, B.make_options(flags=B.BCM_OUT_DEVICE), ids, far, reach)
+        assert ids.cpu().numpy().view(np.uint32).tolist() == exp.tolist()
+        assert far.cpu().numpy().view(np.uint64).tolist() == f[exp].tolist()
+        fa = torch.zeros(g.n, dtype=torch.int64, device="cuda")
+        ra = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+        B.bcm_farness_all(h, B.make_options(flags=B.BCM_OUT_DEVICE), fa, ra)
+        assert np.array_equal(fa.cpu().numpy().view(np.uint64), f)
+        assert np.array_equal(ra.cpu().numpy().view(np.uint32), r)
+    finally:
+        B.bcm_graph_destroy(h)
+
+
+def test_errors(B, gen):
+    g = gen.path(5)
+    with B.BcmGraph.from_graph(g) as h:
+        for bad in (dict(k=0), dict(k=1025)):
+            with pytest.raises(B.BcmError) as ei:
+                h.topk(**bad)
+            assert ei.value.status == B.BCM_ERR_INVALID
+        with pytest.raises(B.BcmError) as ei:
+            h.topk(1, lanes=32)
+        assert ei.value.status == B.BCM_ERR_UNSUPPORTED
+        with pytest.raises(B.BcmError) as ei:
+            h.topk(1, lanes=256, threads=128)
+        assert ei.value.status == B.BCM_ERR_UNSUPPORTED
+    bad_rp = np.array([0, 2, 1, 3], np.uint64)
+    with pytest.raises(B.BcmError) as ei:
+        B.BcmGraph(bad_rp, np.array([1, 2, 0], np.uint32), 3, False)
+    assert ei.value.status == B.BCM_ERR_INVALID
+    with pytest.raises(B.BcmError) as ei:
+        B.BcmGraph(np.array([0, 1, 1], np.uint64), np.array([5], np.uint32), 2, False)
+    assert ei.value.status == B.BCM_ERR_INVALID
+    # an undirected graph whose arc 0->1 has no partner
+    with pytest.raises(B.BcmError) as ei:
+        B.BcmGraph(np.array([0, 1, 1], np.uint64), np.array([1], np.uint32), 2, False,
+                   flags=B.BCM_CHECK_SYMMETRIC)
+    assert ei.value.status == B.BCM_ERR_NOT_SYMMETRIC
+    with B.BcmGraph.from_graph(gen.grid(3, 3), flags=B.BCM_CHECK_SYMMETRIC) as h:
+        assert h.topk(1)[0].tolist() == [4]
+
+
+def test_repeated_runs_reuse_clean_workspace(B, gen, orc):
+    g = gen.ba(500, 3, seed=21)
+    f, r = orc.farness_all(g)
+    with B.BcmGraph.from_graph(g) as h:
+        for it in range(4):
+            for k in (1, 17):
+                ids, gf, gr, st = h.topk(k, lanes=LANES[it % 3])
+                assert np.array_equal(ids, orc.topk(f, r, k))
+            gf, gr, _ = h.farness_all(lanes=LANES[(it + 1) % 3])
+            assert np.array_equal(gf, f)

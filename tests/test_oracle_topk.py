@@ -55,3 +55,12 @@ def test_vertex_transitive_all_tied(orc, gen, g_name):
 def test_k_zero_and_empty(orc):
     assert orc.topk(np.zeros(0, np.uint64), np.zeros(0, np.uint32), 4).size == 0
     assert orc.topk(np.array([3], np.uint64), np.array([2], np.uint32), 0).size == 0
+
+
+def test_processing_order(orc, gen):
+    g = gen.star(6)
+    assert orc.order(g).tolist() == [0, 1, 2, 3, 4, 5]
+    g = gen.path(5)          # degrees 1,2,2,2,1
+    assert orc.order(g).tolist() == [1, 2, 3, 0, 4]
+    g = gen.disjoint_union(gen.path(2), gen.star(4), gen.empty(1))   # degrees 1,1,3,1,1,1,0
+    assert orc.order(g).tolist() == [2, 0, 1, 3, 4, 5, 6]
