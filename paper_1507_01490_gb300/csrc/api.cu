@@ -49,25 +49,45 @@ static bcm_status cuda_fail(cudaError_t e, const char* what) {
 // The slot region of the wave kernels is large (36 n W bytes per CTA) and
 // must start zeroed; every successful run leaves it zeroed again.  Clean
 // regions are kept here for reuse instead of being freed and re-zeroed.
-struct Region { int dev; void* ptr; size_t bytes; };
+// A region is only known to be zero under the slot layout it was last used
+// with (vertex count, words per vertex, CTA count): frontier lists and logs
+// of one layout overlap the bit arrays of another.
+struct Layout {
+    uint32_t n = 0, W = 0, blocks = 0;
+    bool operator==(const Layout& o) const { return n == o.n && W == o.W && blocks == o.blocks; }
+};
+struct Region { int dev; void* ptr; size_t bytes; Layout layout; };
 static std::mutex g_region_mu;
 static std::vector<Region> g_regions;
+static size_t g_cached_bytes = 0;
+static const size_t kCacheCap = 96ull << 30;   // clean regions kept for reuse, at most
 
-static bcm_status region_acquire(size_t bytes, cudaStream_t s, Region* out) {
+static bcm_status region_acquire(size_t bytes, const Layout& lay, cudaStream_t s, Region* out) {
     int dev = 0;
     cudaGetDevice(&dev);
     {
         std::lock_guard<std::mutex> lk(g_region_mu);
         int best = -1;
-        for (size_t i = 0; i < g_regions.size(); ++i)
-            if (g_regions[i].dev == dev && g_regions[i].bytes >= bytes &&
-                (best < 0 || g_regions[i].bytes < g_regions[best].bytes))
+        for (size_t i = 0; i < g_regions.size(); ++i) {
+            const Region& r = g_regions[i];
+            if (r.dev != dev || r.bytes < bytes) continue;
+            // prefer a region already zero under this layout, then the smallest
+            if (best < 0 || (r.layout == lay && !(g_regions[best].layout == lay)) ||
+                ((r.layout == lay) == (g_regions[best].layout == lay) && r.bytes < g_regions[best].bytes))
                 best = (int)i;
+        }
         if (best >= 0) {
             *out = g_regions[best];
+            g_cached_bytes -= g_regions[best].bytes;
             g_regions.erase(g_regions.begin() + best);
-            return BCM_OK;
         }
+    }
+    if (out->ptr) {
+        if (!(out->layout == lay)) {
+            CU(cudaMemsetAsync(out->ptr, 0, out->bytes, s), "workspace clear");
+            out->layout = lay;
+        }
+        return BCM_OK;
     }
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, bytes);
@@ -77,8 +97,13 @@ static bcm_status region_acquire(size_t bytes, cudaStream_t s, Region* out) {
         {
             std::lock_guard<std::mutex> lk(g_region_mu);
             for (size_t i = 0; i < g_regions.size();)
-                if (g_regions[i].dev == dev) { drop.push_back(g_regions[i]); g_regions.erase(g_regions.begin() + i); }
-                else ++i;
+                if (g_regions[i].dev == dev) {
+                    drop.push_back(g_regions[i]);
+                    g_cached_bytes -= g_regions[i].bytes;
+                    g_regions.erase(g_regions.begin() + i);
+                } else {
+                    ++i;
+                }
         }
         cudaGetLastError();
         for (auto& r : drop) cudaFree(r.ptr);
@@ -86,20 +111,25 @@ static bcm_status region_acquire(size_t bytes, cudaStream_t s, Region* out) {
         if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
     }
     CU(cudaMemsetAsync(p, 0, bytes, s), "workspace clear");
-    *out = Region{dev, p, bytes};
+    *out = Region{dev, p, bytes, lay};
     return BCM_OK;
 }
 
 static void region_release(Region& r, bool clean) {
     if (!r.ptr) return;
+    bool kept = false;
     if (clean) {
         std::lock_guard<std::mutex> lk(g_region_mu);
-        g_regions.push_back(r);
-    } else {
-        cudaFree(r.ptr);
+        if (g_cached_bytes + r.bytes <= kCacheCap) {
+            g_regions.push_back(r);
+            g_cached_bytes += r.bytes;
+            kept = true;
+        }
     }
+    if (!kept) cudaFree(r.ptr);
     r.ptr = nullptr;
     r.bytes = 0;
+    r.layout = Layout{};
 }
 
 // Small per-run state of the wave kernels (all zeroed before a run).
@@ -141,7 +171,7 @@ struct bcm_graph {
     uint32_t* d_plain = nullptr;   // stamps [n], two vertex queues [2n]
     unsigned long long* d_far = nullptr;   // exhaustive outputs [n]
     uint32_t* d_reach = nullptr;
-    Region slots{0, nullptr, 0};
+    Region slots{0, nullptr, 0, Layout{}};
     int sms = 0;
 };
 
@@ -179,10 +209,15 @@ bcm_status resolve(bcm_graph* g, const bcm_options* opt, Cfg* c) {
     return BCM_OK;
 }
 
-size_t region_bytes(bcm_graph* g, const Cfg& c) {
-    size_t a = (size_t)c.blocks * slot_bytes(g->n, c.W);
-    size_t b = slot_bytes(g->n, 4);
-    return a > b ? a : b;
+// CTA slots first, then one slot (4 words per vertex) for the seed wave.
+size_t cta_region_bytes(bcm_graph* g, const Cfg& c) { return (size_t)c.blocks * slot_bytes(g->n, c.W); }
+size_t region_bytes(bcm_graph* g, const Cfg& c) { return cta_region_bytes(g, c) + slot_bytes(g->n, 4); }
+Layout region_layout(bcm_graph* g, const Cfg& c) {
+    Layout l;
+    l.n = g->n;
+    l.W = (uint32_t)c.W;
+    l.blocks = (uint32_t)c.blocks;
+    return l;
 }
 
 bcm_status ensure_aux(bcm_graph* g) {
@@ -191,10 +226,18 @@ bcm_status ensure_aux(bcm_graph* g) {
     return BCM_OK;
 }
 
-bcm_status ensure_slots(bcm_graph* g, size_t bytes) {
-    if (g->slots.ptr && g->slots.bytes >= bytes) return BCM_OK;
+bcm_status ensure_slots(bcm_graph* g, const Cfg& c) {
+    size_t bytes = region_bytes(g, c);
+    Layout lay = region_layout(g, c);
+    if (g->slots.ptr && g->slots.bytes >= bytes) {
+        if (!(g->slots.layout == lay)) {
+            CU(cudaMemsetAsync(g->slots.ptr, 0, g->slots.bytes, g->stream), "workspace clear");
+            g->slots.layout = lay;
+        }
+        return BCM_OK;
+    }
     region_release(g->slots, true);
-    return region_acquire(bytes, g->stream, &g->slots);
+    return region_acquire(bytes, lay, g->stream, &g->slots);
 }
 
 bcm_status check_dev_err(int err) {
@@ -312,6 +355,7 @@ WaveParams base_params(bcm_graph* g, const Cfg& c) {
     p.topk.thr = &a->thr;
     p.slot_base = (char*)g->slots.ptr;
     p.slot_stride = slot_bytes(g->n, c.W);
+    p.seed_base = (char*)g->slots.ptr + cta_region_bytes(g, c);
     p.stats = a->stats;
     p.err = &a->err;
     p.lock_limit_ns = c.limit_ns;
@@ -350,7 +394,7 @@ bcm_status run_waves(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, un
     if (st) return st;
     const bool plain = !exhaustive && (c.flags & BCM_PLAIN);
     if (!plain) {
-        st = ensure_slots(g, region_bytes(g, c));
+        st = ensure_slots(g, c);
         if (st) return st;
     }
     CU(cudaMemsetAsync(g->d_aux, 0, sizeof(Aux), s), "aux clear");

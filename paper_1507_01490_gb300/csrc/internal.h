@@ -53,8 +53,9 @@ struct WaveParams {
     TopK topk;
     unsigned long long* out_far;   // exhaustive outputs, indexed by vertex id
     uint32_t* out_reach;
-    char* slot_base;
+    char* slot_base;         // CTA i: slot_base + i * slot_stride
     size_t slot_stride;
+    char* seed_base;         // the seed wave's own slot (4 words per vertex)
     unsigned long long* stats;   // [ST_COUNT]
     int* err;
     unsigned long long lock_limit_ns;

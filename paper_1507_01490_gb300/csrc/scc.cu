@@ -1,17 +1,504 @@
-// Strongly connected components, the weighted SCC DAG and the alpha/omega
-// bounds of Section 2.3 (directed graphs).
+// Strongly connected components, the weighted SCC DAG (Section 1.3) and the
+// alpha/omega bounds on r(v) (Section 2.3) for directed graphs.
+//
+// SCCs:  (1) trimming: a vertex with no remaining in- or out-neighbour is an
+//        SCC by itself; (2) forward and backward reachability from a pivot of
+//        large in*out degree: their intersection is the pivot's SCC (this
+//        takes the giant SCC of a power-law digraph in one step); (3) for
+//        what is left, max-label colouring: every vertex takes the largest id
+//        that reaches it, then a backward search from each vertex that kept
+//        its own id, restricted to its colour, collects that vertex's SCC.
+// DAG:   arcs (C(u), C(w)) with C(u) != C(w), sorted and made unique.
+// Bounds: sinks first (Kahn on the reversed DAG); a component is evaluated
+//        once all its successors are, with
+//           alpha(C) = w(C) + max over arcs (C,D) of alpha(D)
+//           omega(C) = min(n, w(C) + sum over arcs (C,D) of omega(D)).
+#include <cstdio>
 #include <cuda_runtime.h>
 
 #include "internal.h"
 
 namespace bcm {
 
-size_t scc_scratch_bytes(uint32_t n, uint64_t m) { return 1024; }
+static constexpr uint32_t UNSET = 0xffffffffu;
+
+static inline unsigned grid_for(size_t work, int threads = 256) {
+    size_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152 * 32) b = 152 * 32;
+    return (unsigned)b;
+}
+
+#define GRID_STRIDE(i, n) \
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (n); i += (size_t)gridDim.x * blockDim.x)
+
+#define WARP_PER_ITEM(u, n)                                                      \
+    const uint32_t lane_ = threadIdx.x & 31;                                     \
+    for (size_t u = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5; u < (n); \
+         u += ((size_t)gridDim.x * blockDim.x) >> 5)
+
+__global__ void k_count_in(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t* indeg) {
+    WARP_PER_ITEM(u, n) {
+        for (uint32_t e = rp[u] + lane_; e < rp[u + 1]; e += 32) atomicAdd(&indeg[col[e]], 1u);
+    }
+}
+
+__global__ void k_fill_rev(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t* cursor, uint32_t* rcol) {
+    WARP_PER_ITEM(u, n) {
+        for (uint32_t e = rp[u] + lane_; e < rp[u + 1]; e += 32) rcol[atomicAdd(&cursor[col[e]], 1u)] = (uint32_t)u;
+    }
+}
+
+__global__ void k_set_last(uint32_t* a, uint32_t idx, uint32_t v) { a[idx] = v; }
+
+__global__ void k_fill(uint32_t* a, size_t n, uint32_t v) {
+    GRID_STRIDE(i, n) a[i] = v;
+}
+
+// (1) trimming
+__global__ void k_trim(const uint32_t* rp, const uint32_t* col, const uint32_t* rrp, const uint32_t* rcol,
+                       uint32_t n, uint32_t* scc, uint32_t* changed) {
+    GRID_STRIDE(v, n) {
+        if (vload(&scc[v]) != UNSET) continue;
+        bool out = false, in = false;
+        for (uint32_t e = rp[v]; e < rp[v + 1] && !out; ++e) {
+            uint32_t w = col[e];
+            out = (w != v) && vload(&scc[w]) == UNSET;
+        }
+        if (out)
+            for (uint32_t e = rrp[v]; e < rrp[v + 1] && !in; ++e) {
+                uint32_t w = rcol[e];
+                in = (w != v) && vload(&scc[w]) == UNSET;
+            }
+        if (!out || !in) {
+            scc[v] = (uint32_t)v;
+            *changed = 1;
+        }
+    }
+}
+
+__global__ void k_pivot(const uint32_t* rp, const uint32_t* rrp, uint32_t n, const uint32_t* scc,
+                        unsigned long long* best) {
+    GRID_STRIDE(v, n) {
+        if (scc[v] != UNSET) continue;
+        unsigned long long p = (unsigned long long)(rp[v + 1] - rp[v]) * (rrp[v + 1] - rrp[v]);
+        if (p > 0xffffffffull) p = 0xffffffffull;
+        atomicMax(best, (p << 32) | (0xffffffffull - v));
+    }
+}
+
+__global__ void k_seed_mark(uint32_t v, uint32_t* mark, uint32_t* list, uint32_t* cnt) {
+    mark[v] = 1;
+    list[0] = v;
+    *cnt = 1;
+}
+
+// one BFS level over unassigned vertices; same_color restricts to color[w] == color[u]
+__global__ void k_reach(const uint32_t* rp, const uint32_t* col, const uint32_t* front, const uint32_t* fcnt,
+                        uint32_t* next, uint32_t* ncnt, uint32_t* mark, const uint32_t* scc, const uint32_t* color,
+                        int same_color) {
+    const uint32_t cnt = *fcnt;
+    WARP_PER_ITEM(i, cnt) {
+        uint32_t u = front[i];
+        uint32_t cu = same_color ? color[u] : 0;
+        for (uint32_t e0 = rp[u]; e0 < rp[u + 1]; e0 += 32) {
+            uint32_t e = e0 + lane_;
+            bool app = false;
+            uint32_t w = 0;
+            if (e < rp[u + 1]) {
+                w = col[e];
+                if (scc[w] == UNSET && (!same_color || color[w] == cu) && vload(&mark[w]) == 0 &&
+                    atomicExch(&mark[w], 1u) == 0)
+                    app = true;
+            }
+            warp_append(app, w, next, ncnt);
+        }
+    }
+}
+
+__global__ void k_assign_both(uint32_t n, const uint32_t* fw, const uint32_t* bw, uint32_t* scc, uint32_t rep) {
+    GRID_STRIDE(v, n) if (scc[v] == UNSET && fw[v] && bw[v]) scc[v] = rep;
+}
+
+// (3) colouring
+__global__ void k_color_init(uint32_t n, const uint32_t* scc, uint32_t* color) {
+    GRID_STRIDE(v, n) color[v] = (scc[v] == UNSET) ? (uint32_t)v : 0u;
+}
+
+__global__ void k_color_prop(const uint32_t* rp, const uint32_t* col, uint32_t n, const uint32_t* scc, uint32_t* color,
+                             uint32_t* changed) {
+    WARP_PER_ITEM(u, n) {
+        if (scc[u] != UNSET) continue;
+        uint32_t c = vload(&color[u]);
+        for (uint32_t e = rp[u] + lane_; e < rp[u + 1]; e += 32) {
+            uint32_t w = col[e];
+            if (scc[w] == UNSET && vload(&color[w]) < c) {
+                atomicMax(&color[w], c);
+                *changed = 1;
+            }
+        }
+    }
+}
+
+__global__ void k_color_roots(uint32_t n, const uint32_t* scc, const uint32_t* color, uint32_t* mark, uint32_t* list,
+                              uint32_t* cnt) {
+    const uint32_t lane = threadIdx.x & 31;
+    for (size_t b = (blockIdx.x * (size_t)blockDim.x) + (threadIdx.x & ~31u); b < n;
+         b += (size_t)gridDim.x * blockDim.x) {
+        size_t v = b + lane;
+        bool root = v < n && scc[v] == UNSET && color[v] == (uint32_t)v;
+        if (root) mark[v] = 1;
+        warp_append(root, (uint32_t)v, list, cnt);
+    }
+}
+
+__global__ void k_assign_marked(uint32_t n, uint32_t* scc, const uint32_t* color, const uint32_t* mark,
+                                uint32_t* remaining) {
+    GRID_STRIDE(v, n) {
+        if (scc[v] != UNSET) continue;
+        if (mark[v]) scc[v] = color[v];
+        else atomicAdd(remaining, 1u);
+    }
+}
+
+__global__ void k_count_unset(uint32_t n, const uint32_t* scc, uint32_t* cnt) {
+    uint32_t c = 0;
+    GRID_STRIDE(v, n) c += scc[v] == UNSET;
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt, c);
+}
+
+// labels ordered by smallest member
+__global__ void k_minrep(uint32_t n, const uint32_t* scc, uint32_t* minv) {
+    GRID_STRIDE(v, n) atomicMin(&minv[scc[v]], (uint32_t)v);
+}
+
+__global__ void k_min_flags(uint32_t n, const uint32_t* scc, const uint32_t* minv, uint32_t* flags) {
+    GRID_STRIDE(v, n) flags[v] = minv[scc[v]] == (uint32_t)v ? 1u : 0u;
+}
+
+__global__ void k_label(uint32_t n, const uint32_t* scc, const uint32_t* minv, const uint32_t* rank, uint32_t* comp) {
+    GRID_STRIDE(v, n) comp[v] = rank[minv[scc[v]]];
+}
+
+// DAG
+__global__ void k_dag_keys(const uint32_t* rp, const uint32_t* col, uint32_t n, const uint32_t* comp, int b,
+                           unsigned long long* keys) {
+    WARP_PER_ITEM(u, n) {
+        uint32_t cu = comp[u];
+        for (uint32_t e = rp[u] + lane_; e < rp[u + 1]; e += 32) {
+            uint32_t cw = comp[col[e]];
+            keys[e] = (cu != cw) ? (((unsigned long long)cu << b) | cw) : ~0ull;
+        }
+    }
+}
+
+__global__ void k_unique_flags(const unsigned long long* keys, uint64_t m, uint32_t* flags) {
+    GRID_STRIDE(i, m) {
+        unsigned long long k = keys[i];
+        flags[i] = (k != ~0ull && (i == 0 || keys[i - 1] != k)) ? 1u : 0u;
+    }
+}
+
+__global__ void k_unique_scatter(const unsigned long long* keys, uint64_t m, const uint32_t* flags,
+                                 const uint32_t* pos, int b, uint32_t* dsrc, uint32_t* ddst) {
+    GRID_STRIDE(i, m) {
+        if (!flags[i]) continue;
+        unsigned long long k = keys[i];
+        dsrc[pos[i]] = (uint32_t)(k >> b);
+        ddst[pos[i]] = (uint32_t)(k & ((1ull << b) - 1));
+    }
+}
+
+__global__ void k_hist(const uint32_t* a, size_t cnt, uint32_t* h) {
+    GRID_STRIDE(i, cnt) atomicAdd(&h[a[i]], 1u);
+}
+
+__global__ void k_scatter_pred(const uint32_t* dsrc, const uint32_t* ddst, uint32_t nd, uint32_t* cursor,
+                               uint32_t* pred) {
+    GRID_STRIDE(i, nd) pred[atomicAdd(&cursor[ddst[i]], 1u)] = dsrc[i];
+}
+
+__global__ void k_sinks(uint32_t nc, const uint32_t* drp, uint32_t* outcnt, uint32_t* list, uint32_t* cnt) {
+    const uint32_t lane = threadIdx.x & 31;
+    for (size_t b = (blockIdx.x * (size_t)blockDim.x) + (threadIdx.x & ~31u); b < nc;
+         b += (size_t)gridDim.x * blockDim.x) {
+        size_t c = b + lane;
+        bool sink = false;
+        if (c < nc) {
+            uint32_t d = drp[c + 1] - drp[c];
+            outcnt[c] = d;
+            sink = d == 0;
+        }
+        warp_append(sink, (uint32_t)c, list, cnt);
+    }
+}
+
+__global__ void k_dp_eval(const uint32_t* front, const uint32_t* fcnt, const uint32_t* drp, const uint32_t* ddst,
+                          const uint32_t* wsz, uint32_t* A, uint32_t* Om, uint32_t n) {
+    const uint32_t cnt = *fcnt;
+    GRID_STRIDE(i, cnt) {
+        uint32_t c = front[i];
+        uint32_t amax = 0;
+        unsigned long long osum = 0;
+        for (uint32_t e = drp[c]; e < drp[c + 1]; ++e) {
+            uint32_t d = ddst[e];
+            uint32_t a = vload(&A[d]);
+            amax = a > amax ? a : amax;
+            osum += vload(&Om[d]);
+            if (osum > n) osum = n;
+        }
+        A[c] = wsz[c] + amax;
+        unsigned long long o = wsz[c] + osum;
+        Om[c] = (uint32_t)(o > n ? n : o);
+    }
+}
+
+__global__ void k_dp_release(const uint32_t* front, const uint32_t* fcnt, const uint32_t* prp, const uint32_t* pred,
+                             uint32_t* outcnt, uint32_t* next, uint32_t* ncnt) {
+    const uint32_t cnt = *fcnt;
+    WARP_PER_ITEM(i, cnt) {
+        uint32_t c = front[i];
+        for (uint32_t e0 = prp[c]; e0 < prp[c + 1]; e0 += 32) {
+            uint32_t e = e0 + lane_;
+            bool ready = false;
+            uint32_t p = 0;
+            if (e < prp[c + 1]) {
+                p = pred[e];
+                ready = atomicSub(&outcnt[p], 1u) == 1u;
+            }
+            warp_append(ready, p, next, ncnt);
+        }
+    }
+}
+
+__global__ void k_xbounds(uint32_t n, const uint32_t* comp, const uint32_t* A, const uint32_t* Om, uint32_t* xlo,
+                          uint32_t* xhi) {
+    GRID_STRIDE(v, n) {
+        xlo[v] = A[comp[v]];
+        xhi[v] = Om[comp[v]];
+    }
+}
+
+// ---------------------------------------------------------------- host
+static inline size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+
+size_t scc_scratch_bytes(uint32_t n, uint64_t m) {
+    size_t nb = al(((size_t)n + 1) * 4), mb = al((m ? m : 1) * 4), m8 = al((m ? m : 1) * 8);
+    size_t s = 0;
+    s += nb * 12;                 // rrp, cursor, color, fw, bw, lists x2, minv, flags, A, Om, wsz/outcnt
+    s += mb * 4;                  // rcol, dsrc, ddst, pred
+    s += m8 * 2;                  // keys, keys_tmp
+    s += al(scan_scratch_bytes((m > n ? m : n) + 1));
+    s += al(radix_scratch_bytes(m ? m : 1));
+    s += 4096;
+    return s;
+}
+
+namespace {
+struct Bump {
+    char* p; size_t left;
+    void* take(size_t b) {
+        b = al(b);
+        if (b > left) return nullptr;
+        void* r = p;
+        p += b;
+        left -= b;
+        return r;
+    }
+};
+
+int read_u32(const uint32_t* d, uint32_t* h, cudaStream_t s) {
+    if (cudaMemcpyAsync(h, d, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) return -1;
+    return cudaStreamSynchronize(s) == cudaSuccess ? 0 : -1;
+}
+}  // namespace
+
+#define LAUNCH(...)                                                  \
+    do {                                                             \
+        __VA_ARGS__;                                                 \
+        note_launch();                                               \
+        if (cudaGetLastError() != cudaSuccess) return -1;            \
+    } while (0)
 
 int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, uint32_t n, uint64_t m, uint32_t* comp,
                       uint32_t* xlo, uint32_t* xhi, uint32_t* n_scc_host, void* scratch, size_t scratch_bytes,
                       int* err, cudaStream_t s) {
-    return -2;
+    if (n == 0) { *n_scc_host = 0; return 0; }
+    Bump B{(char*)scratch, scratch_bytes};
+    uint32_t* rrp = (uint32_t*)B.take(((size_t)n + 1) * 4);
+    uint32_t* cursor = (uint32_t*)B.take(((size_t)n + 1) * 4);
+    uint32_t* rcol = (uint32_t*)B.take((m ? m : 1) * 4);
+    uint32_t* sccv = comp;        // representative per vertex until the final labels
+    uint32_t* color = (uint32_t*)B.take(((size_t)n + 1) * 4);
+    uint32_t* fw = (uint32_t*)B.take(((size_t)n + 1) * 4);
+    uint32_t* bw = (uint32_t*)B.take(((size_t)n + 1) * 4);
+    uint32_t* L0 = (uint32_t*)B.take(((size_t)n + 1) * 4);
+    uint32_t* L1 = (uint32_t*)B.take(((size_t)n + 1) * 4);
+    uint32_t* minv = (uint32_t*)B.take(((size_t)n + 1) * 4);
+    uint32_t* flags = (uint32_t*)B.take(((size_t)(m > n ? m : n) + 1) * 4);
+    uint32_t* cnts = (uint32_t*)B.take(256);     // [0] changed, [1],[2] list counts, [3] total, [4] remaining
+    unsigned long long* best = (unsigned long long*)B.take(64);
+    void* scan_scr = B.take(scan_scratch_bytes((m > n ? m : n) + 1));
+    if (!rrp || !cursor || !rcol || !color || !fw || !bw || !L0 || !L1 || !minv || !flags || !cnts || !best ||
+        !scan_scr)
+        return -1;
+    const unsigned gv = grid_for(n), gw = grid_for((size_t)n * 32);
+    (void)err;
+
+    // reverse CSR
+    cudaMemsetAsync(cursor, 0, ((size_t)n + 1) * 4, s);
+    LAUNCH(k_count_in<<<gw, 256, 0, s>>>(rp, col, n, cursor));
+    if (exclusive_scan_u32(cursor, rrp, n, &cnts[3], scan_scr, s)) return -1;
+    LAUNCH(k_set_last<<<1, 1, 0, s>>>(rrp, n, (uint32_t)m));
+    cudaMemcpyAsync(cursor, rrp, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
+    LAUNCH(k_fill_rev<<<gw, 256, 0, s>>>(rp, col, n, cursor, rcol));
+    LAUNCH(k_fill<<<gv, 256, 0, s>>>(sccv, n, UNSET));
+
+    uint32_t h = 0;
+    // (1) trimming, a few rounds
+    for (int round = 0; round < 8; ++round) {
+        cudaMemsetAsync(cnts, 0, 4, s);
+        LAUNCH(k_trim<<<gv, 256, 0, s>>>(rp, col, rrp, rcol, n, sccv, cnts));
+        if (read_u32(cnts, &h, s)) return -1;
+        if (!h) break;
+    }
+    // (2) forward-backward from the pivot
+    cudaMemsetAsync(best, 0, 8, s);
+    LAUNCH(k_pivot<<<gv, 256, 0, s>>>(rp, rrp, n, sccv, best));
+    unsigned long long hb = 0;
+    cudaMemcpyAsync(&hb, best, 8, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+    if (hb) {
+        uint32_t pivot = 0xffffffffu - (uint32_t)(hb & 0xffffffffull);
+        for (int dir = 0; dir < 2; ++dir) {
+            uint32_t* mark = dir ? bw : fw;
+            cudaMemsetAsync(mark, 0, (size_t)n * 4, s);
+            LAUNCH(k_seed_mark<<<1, 1, 0, s>>>(pivot, mark, L0, &cnts[1]));
+            uint32_t *cur = L0, *nxt = L1, *cc = &cnts[1], *nc = &cnts[2];
+            for (;;) {
+                cudaMemsetAsync(nc, 0, 4, s);
+                LAUNCH(k_reach<<<gw, 256, 0, s>>>(dir ? rrp : rp, dir ? rcol : col, cur, cc, nxt, nc, mark, sccv,
+                                                  color, 0));
+                if (read_u32(nc, &h, s)) return -1;
+                if (!h) break;
+                uint32_t* t = cur; cur = nxt; nxt = t;
+                uint32_t* tc = cc; cc = nc; nc = tc;
+            }
+        }
+        LAUNCH(k_assign_both<<<gv, 256, 0, s>>>(n, fw, bw, sccv, pivot));
+        for (int round = 0; round < 8; ++round) {
+            cudaMemsetAsync(cnts, 0, 4, s);
+            LAUNCH(k_trim<<<gv, 256, 0, s>>>(rp, col, rrp, rcol, n, sccv, cnts));
+            if (read_u32(cnts, &h, s)) return -1;
+            if (!h) break;
+        }
+    }
+    // (3) colouring until every vertex has an SCC
+    cudaMemsetAsync(&cnts[4], 0, 4, s);
+    LAUNCH(k_count_unset<<<gv, 256, 0, s>>>(n, sccv, &cnts[4]));
+    uint32_t remaining = 0;
+    if (read_u32(&cnts[4], &remaining, s)) return -1;
+    while (remaining) {
+        LAUNCH(k_color_init<<<gv, 256, 0, s>>>(n, sccv, color));
+        for (;;) {
+            cudaMemsetAsync(cnts, 0, 4, s);
+            LAUNCH(k_color_prop<<<gw, 256, 0, s>>>(rp, col, n, sccv, color, cnts));
+            if (read_u32(cnts, &h, s)) return -1;
+            if (!h) break;
+        }
+        cudaMemsetAsync(bw, 0, (size_t)n * 4, s);
+        cudaMemsetAsync(&cnts[1], 0, 8, s);
+        LAUNCH(k_color_roots<<<gv, 256, 0, s>>>(n, sccv, color, bw, L0, &cnts[1]));
+        uint32_t *cur = L0, *nxt = L1, *cc = &cnts[1], *nc = &cnts[2];
+        for (;;) {
+            cudaMemsetAsync(nc, 0, 4, s);
+            LAUNCH(k_reach<<<gw, 256, 0, s>>>(rrp, rcol, cur, cc, nxt, nc, bw, sccv, color, 1));
+            if (read_u32(nc, &h, s)) return -1;
+            if (!h) break;
+            uint32_t* t = cur; cur = nxt; nxt = t;
+            uint32_t* tc = cc; cc = nc; nc = tc;
+        }
+        cudaMemsetAsync(&cnts[4], 0, 4, s);
+        LAUNCH(k_assign_marked<<<gv, 256, 0, s>>>(n, sccv, color, bw, &cnts[4]));
+        if (read_u32(&cnts[4], &remaining, s)) return -1;
+    }
+    // labels by smallest member
+    LAUNCH(k_fill<<<gv, 256, 0, s>>>(minv, n, UNSET));
+    LAUNCH(k_minrep<<<gv, 256, 0, s>>>(n, sccv, minv));
+    LAUNCH(k_min_flags<<<gv, 256, 0, s>>>(n, sccv, minv, flags));
+    if (exclusive_scan_u32(flags, flags, n, &cnts[3], scan_scr, s)) return -1;
+    LAUNCH(k_label<<<gv, 256, 0, s>>>(n, sccv, minv, flags, color));   // labels into color
+    uint32_t nscc = 0;
+    if (read_u32(&cnts[3], &nscc, s)) return -1;
+    cudaMemcpyAsync(comp, color, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
+    *n_scc_host = nscc;
+
+    // DAG arcs, unique, sorted by (source, target)
+    int b = 1;
+    while ((1ull << b) < (unsigned long long)nscc) ++b;
+    uint32_t* wsz = minv;         // reuse
+    uint32_t* A = fw;
+    uint32_t* Om = bw;
+    uint32_t* outcnt = cursor;
+    uint32_t* drp = rrp;          // reverse CSR no longer needed
+    uint32_t* prp = L1;
+    uint32_t ndag = 0;
+    uint32_t* dsrc = nullptr;
+    uint32_t* ddst = nullptr;
+    uint32_t* pred = nullptr;
+    if (m) {
+        unsigned long long* keys = (unsigned long long*)B.take(m * 8);
+        unsigned long long* ktmp = (unsigned long long*)B.take(m * 8);
+        dsrc = (uint32_t*)B.take(m * 4);
+        ddst = (uint32_t*)B.take(m * 4);
+        pred = rcol;
+        void* rscr = B.take(radix_scratch_bytes(m));
+        if (!keys || !ktmp || !dsrc || !ddst || !rscr) return -1;
+        LAUNCH(k_dag_keys<<<gw, 256, 0, s>>>(rp, col, n, comp, b, keys));
+        bool in_tmp = false;
+        if (radix_sort_u64((uint64_t*)keys, (uint64_t*)ktmp, m, 2 * b, rscr, s, &in_tmp)) return -1;
+        unsigned long long* sk = in_tmp ? ktmp : keys;
+        LAUNCH(k_unique_flags<<<grid_for(m), 256, 0, s>>>(sk, m, flags));
+        uint32_t* pos = (uint32_t*)(in_tmp ? (void*)keys : (void*)ktmp);   // the other key buffer as scratch
+        if (exclusive_scan_u32(flags, pos, m, &cnts[3], scan_scr, s)) return -1;
+        LAUNCH(k_unique_scatter<<<grid_for(m), 256, 0, s>>>(sk, m, flags, pos, b, dsrc, ddst));
+        if (read_u32(&cnts[3], &ndag, s)) return -1;
+    }
+    // component sizes; DAG CSR (successors) and predecessor lists
+    cudaMemsetAsync(wsz, 0, ((size_t)nscc + 1) * 4, s);
+    LAUNCH(k_hist<<<gv, 256, 0, s>>>(comp, n, wsz));
+    cudaMemsetAsync(outcnt, 0, ((size_t)nscc + 1) * 4, s);
+    if (ndag) LAUNCH(k_hist<<<grid_for(ndag), 256, 0, s>>>(dsrc, ndag, outcnt));
+    if (exclusive_scan_u32(outcnt, drp, nscc, &cnts[3], scan_scr, s)) return -1;
+    LAUNCH(k_set_last<<<1, 1, 0, s>>>(drp, nscc, ndag));
+    cudaMemsetAsync(outcnt, 0, ((size_t)nscc + 1) * 4, s);
+    if (ndag) LAUNCH(k_hist<<<grid_for(ndag), 256, 0, s>>>(ddst, ndag, outcnt));
+    if (exclusive_scan_u32(outcnt, prp, nscc, &cnts[3], scan_scr, s)) return -1;
+    LAUNCH(k_set_last<<<1, 1, 0, s>>>(prp, nscc, ndag));
+    cudaMemcpyAsync(outcnt, prp, (size_t)nscc * 4, cudaMemcpyDeviceToDevice, s);
+    if (ndag) LAUNCH(k_scatter_pred<<<grid_for(ndag), 256, 0, s>>>(dsrc, ddst, ndag, outcnt, pred));
+    // alpha / omega, sinks first
+    uint32_t* F0 = L0;
+    uint32_t* F1 = color;         // labels were copied out to comp
+    cudaMemsetAsync(&cnts[1], 0, 8, s);
+    LAUNCH(k_sinks<<<grid_for(nscc), 256, 0, s>>>(nscc, drp, outcnt, F0, &cnts[1]));
+    uint32_t *cur = F0, *nxt = F1, *cc = &cnts[1], *nc = &cnts[2];
+    uint32_t fcount = 0;
+    if (read_u32(cc, &fcount, s)) return -1;
+    uint32_t done = 0;
+    while (fcount) {
+        done += fcount;
+        LAUNCH(k_dp_eval<<<grid_for(fcount), 256, 0, s>>>(cur, cc, drp, ddst, wsz, A, Om, n));
+        cudaMemsetAsync(nc, 0, 4, s);
+        LAUNCH(k_dp_release<<<grid_for((size_t)fcount * 32), 256, 0, s>>>(cur, cc, prp, pred, outcnt, nxt, nc));
+        if (read_u32(nc, &fcount, s)) return -1;
+        uint32_t* t = cur; cur = nxt; nxt = t;
+        uint32_t* tc = cc; cc = nc; nc = tc;
+    }
+    if (done != nscc) return -1;   // the DAG must be acyclic
+    LAUNCH(k_xbounds<<<gv, 256, 0, s>>>(n, comp, A, Om, xlo, xhi));
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace bcm
