@@ -1,0 +1,440 @@
+#!/usr/bin/env python3
+"""Benchmark: exact top-k closeness (BCM / BFSCut) on one GB300.
+
+Workload (default): the synthetic Chung-Lu power-law graph, n = 2^20, mean
+degree 10, degree exponent 2.3, seed 2 (~5.2M edges, 10.4M arcs), k = 10.
+A step is one whole pass of the hot path on that graph with the CSR already in
+HBM: create the handle from device memory, preprocess (connected components
+for r(v), degree order), BFSCut top-k, release.  The value is seconds per
+graph (lower is better); GTEPS = arcs scanned (m_vis) / step time.
+
+Also reported, on the same graph: the plain one-source-per-launch GPU
+BFSCut, per-k times for k in {1, 10, 100}, the end-to-end time through the
+C-ABI from pinned host buffers, the dominant kernel's roofline, the CPU
+oracle timed on a bounded sample, and a bit-exactness check of the result
+against the oracle on sampled outputs.
+
+--gpus N (under torchrun) runs N independent replicas, one per GPU: the
+method's sources could be sharded, but no cross-GPU exchange is built, so
+per-GPU work is fixed and scaling is weak.
+--impl reference times the CPU oracle (one BFS per source, all host cores)
+on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "top-k closeness s/graph & GTEPS, batched vs plain GPU BFSCut, bit-exact"
+UNIT = "s/graph"
+WORKLOADS = {
+    "chunglu1m": "Chung-Lu power-law graph, n=2^20, mean degree 10, degree exponent 2.3, seed 2, "
+                 "self-loops and repeats removed, undirected",
+    "rmat20": "R-MAT scale 20, edge factor 16, (0.57,0.19,0.19,0.05), seed 3, directed",
+    "grid2048": "2048x2048 grid, 5% of edges deleted (seed 4), largest component",
+    "ba2000": "Barabasi-Albert n=2000, m=3, seed 1",
+    "chunglu256k": "Chung-Lu power-law graph, n=2^18, mean degree 10, degree exponent 2.3, seed 2 "
+                   "(profiling-size case of the same recipe)",
+}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profile_traffic(kernel_src_hash):
+    """dram bytes per launch of the wave kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "k_wave_cta_chunglu1m.md")
+    if not os.path.exists(p):
+        return None
+    traffic, src = None, None
+    for line in open(p):
+        if line.startswith("traffic_bytes_per_launch:"):
+            traffic = float(line.split(":", 1)[1])
+        if line.startswith("kernel_source_sha256:"):
+            src = line.split(":", 1)[1].strip()
+    return traffic if (src == kernel_src_hash and traffic) else None
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("msbfs.cu", "common.cuh", "internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1507_01490_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def m_tot_undirected(g, reach):
+    """Arcs the textbook algorithm scans: every u is scanned by each of the
+    r(u) sources of its component (undirected graphs)."""
+    return int(np.sum(g.degrees().astype(np.int64) * reach.astype(np.int64)))
+
+
+# ------------------------------------------------------------------- oracle
+def cpu_sample(g, budget_s, seed=7):
+    """Oracle (exhaustive BFS, all host cores) on a growing sample of sources
+    until ~budget_s of work; returns (seconds per graph, sources, cores)."""
+    import oracle
+    from paper_1507_01490_gb300 import graphgen
+    cores = oracle.default_threads()
+    done, spent, size = 0, 0.0, max(cores * 4, 64)
+    while spent < budget_s and done < g.n:
+        cnt = min(size, g.n - done)
+        src = graphgen.uniform_u32(seed + done, cnt, g.n)
+        t = time.perf_counter()
+        oracle.farness_all(g, sources=src, threads=cores)
+        spent += time.perf_counter() - t
+        done += cnt
+        size = min(size * 2, 1 << 16)
+    return spent / done * g.n, done, cores
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_1507_01490_gb300 import graphgen
+    g = graphgen.workload(args.workload)
+    per_step = []
+    budget = args.ref_step_seconds
+    for i in range(args.warmup + args.steps):
+        s_per_graph, done, cores = cpu_sample(g, budget, seed=1000 + i)
+        if i >= args.warmup:
+            per_step.append(s_per_graph)
+    v = float(np.mean(per_step))
+    sample = "exhaustive BFS from %d-%d uniformly drawn sources of %d per step, scaled by n" % (
+        64, g.n, g.n)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "k": args.k},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "about %.0f s of CPU work per step: %s" % (budget, sample)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------- ours
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="chunglu1m", choices=sorted(WORKLOADS))
+    ap.add_argument("--k", type=int, default=10)
+    ap.add_argument("--lanes", type=int, default=0, help="0: library default")
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--blocks", type=int, default=0)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain one-source baseline")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-verify", action="store_true", help="skip the oracle check of the result")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer timing")
+    ap.add_argument("--no-perk", action="store_true", help="skip the per-k timings")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=8.0)
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1507_01490_gb300 import bcm as B, graphgen
+
+    g = graphgen.workload(args.workload)
+    k = args.k
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    rp_d = torch.from_numpy(g.row_ptr.view(np.int64)).to(dev)
+    col_d = torch.from_numpy(g.col.view(np.int32)).to(dev)
+    kk = min(k, g.n)
+    kbuf = min(max(k, 100), g.n)          # output rows for the largest k queried below
+    ids_d = torch.zeros(kbuf, dtype=torch.int32, device=dev)
+    far_d = torch.zeros(kbuf, dtype=torch.int64, device=dev)
+    reach_d = torch.zeros(kbuf, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB of L2
+    opts = B.make_options(lanes=args.lanes, threads=args.threads, blocks=args.blocks, flags=B.BCM_OUT_DEVICE)
+    torch.cuda.synchronize()
+
+    def step(kq=k, o=opts, stats=None):
+        h = B.bcm_graph_create(rp_d, col_d, g.n, g.m, g.directed, ptr_on_device=True,
+                               stream=stream.cuda_stream)
+        try:
+            assert min(kq, g.n) <= kbuf
+            B.bcm_topk(h, kq, o, ids_d, far_d, reach_d, stats)
+        finally:
+            B.bcm_graph_destroy(h)
+
+    def timed(fn, reps):
+        """per-step device time (CUDA events on the library's stream), L2 flushed before each"""
+        ts = []
+        for _ in range(reps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return ts
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = B.bcm_launch_count()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    step_times = timed(step, args.steps)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    launches = B.bcm_launch_count() - l0
+    clk = clocks.stop()
+    total = sum(step_times)
+    if dist:
+        t = torch.tensor([total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    s_per_graph = total / (args.steps * world)
+
+    # one more step with stats (outside the timed region)
+    st = B.bcm_stats()
+    step(stats=st)
+    st = st.as_dict()
+    got_ids = ids_d[:kk].cpu().numpy().view(np.uint32).copy()
+    got_far = far_d[:kk].cpu().numpy().view(np.uint64).copy()
+    got_reach = reach_d[:kk].cpu().numpy().view(np.uint32).copy()
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    # per-k times and the plain baseline
+    per_k = {}
+    for kq in ([] if args.no_perk else sorted({1, 10, 100} | {k})):
+        kq_opts = B.make_options(lanes=args.lanes, threads=args.threads, blocks=args.blocks,
+                                 flags=B.BCM_OUT_DEVICE)
+        ts = timed(lambda: step(kq, kq_opts), 3)
+        s2 = B.bcm_stats()
+        step(kq, kq_opts, s2)
+        per_k[str(kq)] = {"s_per_graph": float(np.median(ts)), "m_vis": s2.m_vis,
+                          "gteps": s2.m_vis / float(np.median(ts)) / 1e9}
+    # restore k's outputs for verification
+    step()
+    plain = None
+    if not args.no_plain:
+        popts = B.make_options(flags=B.BCM_OUT_DEVICE | B.BCM_PLAIN)
+        sp = B.bcm_stats()
+        tp = timed(lambda: step(k, popts, sp), 1)[0]
+        p_ids = ids_d[:kk].cpu().numpy().view(np.uint32).copy()
+        plain = {"s_per_graph": tp, "m_vis": sp.m_vis, "gteps": sp.m_vis / tp / 1e9,
+                 "launches": sp.launches, "same_result": bool(np.array_equal(p_ids, got_ids))}
+        step()
+
+    # e2e: through the C-ABI from pinned host memory, results back to host
+    rp_h = torch.from_numpy(g.row_ptr.view(np.int64)).pin_memory()
+    col_h = torch.from_numpy(g.col.view(np.int32)).pin_memory()
+    ids_h = torch.zeros(kk, dtype=torch.int32).pin_memory()
+    far_h = torch.zeros(kk, dtype=torch.int64).pin_memory()
+    reach_h = torch.zeros(kk, dtype=torch.int32).pin_memory()
+    hopts = B.make_options(lanes=args.lanes, threads=args.threads, blocks=args.blocks)
+
+    def e2e_step():
+        h = B.bcm_graph_create(rp_h.data_ptr(), col_h.data_ptr(), g.n, g.m, g.directed, ptr_on_device=False,
+                               stream=stream.cuda_stream)
+        try:
+            B.bcm_topk(h, k, hopts, ids_h.data_ptr(), far_h.data_ptr(), reach_h.data_ptr())
+        finally:
+            B.bcm_graph_destroy(h)
+
+    e2e_t = []
+    if not args.no_e2e:
+        e2e_step()
+    for _ in range(0 if args.no_e2e else max(3, min(args.steps, 10))):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        e2e_step()
+        e2e_t.append(time.perf_counter() - t)
+    e2e_v = float(np.mean(e2e_t)) if e2e_t else None
+    h2d = int(g.row_ptr.nbytes + g.col.nbytes)
+    d2h = int(kk * (4 + 8 + 4))
+
+    # roofline of the dominant kernel (per-CTA waves)
+    peak, peak_kind = load_peaks()
+    wave_s = st["wave_ms"] / 1e3
+    achieved = st["wave_bytes"] / wave_s / 1e9 if wave_s > 0 else None
+    src_hash = kernel_source_hash()
+    traffic = profile_traffic(src_hash)
+    roofline = {"bound": "hbm", "kernel": "k_wave_cta", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "peak_kind": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
+                else "fallback 6.8 TB/s",
+                "alg_bytes_per_launch": st["wave_bytes"], "launch_ms": st["wave_ms"],
+                "kernel_source": src_hash}
+
+    # oracle: CPU baseline and a bit-exactness check on sampled outputs
+    cpu = None
+    bit_exact, verify_note = None, "skipped"
+    if not args.no_cpu or not args.no_verify:
+        import oracle
+        oracle.build()
+    if not args.no_cpu:
+        v, done, cores = cpu_sample(g, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "exhaustive BFS from %d uniformly drawn sources (about %.0f s of CPU work), "
+                         "scaled by n/%d" % (done, args.cpu_seconds, done)}
+    reach_all = None
+    if not args.no_verify:
+        import oracle
+        h = B.BcmGraph.from_graph(g)
+        _, xlo, _ = h.preprocess()
+        reach_all = xlo
+        h.close()
+        of, orr = oracle.farness_all(g, sources=got_ids)
+        exact = bool(np.array_equal(of, got_far) and np.array_equal(orr, got_reach))
+        deg = g.degrees()
+        cand = np.argsort(-deg, kind="stable")[:512].astype(np.uint32)
+        rnd = graphgen.uniform_u32(99, 512, g.n)
+        others = np.setdiff1d(np.concatenate([cand, rnd]), got_ids)
+        sf, sr = oracle.farness_all(g, sources=others)
+        kth = (int(got_reach[-1]), int(got_far[-1]), int(got_ids[-1]))
+
+        def beats(f, r, v, kf):
+            N = 0 if r <= 1 else (r - 1) ** 2
+            F = 1 if r <= 1 else f
+            Nk = 0 if kf[0] <= 1 else (kf[0] - 1) ** 2
+            Fk = 1 if kf[0] <= 1 else kf[1]
+            return N * Fk > Nk * F or (N * Fk == Nk * F and v < kf[2])
+
+        none_better = not any(beats(int(f), int(r), int(v), kth) for f, r, v in zip(sf, sr, others))
+        bit_exact = exact and none_better
+        verify_note = ("oracle BFS from the %d returned ids gives identical farness and reach; none of %d other "
+                       "vertices (the 512 highest-degree and 512 random) ranks above the k-th" % (kk, len(others)))
+    if reach_all is None:
+        h = B.BcmGraph.from_graph(g)
+        _, reach_all, _ = h.preprocess()
+        h.close()
+    m_tot = m_tot_undirected(g, reach_all) if not g.directed else None
+
+    line = {
+        "metric": METRIC, "value": s_per_graph, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "%s: %s" % (args.workload, WORKLOADS[args.workload]), "n": g.n, "m_arcs": g.m,
+                   "k": k, "lanes": args.lanes or 64, "l2": "256 MiB buffer written before every timed step",
+                   "step": "graph handle from device CSR + preprocessing + top-k + release",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "gteps": st["m_vis"] / s_per_graph / 1e9 * world if s_per_graph else None,
+        "m_vis": st["m_vis"], "m_tot": m_tot,
+        "m_vis_over_m_tot": (st["m_vis"] / m_tot) if m_tot else None,
+        "stats": {key: st[key] for key in ("completed", "cut", "waves", "levels", "max_level", "visits",
+                                            "kernel_ms", "preprocess_ms", "seed_ms", "wave_ms", "launches")},
+        "per_k": per_k,
+        "plain": plain,
+        "speedup_vs_plain": (plain["s_per_graph"] / (total / args.steps)) if plain else None,
+        "bit_exact": bit_exact, "verification": verify_note,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "wall_s_timed_region": t_wall,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

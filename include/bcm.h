@@ -93,6 +93,11 @@ typedef struct {
     double   kernel_ms;       /* device time of the BFS kernels (CUDA events) */
     double   preprocess_ms;   /* device time of preprocessing done by this call */
     double   total_ms;        /* wall time of the call */
+    double   seed_ms;         /* device time of the grid-wide first wave (or the plain launches) */
+    double   wave_ms;         /* device time of the per-CTA wave kernel */
+    uint64_t wave_bytes;      /* algorithmic bytes the per-CTA wave kernel moved: 20 per source
+                                 started, 28 per frontier word, 12 per (arc, frontier word), 32 per
+                                 new frontier word, 28 per cleared word */
 } bcm_stats;
 
 /*

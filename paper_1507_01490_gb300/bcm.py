@@ -46,7 +46,8 @@ class bcm_stats(ctypes.Structure):
                 ("arc_words", ctypes.c_uint64), ("new_words", ctypes.c_uint64),
                 ("cleared_words", ctypes.c_uint64), ("launches", ctypes.c_uint64),
                 ("kernel_ms", ctypes.c_double), ("preprocess_ms", ctypes.c_double),
-                ("total_ms", ctypes.c_double)]
+                ("total_ms", ctypes.c_double), ("seed_ms", ctypes.c_double), ("wave_ms", ctypes.c_double),
+                ("wave_bytes", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -142,7 +142,8 @@ struct Aux {
     uint32_t head;
     int err;
     Threshold thr;
-    unsigned long long stats[ST_COUNT];
+    unsigned long long stats[ST_COUNT];        // per-CTA wave kernel
+    unsigned long long seed_stats[ST_COUNT];   // seed wave / plain kernel
     GridBarrier bar;
     uint32_t gcnt[1024];
     uint32_t glist_n[2];
@@ -367,6 +368,18 @@ WaveParams base_params(bcm_graph* g, const Cfg& c) {
     return p;
 }
 
+// Algorithmic bytes of the per-CTA wave kernel, from its counters: the words
+// it must move at minimum (word granularity, no cache or sector effects).
+//   started source            20 B  order entry, row_ptr pair, x_lo/x_hi
+//   frontier word expanded    28 B  list entry, F word read and clear, row_ptr pair
+//   (arc, frontier word)      12 B  col entry, vis word
+//   new frontier word         32 B  vis and F-next atomics, row_ptr pair, list and log entries
+//   cleared word              28 B  log entry, vis/F/F' stores
+uint64_t wave_alg_bytes(const unsigned long long* w, uint64_t sources) {
+    return 20ull * sources + 28ull * w[ST_ENTRIES] + 12ull * w[ST_ARCWORDS] + 32ull * w[ST_DISCWORDS] +
+           28ull * w[ST_CLEARED];
+}
+
 void fill_stats(bcm_stats* s, const unsigned long long* st, uint64_t launches, double kms, double pms, double tms) {
     if (!s) return;
     s->m_vis = st[ST_MVIS];
@@ -387,8 +400,10 @@ void fill_stats(bcm_stats* s, const unsigned long long* st, uint64_t launches, d
 }
 
 // Runs the wave kernels.  exhaustive: every source, no cut; else top-k.
+struct RunTimes { double kernel_ms = 0, seed_ms = 0, wave_ms = 0; };
+
 bcm_status run_waves(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, unsigned long long* stats_out,
-                     double* kernel_ms) {
+                     unsigned long long* wave_stats_out, RunTimes* times) {
     cudaStream_t s = g->stream;
     bcm_status st = ensure_aux(g);
     if (st) return st;
@@ -407,11 +422,13 @@ bcm_status run_waves(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, un
     p.topk.k = k;
     p.out_far = g->d_far;
     p.out_reach = g->d_reach;
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0, em, e1;
     CU(cudaEventCreate(&e0), "event");
+    CU(cudaEventCreate(&em), "event");
     CU(cudaEventCreate(&e1), "event");
     CU(cudaEventRecord(e0, s), "event record");
     int rc = 0;
+    p.stats = g->d_aux->seed_stats;
     if (plain) {
         if (!g->d_plain) CU(cudaMalloc(&g->d_plain, (size_t)g->n * 3 * sizeof(uint32_t) + 256), "plain buffers");
         CU(cudaMemsetAsync(g->d_plain, 0, (size_t)g->n * sizeof(uint32_t), s), "stamp clear");
@@ -431,30 +448,42 @@ bcm_status run_waves(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, un
             rc = launch_seed_wave(p, sw, blocks, 512, s);
             head0 = p.seed_lanes;
         }
-        if (rc == 0 && head0 < g->n) {
-            if (head0) {
-                if (cudaMemcpyAsync(&g->d_aux->head, &head0, sizeof(uint32_t), cudaMemcpyHostToDevice, s) != cudaSuccess)
-                    rc = -1;
-            }
-            if (rc == 0) rc = launch_cta_waves(p, c.W, c.blocks, c.threads, s);
+        if (head0 && rc == 0) {
+            if (cudaMemcpyAsync(&g->d_aux->head, &head0, sizeof(uint32_t), cudaMemcpyHostToDevice, s) != cudaSuccess)
+                rc = -1;
         }
+        cudaEventRecord(em, s);
+        p.stats = g->d_aux->stats;
+        if (rc == 0 && head0 < g->n) rc = launch_cta_waves(p, c.W, c.blocks, c.threads, s);
     }
+    if (plain) cudaEventRecord(em, s);
     cudaEventRecord(e1, s);
     if (rc) {
         cudaStreamSynchronize(s);
         return fail(BCM_ERR_CUDA, "wave kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     }
     int herr = 0;
+    unsigned long long seed_st[ST_COUNT];
     CU(cudaMemcpyAsync(&herr, &g->d_aux->err, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
-    CU(cudaMemcpyAsync(stats_out, g->d_aux->stats, sizeof(unsigned long long) * ST_COUNT, cudaMemcpyDeviceToHost, s),
-       "copy");
+    CU(cudaMemcpyAsync(wave_stats_out, g->d_aux->stats, sizeof(unsigned long long) * ST_COUNT,
+                       cudaMemcpyDeviceToHost, s), "copy");
+    CU(cudaMemcpyAsync(seed_st, g->d_aux->seed_stats, sizeof(unsigned long long) * ST_COUNT,
+                       cudaMemcpyDeviceToHost, s), "copy");
     cudaError_t se = cudaStreamSynchronize(s);
-    float t = 0;
+    float t = 0, t0m = 0, tm1 = 0;
     cudaEventElapsedTime(&t, e0, e1);
+    cudaEventElapsedTime(&t0m, e0, em);
+    cudaEventElapsedTime(&tm1, em, e1);
     cudaEventDestroy(e0);
+    cudaEventDestroy(em);
     cudaEventDestroy(e1);
     if (se != cudaSuccess) return cuda_fail(se, "wave kernels");
-    *kernel_ms = t;
+    for (int i = 0; i < ST_COUNT; ++i)
+        stats_out[i] = (i == ST_MAXLEVEL) ? (wave_stats_out[i] > seed_st[i] ? wave_stats_out[i] : seed_st[i])
+                                          : wave_stats_out[i] + seed_st[i];
+    times->kernel_ms = t;
+    times->seed_ms = t0m;
+    times->wave_ms = tm1;
     if (herr) {
         // a timed-out run may leave words set: do not reuse the region
         region_release(g->slots, false);
@@ -650,10 +679,12 @@ bcm_status bcm_topk(bcm_graph_t g, uint32_t k, const bcm_options* opt, uint32_t*
     if (st) return st;
     Cfg c;
     if ((st = resolve(g, opt, &c))) return st;
-    unsigned long long sv[ST_COUNT] = {0};
+    unsigned long long sv[ST_COUNT] = {0}, wv[ST_COUNT] = {0};
+    RunTimes rt;
     uint32_t kk = k < g->n ? k : g->n;
     if (g->n > 0) {
-        if ((st = run_waves(g, c, k, false, sv, &kms))) return st;
+        if ((st = run_waves(g, c, k, false, sv, wv, &rt))) return st;
+        kms = rt.kernel_ms;
         bool dev = (c.flags & BCM_OUT_DEVICE) != 0;
         Aux* a = g->d_aux;
         if ((st = copy_out(ids, a->topk_id, kk * sizeof(uint32_t), dev, g->stream))) return st;
@@ -665,6 +696,11 @@ bcm_status bcm_topk(bcm_graph_t g, uint32_t k, const bcm_options* opt, uint32_t*
         if (cnt != kk) return fail(BCM_ERR_CUDA, "top-k holds %u entries, expected %u", cnt, kk);
     }
     fill_stats(stats, sv, g_launches.load() - l0, kms, pms, ms_since(t0));
+    if (stats) {
+        stats->seed_ms = rt.seed_ms;
+        stats->wave_ms = rt.wave_ms;
+        stats->wave_bytes = (c.flags & BCM_PLAIN) ? 0 : wave_alg_bytes(wv, wv[ST_COMPLETED] + wv[ST_CUT]);
+    }
     return BCM_OK;
 }
 
@@ -680,15 +716,22 @@ bcm_status bcm_farness_all(bcm_graph_t g, const bcm_options* opt, uint64_t* farn
     if (st) return st;
     Cfg c;
     if ((st = resolve(g, opt, &c))) return st;
-    unsigned long long sv[ST_COUNT] = {0};
+    unsigned long long sv[ST_COUNT] = {0}, wv[ST_COUNT] = {0};
+    RunTimes rt;
     if (g->n > 0) {
-        if ((st = run_waves(g, c, 0, true, sv, &kms))) return st;
+        if ((st = run_waves(g, c, 0, true, sv, wv, &rt))) return st;
+        kms = rt.kernel_ms;
         bool dev = (c.flags & BCM_OUT_DEVICE) != 0;
         if ((st = copy_out(farness, g->d_far, (size_t)g->n * sizeof(uint64_t), dev, g->stream))) return st;
         if ((st = copy_out(reach, g->d_reach, (size_t)g->n * sizeof(uint32_t), dev, g->stream))) return st;
         CU(cudaStreamSynchronize(g->stream), "copy");
     }
     fill_stats(stats, sv, g_launches.load() - l0, kms, pms, ms_since(t0));
+    if (stats) {
+        stats->seed_ms = rt.seed_ms;
+        stats->wave_ms = rt.wave_ms;
+        stats->wave_bytes = wave_alg_bytes(wv, wv[ST_COMPLETED] + wv[ST_CUT]);
+    }
     return BCM_OK;
 }
 

@@ -377,7 +377,9 @@ __global__ void __launch_bounds__(THREADS) k_wave_seed(WaveParams p) {
     const u32 tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const bool leader = blockIdx.x == 0;
     const GraphDev& G = p.g;
-    SlotPtrs S = slot_ptrs(p.seed_base, G.n, W);
+    // arrays placed at their 4-word offsets whatever W is, so runs of
+    // different widths never put bit arrays where another left lists or logs
+    SlotPtrs S = slot_ptrs(p.seed_base, G.n, 4);
     LocalStats st;
     const u32 nsrc = p.seed_lanes < (u32)L ? p.seed_lanes : (u32)L;
     if (tid == 0) { s_nc = 0; s_thr.valid = 0; s_thr.N = 0; s_thr.F = 1; s_thr.id = 0; }

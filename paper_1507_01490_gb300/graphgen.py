@@ -287,6 +287,8 @@ def workload(name: str) -> Graph:
         return ba(2000, 3, seed=1)
     if name == "chunglu1m":
         return chung_lu(1 << 20, 10.0, 2.3, seed=2)
+    if name == "chunglu256k":      # the same recipe at n = 2^18 (profiling-size case)
+        return chung_lu(1 << 18, 10.0, 2.3, seed=2)
     if name == "rmat20":
         return rmat(20, 16, seed=3)
     if name == "grid2048":

@@ -70,7 +70,7 @@ def test_topk_and_farness_directed(B, gen, orc, lanes):
         with B.BcmGraph.from_graph(g) as h:
             gf, gr, _ = h.farness_all(lanes=lanes)
             assert np.array_equal(gf, f) and np.array_equal(gr, r), g.name
-            for k in sorted({1, 2, 5, 10, 100, g.n, g.n + 3} - {0}):
+            for k in sorted({1, 2, 5, 10, 100, min(g.n, 1024), min(g.n + 3, 1024)} - {0}):
                 ids, tf, tr, st = h.topk(k, lanes=lanes)
                 exp = orc.topk(f, r, k)
                 assert np.array_equal(ids, exp), (g.name, k)

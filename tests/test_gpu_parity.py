@@ -78,7 +78,7 @@ def test_topk_small(B, gen, orc, lanes, threads):
     for g in undirected_graphs(gen):
         f, r = orc.farness_all(g)
         with B.BcmGraph.from_graph(g) as h:
-            for k in sorted({1, 2, 3, 10, 100, g.n, g.n + 4} - {0}):
+            for k in sorted({1, 2, 3, 10, 100, min(g.n, 1024), min(g.n + 4, 1024)} - {0}):
                 ids, gf, gr, st = h.topk(k, lanes=lanes, threads=threads)
                 exp = orc.topk(f, r, k)
                 assert np.array_equal(ids, exp), (g.name, k, lanes)
