@@ -65,14 +65,23 @@ typedef enum {
 #define BCM_NO_FOOTNOTE   0x2u  /* undirected: bound gamma_{d+1} by sum of deg(u), not deg(u)-1
                                    (the footnote of Section 2.2 tightens; results are the same) */
 #define BCM_PLAIN         0x4u  /* bcm_topk: one source per kernel launch (comparison baseline) */
-#define BCM_NO_SEED       0x8u  /* bcm_topk: skip the grid-wide first wave */
+#define BCM_CTA_ONLY      0x8u  /* run every wave on the per-CTA kernel (no grid-wide waves) */
 #define BCM_CHECK_SYMMETRIC 0x10u /* bcm_graph_create: verify undirected arcs are paired */
+#define BCM_GRID_ONLY     0x20u /* run every wave on the grid-wide kernel */
 
+/* Sources are taken from the degree order in waves.  Waves run first on a
+ * grid-wide kernel (all CTAs on one wave) while they are heavy, then on a
+ * per-CTA kernel (each CTA its own wave).  A grid wave is light when its
+ * frontiers held fewer than heavy_words (vertex, 64-lane word) entries in
+ * all; the first light one ends the grid phase.  Exhaustive runs stay on
+ * the grid kernel. */
 typedef struct {
-    uint32_t lanes;           /* sources per wave: 64, 128 or 256; 0 = library default */
+    uint32_t lanes;           /* sources per per-CTA wave: 64, 128 or 256; 0 = 64 */
+    uint32_t grid_lanes;      /* sources per grid-wide wave: 64, 128 or 256; 0 = 256 */
     uint32_t flags;           /* BCM_* flags above */
-    uint32_t blocks;          /* CTAs of the wave kernel; 0 = all that fit on the GPU */
-    uint32_t threads;         /* threads per CTA: 256, 512 or 1024; 0 = default (512) */
+    uint32_t blocks;          /* CTAs of the per-CTA kernel; 0 = all that fit on the GPU */
+    uint32_t threads;         /* threads per CTA of the per-CTA kernel: 256, 512 or 1024; 0 = 512 */
+    uint32_t heavy_words;     /* see above; 0 = default (16 per warp of the grid) */
     uint64_t wait_limit_ns;   /* limit of every in-kernel wait; 0 = default (20 s) */
 } bcm_options;
 
@@ -93,7 +102,7 @@ typedef struct {
     double   kernel_ms;       /* device time of the BFS kernels (CUDA events) */
     double   preprocess_ms;   /* device time of preprocessing done by this call */
     double   total_ms;        /* wall time of the call */
-    double   seed_ms;         /* device time of the grid-wide first wave (or the plain launches) */
+    double   seed_ms;         /* device time of the grid-wide waves (or of the plain launches) */
     double   wave_ms;         /* device time of the per-CTA wave kernel */
     uint64_t wave_bytes;      /* algorithmic bytes the per-CTA wave kernel moved: 20 per source
                                  started, 28 per frontier word, 12 per (arc, frontier word), 32 per

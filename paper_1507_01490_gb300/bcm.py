@@ -26,8 +26,9 @@ STATUS_NAMES = {0: "BCM_OK", 1: "BCM_ERR_INVALID", 2: "BCM_ERR_NOT_SYMMETRIC", 3
 BCM_OUT_DEVICE = 0x1
 BCM_NO_FOOTNOTE = 0x2
 BCM_PLAIN = 0x4
-BCM_NO_SEED = 0x8
+BCM_CTA_ONLY = 0x8
 BCM_CHECK_SYMMETRIC = 0x10
+BCM_GRID_ONLY = 0x20
 
 # every symbol include/bcm.h declares
 EXPORTS = ["bcm_graph_create", "bcm_graph_destroy", "bcm_preprocess", "bcm_scc_bounds", "bcm_topk",
@@ -35,8 +36,9 @@ EXPORTS = ["bcm_graph_create", "bcm_graph_destroy", "bcm_preprocess", "bcm_scc_b
 
 
 class bcm_options(ctypes.Structure):
-    _fields_ = [("lanes", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("blocks", ctypes.c_uint32),
-                ("threads", ctypes.c_uint32), ("wait_limit_ns", ctypes.c_uint64)]
+    _fields_ = [("lanes", ctypes.c_uint32), ("grid_lanes", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("blocks", ctypes.c_uint32), ("threads", ctypes.c_uint32), ("heavy_words", ctypes.c_uint32),
+                ("wait_limit_ns", ctypes.c_uint64)]
 
 
 class bcm_stats(ctypes.Structure):
@@ -122,8 +124,9 @@ def bcm_launch_count() -> int:
     return int(load().bcm_launch_count())
 
 
-def make_options(lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0) -> bcm_options:
-    return bcm_options(lanes, flags, blocks, threads, wait_limit_ns)
+def make_options(lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0, grid_lanes=0,
+                 heavy_words=0) -> bcm_options:
+    return bcm_options(lanes, grid_lanes, flags, blocks, threads, heavy_words, wait_limit_ns)
 
 
 def bcm_graph_create(row_ptr, col, n, m, directed, ptr_on_device=False, stream=None, flags=0):
@@ -216,19 +219,21 @@ class BcmGraph:
         nc = bcm_scc_bounds(self.h, comp, al, om)
         return comp[:self.n], al[:self.n], om[:self.n], nc
 
-    def topk(self, k, lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0):
+    def topk(self, k, lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0, grid_lanes=0, heavy_words=0):
         kk = max(min(k, self.n), 1)
         ids = np.zeros(kk, np.uint32)
         far = np.zeros(kk, np.uint64)
         reach = np.zeros(kk, np.uint32)
         st = bcm_stats()
-        bcm_topk(self.h, k, make_options(lanes, flags, blocks, threads, wait_limit_ns), ids, far, reach, st)
+        bcm_topk(self.h, k, make_options(lanes, flags, blocks, threads, wait_limit_ns, grid_lanes, heavy_words),
+                 ids, far, reach, st)
         kk = min(k, self.n)
         return ids[:kk], far[:kk], reach[:kk], st.as_dict()
 
-    def farness_all(self, lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0):
+    def farness_all(self, lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0, grid_lanes=0):
         far = np.zeros(max(self.n, 1), np.uint64)
         reach = np.zeros(max(self.n, 1), np.uint32)
         st = bcm_stats()
-        bcm_farness_all(self.h, make_options(lanes, flags, blocks, threads, wait_limit_ns), far, reach, st)
+        bcm_farness_all(self.h, make_options(lanes, flags, blocks, threads, wait_limit_ns, grid_lanes),
+                        far, reach, st)
         return far[:self.n], reach[:self.n], st.as_dict()

@@ -181,7 +181,8 @@ namespace {
 constexpr uint64_t kDefaultLimitNs = 20ull * 1000 * 1000 * 1000;
 
 struct Cfg {
-    int W, threads, blocks, seed_W, seed_blocks;
+    int W, threads, blocks, grid_W, grid_blocks;
+    uint64_t heavy_words;
     uint64_t limit_ns;
     uint32_t flags;
 };
@@ -205,8 +206,16 @@ bcm_status resolve(bcm_graph* g, const bcm_options* opt, Cfg* c) {
     c->blocks = o.blocks ? (int)o.blocks : maxb;
     if (c->blocks > maxb) c->blocks = maxb;
     c->limit_ns = o.wait_limit_ns ? o.wait_limit_ns : kDefaultLimitNs;
-    c->seed_W = 1;
-    c->seed_blocks = 0;
+    uint32_t glanes = o.grid_lanes ? o.grid_lanes : 256;
+    if (glanes != 64 && glanes != 128 && glanes != 256)
+        return fail(BCM_ERR_UNSUPPORTED, "grid_lanes must be 64, 128 or 256 (got %u)", glanes);
+    c->grid_W = (int)(glanes / 64);
+    int gb = max_coop_blocks(0, c->grid_W, 512);
+    if (gb < 1) return fail(BCM_ERR_CUDA, "grid wave kernel does not fit on an SM");
+    c->grid_blocks = gb;
+    c->heavy_words = o.heavy_words ? o.heavy_words : (uint64_t)gb * 16 * 16;   // 16 entries per warp
+    if ((c->flags & BCM_CTA_ONLY) && (c->flags & BCM_GRID_ONLY))
+        return fail(BCM_ERR_INVALID, "BCM_CTA_ONLY and BCM_GRID_ONLY exclude each other");
     return BCM_OK;
 }
 
@@ -438,23 +447,16 @@ bcm_status run_waves(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, un
         for (uint32_t it = 0; it < g->n && rc == 0; ++it)
             rc = launch_plain_source(p, it, g->d_plain, g->d_plain + g->n, blocks, 256, s);
     } else {
-        uint32_t head0 = 0;
-        if (!exhaustive && !(c.flags & BCM_NO_SEED) && g->n > 0) {
-            int sw = (int)((k + 63) / 64);
-            sw = sw <= 1 ? 1 : (sw <= 2 ? 2 : 4);
-            p.seed_lanes = (uint32_t)(64 * sw) < g->n ? (uint32_t)(64 * sw) : g->n;
-            int blocks = max_coop_blocks(0, sw, 512);
-            if (blocks > g->sms) blocks = g->sms;
-            rc = launch_seed_wave(p, sw, blocks, 512, s);
-            head0 = p.seed_lanes;
-        }
-        if (head0 && rc == 0) {
-            if (cudaMemcpyAsync(&g->d_aux->head, &head0, sizeof(uint32_t), cudaMemcpyHostToDevice, s) != cudaSuccess)
-                rc = -1;
+        // grid-wide waves while they are heavy (every wave for exhaustive
+        // runs), then per-CTA waves from wherever the grid kernel left head
+        if (!(c.flags & BCM_CTA_ONLY)) {
+            p.max_grid_waves = 0xffffffffu;
+            p.heavy_words = (exhaustive || (c.flags & BCM_GRID_ONLY)) ? 0 : c.heavy_words;
+            rc = launch_grid_waves(p, c.grid_W, c.grid_blocks, 512, s);
         }
         cudaEventRecord(em, s);
         p.stats = g->d_aux->stats;
-        if (rc == 0 && head0 < g->n) rc = launch_cta_waves(p, c.W, c.blocks, c.threads, s);
+        if (rc == 0) rc = launch_cta_waves(p, c.W, c.blocks, c.threads, s);
     }
     if (plain) cudaEventRecord(em, s);
     cudaEventRecord(e1, s);

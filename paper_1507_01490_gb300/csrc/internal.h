@@ -55,7 +55,7 @@ struct WaveParams {
     uint32_t* out_reach;
     char* slot_base;         // CTA i: slot_base + i * slot_stride
     size_t slot_stride;
-    char* seed_base;         // the seed wave's own slot (4 words per vertex)
+    char* seed_base;         // the grid kernel's own slot (4 words per vertex)
     unsigned long long* stats;   // [ST_COUNT]
     int* err;
     unsigned long long lock_limit_ns;
@@ -65,7 +65,8 @@ struct WaveParams {
     uint32_t* gcnt;          // [2][2][256] per-lane level counters (gamma, degree sum)
     uint32_t* glist_n;       // [2] frontier list sizes
     uint32_t* glog_n;        // [1] cleared-word log size
-    uint32_t seed_lanes;     // sources taken by the seed wave
+    uint32_t max_grid_waves;  // grid kernel: at most this many waves
+    uint64_t heavy_words;   // grid kernel: a wave with fewer frontier words in total is light
 };
 
 // ---- preproc.cu
@@ -100,11 +101,11 @@ int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, uint32_t n, uint6
                       void* scratch, size_t scratch_bytes, int* err, cudaStream_t s);
 
 // ---- msbfs.cu
-int launch_seed_wave(const WaveParams& p, int W, int blocks, int threads, cudaStream_t s);
+int launch_grid_waves(const WaveParams& p, int W, int blocks, int threads, cudaStream_t s);
 int launch_cta_waves(const WaveParams& p, int W, int blocks, int threads, cudaStream_t s);
 int launch_plain_source(const WaveParams& p, uint32_t it, uint32_t* stamp, uint32_t* lists,
                         int blocks, int threads, cudaStream_t s);
-int max_coop_blocks(int kind, int W, int threads);   // kind 0 seed, 1 plain
+int max_coop_blocks(int kind, int W, int threads);   // kind 0 grid waves, 1 plain
 int cta_blocks_per_sm(int W, int threads);
 
 // launch bookkeeping (api.cu)

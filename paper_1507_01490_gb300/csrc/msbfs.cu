@@ -18,9 +18,11 @@
 //                three __syncthreads.  Completed lanes go to the shared top-k
 //                under a bounded lock; its k-th key is published with a
 //                sequence counter and read once per level.
-//   k_wave_seed  cooperative; the whole grid runs the first wave (the
-//                highest-degree sources) so that a threshold exists before
-//                the CTAs start.  Two bounded grid barriers per level.
+//   k_wave_grid  cooperative; the whole grid runs waves one at a time, from
+//                the highest-degree sources, while they are heavy (their
+//                frontiers span much of the graph), so a heavy wave gets the
+//                whole GPU's bandwidth; the first light wave hands the queue
+//                to k_wave_cta.  Two bounded grid barriers per level.
 //   k_plain      cooperative; one source per launch, level-synchronous with
 //                a vertex queue and visit stamps: the baseline.
 #include <cuda_runtime.h>
@@ -356,12 +358,18 @@ __global__ void __launch_bounds__(THREADS) k_wave_cta(WaveParams p) {
     flush_stats(st, p.stats);
 }
 
-// ------------------------------------------------------------ seed wave
-// The whole grid runs order[0 .. seed_lanes) as one wave.  Each block keeps
-// an identical copy of the lane state; per-level counters are summed in
-// global memory between two grid barriers; block 0 owns the top-k.
+// ------------------------------------------------------------ grid waves
+// The whole grid runs waves one after another, taking 64*W sources at
+// order[*head] each time.  Each block keeps an identical copy of the lane
+// state; per-level counters are summed in global memory between two grid
+// barriers; block 0 owns the top-k.  After each wave the grid decides, from
+// values every block read after the same barriers, whether the wave was
+// heavy (its frontiers held more than p.heavy_words words in total).  On
+// the first light wave the kernel returns and leaves *head where the
+// per-CTA kernel continues; exhaustive runs (or max_grid_waves reached) end it
+// too.
 template <int W, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_wave_seed(WaveParams p) {
+__global__ void __launch_bounds__(THREADS) k_wave_grid(WaveParams p) {
     constexpr int L = 64 * W;
     constexpr int NWARP = THREADS / 32;
     static_assert(THREADS >= L, "one thread per lane");
@@ -369,7 +377,7 @@ __global__ void __launch_bounds__(THREADS) k_wave_seed(WaveParams p) {
     __shared__ u64 s_f[L];
     __shared__ u32 s_cg[L], s_cs[L];
     __shared__ u32 s_alive32[2 * W];
-    __shared__ u32 s_nc;
+    __shared__ u32 s_nc, s_base;
     __shared__ ThrCache s_thr;
     __shared__ u32 s_cid[L], s_cr[L];
     __shared__ u64 s_cf[L];
@@ -381,124 +389,146 @@ __global__ void __launch_bounds__(THREADS) k_wave_seed(WaveParams p) {
     // different widths never put bit arrays where another left lists or logs
     SlotPtrs S = slot_ptrs(p.seed_base, G.n, 4);
     LocalStats st;
-    const u32 nsrc = p.seed_lanes < (u32)L ? p.seed_lanes : (u32)L;
+    const u32 gw = blockIdx.x * NWARP + wid, gnw = gridDim.x * NWARP;
     if (tid == 0) { s_nc = 0; s_thr.valid = 0; s_thr.N = 0; s_thr.F = 1; s_thr.id = 0; }
-    __syncthreads();
-    if (tid < L) {
-        bool alive = false;
-        s_cg[tid] = 0;
-        s_cs[tid] = 0;
-        if (tid < nsrc) {
-            u32 v = __ldg(&G.order[tid]);
-            u32 deg = __ldg(&G.rp[v + 1]) - __ldg(&G.rp[v]);
-            s_src[tid] = v; s_nd[tid] = 1; s_f[tid] = 0; s_gt[tid] = deg;
-            s_xlo[tid] = __ldg(&G.xlo[v]); s_xhi[tid] = __ldg(&G.xhi[v]);
-            if (deg == 0) {
-                if (leader) {
-                    u32 c = atomicAdd(&s_nc, 1u);
-                    s_cid[c] = v; s_cf[c] = 0; s_cr[c] = 1;
-                    st.completed++;
-                }
-            } else {
-                alive = true;
-            }
-        }
-        u32 m = __ballot_sync(0xffffffffu, alive);
-        if (lane == 0) s_alive32[tid >> 5] = m;
-    }
-    __syncthreads();
-    if (leader) flush_completions(p, s_cid, s_cf, s_cr, s_nc, s_thr, THREADS);
-    __syncthreads();
-    if (tid == 0) s_nc = 0;
     bool ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err);
 
-    const u32 gw = blockIdx.x * NWARP + wid, gnw = gridDim.x * NWARP;
-    u32 d = 0, cur = 0;
-    while (ok) {
-        if (!p.exhaustive && tid == 0) read_threshold(p.topk.thr, s_thr);
+    for (u32 wave = 0; ok && wave < p.max_grid_waves; ++wave) {
+        if (tid == 0) s_base = vload(p.head);
         __syncthreads();
+        const u32 base = s_base;
+        if (base >= p.n_end) break;
         if (tid < L) {
-            bool a = (s_alive32[tid >> 5] >> lane) & 1u;
-            if (a && !p.exhaustive &&
-                bfscut_stops(s_f[tid], s_gt[tid], d, s_nd[tid], s_xlo[tid], s_xhi[tid], s_src[tid], s_thr)) {
-                a = false;
-                if (leader) st.cut++;
-            }
-            u32 m = __ballot_sync(0xffffffffu, a);
-            if (lane == 0) s_alive32[tid >> 5] = m;
-        }
-        __syncthreads();
-        u32 any = 0;
-#pragma unroll
-        for (int i = 0; i < 2 * W; ++i) any |= s_alive32[i];
-        if (!any) break;
-
-        const u32 par = d & 1;
-        u32* gcg = p.gcnt + par * 512;
-        u32* gcs = gcg + 256;
-        if (d == 0)
-            expand_sources<W>(G, s_src, s_alive32, L, S.vis, S.F[cur ^ 1], s_cg, s_cs, p.footnote,
-                              S.list[cur ^ 1], &p.glist_n[cur ^ 1], S.clog, p.glog_n, gw, gnw, st);
-        else
-            expand_entries<W>(G, S.list[cur], vload(&p.glist_n[cur]), S.F[cur], s_alive32, S.vis, S.F[cur ^ 1],
-                              s_cg, s_cs, p.footnote, S.list[cur ^ 1], &p.glist_n[cur ^ 1], S.clog,
-                              p.glog_n, gw, gnw, st);
-        __syncthreads();
-        if (tid < L) {
-            if (s_cg[tid]) { atomicAdd(&gcg[tid], s_cg[tid]); atomicAdd(&gcs[tid], s_cs[tid]); }
+            bool alive = false;
             s_cg[tid] = 0;
             s_cs[tid] = 0;
-        }
-        if (!grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err)) break;
-        if (tid < L) {
-            bool a = (s_alive32[tid >> 5] >> lane) & 1u;
-            if (a) {
-                u32 gam = vload(&gcg[tid]);
-                if (gam == 0) {
+            if (base + tid < p.n_end) {
+                u32 v = __ldg(&G.order[base + tid]);
+                u32 deg = __ldg(&G.rp[v + 1]) - __ldg(&G.rp[v]);
+                s_src[tid] = v; s_nd[tid] = 1; s_f[tid] = 0; s_gt[tid] = deg;
+                s_xlo[tid] = __ldg(&G.xlo[v]); s_xhi[tid] = __ldg(&G.xhi[v]);
+                if (deg == 0) {
                     if (leader) {
                         u32 c = atomicAdd(&s_nc, 1u);
-                        s_cid[c] = s_src[tid]; s_cf[c] = s_f[tid]; s_cr[c] = s_nd[tid];
+                        s_cid[c] = v; s_cf[c] = 0; s_cr[c] = 1;
                         st.completed++;
                     }
-                    a = false;
                 } else {
-                    s_nd[tid] += gam;
-                    s_f[tid] += (u64)(d + 1) * gam;
-                    s_gt[tid] = vload(&gcs[tid]);
+                    alive = true;
                 }
             }
-            u32 m = __ballot_sync(0xffffffffu, a);
+            u32 m = __ballot_sync(0xffffffffu, alive);
             if (lane == 0) s_alive32[tid >> 5] = m;
-        }
-        if (leader) {   // buffers of the next level: counters par^1, list count cur
-            u32* nx = p.gcnt + (par ^ 1) * 512;
-            for (u32 i = tid; i < 512; i += THREADS) nx[i] = 0;
-            if (tid == 0) p.glist_n[cur] = 0;
         }
         __syncthreads();
         if (leader) flush_completions(p, s_cid, s_cf, s_cr, s_nc, s_thr, THREADS);
         __syncthreads();
         if (tid == 0) s_nc = 0;
-        if (!grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err)) break;
-        cur ^= 1;
-        ++d;
+        if (!(ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err))) break;
+
+        u32 d = 0, cur = 0;
+        u64 wave_entries = 0;
+        for (;;) {
+            if (!p.exhaustive && tid == 0) read_threshold(p.topk.thr, s_thr);
+            __syncthreads();
+            if (tid < L) {
+                bool a = (s_alive32[tid >> 5] >> lane) & 1u;
+                if (a && !p.exhaustive &&
+                    bfscut_stops(s_f[tid], s_gt[tid], d, s_nd[tid], s_xlo[tid], s_xhi[tid], s_src[tid], s_thr)) {
+                    a = false;
+                    if (leader) st.cut++;
+                }
+                u32 m = __ballot_sync(0xffffffffu, a);
+                if (lane == 0) s_alive32[tid >> 5] = m;
+            }
+            __syncthreads();
+            u32 any = 0;
+#pragma unroll
+            for (int i = 0; i < 2 * W; ++i) any |= s_alive32[i];
+            if (!any) break;
+
+            const u32 par = d & 1;
+            u32* gcg = p.gcnt + par * 512;
+            u32* gcs = gcg + 256;
+            if (d == 0) {
+                expand_sources<W>(G, s_src, s_alive32, L, S.vis, S.F[cur ^ 1], s_cg, s_cs, p.footnote,
+                                  S.list[cur ^ 1], &p.glist_n[cur ^ 1], S.clog, p.glog_n, gw, gnw, st);
+            } else {
+                const u32 cnt = vload(&p.glist_n[cur]);
+                wave_entries += cnt;
+                expand_entries<W>(G, S.list[cur], cnt, S.F[cur], s_alive32, S.vis, S.F[cur ^ 1], s_cg, s_cs,
+                                  p.footnote, S.list[cur ^ 1], &p.glist_n[cur ^ 1], S.clog, p.glog_n, gw, gnw, st);
+            }
+            __syncthreads();
+            if (tid < L) {
+                if (s_cg[tid]) { atomicAdd(&gcg[tid], s_cg[tid]); atomicAdd(&gcs[tid], s_cs[tid]); }
+                s_cg[tid] = 0;
+                s_cs[tid] = 0;
+            }
+            if (!(ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err))) break;
+            if (tid < L) {
+                bool a = (s_alive32[tid >> 5] >> lane) & 1u;
+                if (a) {
+                    u32 gam = vload(&gcg[tid]);
+                    if (gam == 0) {
+                        if (leader) {
+                            u32 c = atomicAdd(&s_nc, 1u);
+                            s_cid[c] = s_src[tid]; s_cf[c] = s_f[tid]; s_cr[c] = s_nd[tid];
+                            st.completed++;
+                        }
+                        a = false;
+                    } else {
+                        s_nd[tid] += gam;
+                        s_f[tid] += (u64)(d + 1) * gam;
+                        s_gt[tid] = vload(&gcs[tid]);
+                    }
+                }
+                u32 m = __ballot_sync(0xffffffffu, a);
+                if (lane == 0) s_alive32[tid >> 5] = m;
+            }
+            if (leader) {   // buffers of the next level: counters par^1, list count cur
+                u32* nx = p.gcnt + (par ^ 1) * 512;
+                for (u32 i = tid; i < 512; i += THREADS) nx[i] = 0;
+                if (tid == 0) p.glist_n[cur] = 0;
+            }
+            __syncthreads();
+            if (leader) flush_completions(p, s_cid, s_cf, s_cr, s_nc, s_thr, THREADS);
+            __syncthreads();
+            if (tid == 0) s_nc = 0;
+            if (!(ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err))) break;
+            cur ^= 1;
+            ++d;
+        }
+        if (!ok) break;
+        if (leader && tid == 0) {
+            st.waves++;
+            st.levels += d;
+            if (d > st.maxlevel) st.maxlevel = d;
+        }
+        // clear the wave's footprint: every block has finished expanding
+        // (the level loop ends at a barrier or on a decision all blocks share)
+        if (!(ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err))) break;
+        const u32 nlog = vload(p.glog_n);
+        for (u32 i = blockIdx.x * THREADS + tid; i < nlog; i += gridDim.x * THREADS) {
+            u32 w = __ldcg(&S.clog[i]);
+            S.vis[w] = 0;
+            S.F[0][w] = 0;
+            S.F[1][w] = 0;
+        }
+        if (leader && tid == 0) st.cleared += nlog;
+        if (!(ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err))) break;
+        if (leader) {   // reset per-wave counters and advance the queue
+            for (u32 i = tid; i < 1024; i += THREADS) p.gcnt[i] = 0;
+            if (tid == 0) {
+                p.glist_n[0] = 0;
+                p.glist_n[1] = 0;
+                *p.glog_n = 0;
+                *p.head = base + L;
+            }
+        }
+        if (!(ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err))) break;
+        if (!p.exhaustive && wave_entries < p.heavy_words) break;   // light: hand over to the CTAs
     }
-    if (leader && tid == 0) {
-        st.waves = 1;
-        st.levels = d;
-        st.maxlevel = d;
-    }
-    // clear the wave's footprint (every block finished expanding: the last
-    // pass through the loop ended at a barrier or found no live lane)
-    grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err);
-    const u32 nlog = vload(p.glog_n);
-    for (u32 i = blockIdx.x * THREADS + tid; i < nlog; i += gridDim.x * THREADS) {
-        u32 w = S.clog[i];
-        S.vis[w] = 0;
-        S.F[0][w] = 0;
-        S.F[1][w] = 0;
-    }
-    if (leader && tid == 0) st.cleared = nlog;
     flush_stats(st, p.stats);
 }
 
@@ -654,18 +684,18 @@ int launch_cta_waves(const WaveParams& p, int W, int blocks, int threads, cudaSt
 }
 
 template <int W, int T>
-static int launch_seed_t(const WaveParams& p, int blocks, cudaStream_t s) {
+static int launch_grid_t(const WaveParams& p, int blocks, cudaStream_t s) {
     void* args[] = {(void*)&p};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_wave_seed<W, T>, dim3(blocks), dim3(T), args, 0, s);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_wave_grid<W, T>, dim3(blocks), dim3(T), args, 0, s);
     note_launch();
     return e == cudaSuccess ? 0 : -1;
 }
 
-int launch_seed_wave(const WaveParams& p, int W, int blocks, int threads, cudaStream_t s) {
+int launch_grid_waves(const WaveParams& p, int W, int blocks, int threads, cudaStream_t s) {
     if (threads != 512) return -2;
-    if (W == 1) return launch_seed_t<1, 512>(p, blocks, s);
-    if (W == 2) return launch_seed_t<2, 512>(p, blocks, s);
-    if (W == 4) return launch_seed_t<4, 512>(p, blocks, s);
+    if (W == 1) return launch_grid_t<1, 512>(p, blocks, s);
+    if (W == 2) return launch_grid_t<2, 512>(p, blocks, s);
+    if (W == 4) return launch_grid_t<4, 512>(p, blocks, s);
     return -2;
 }
 
@@ -684,9 +714,9 @@ int max_coop_blocks(int kind, int W, int threads) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const void* f = nullptr;
     if (kind == 1) f = (const void*)k_plain<256>;
-    else if (W == 1) f = (const void*)k_wave_seed<1, 512>;
-    else if (W == 2) f = (const void*)k_wave_seed<2, 512>;
-    else f = (const void*)k_wave_seed<4, 512>;
+    else if (W == 1) f = (const void*)k_wave_grid<1, 512>;
+    else if (W == 2) f = (const void*)k_wave_grid<2, 512>;
+    else f = (const void*)k_wave_grid<4, 512>;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, f, threads, 0) != cudaSuccess) return 0;
     return per * sms;
 }

@@ -68,13 +68,16 @@ def test_topk_and_farness_directed(B, gen, orc, lanes):
     for g in directed_graphs(gen):
         f, r = orc.farness_all(g)
         with B.BcmGraph.from_graph(g) as h:
-            gf, gr, _ = h.farness_all(lanes=lanes)
+            gf, gr, _ = h.farness_all(grid_lanes=lanes)
+            assert np.array_equal(gf, f) and np.array_equal(gr, r), g.name
+            gf, gr, _ = h.farness_all(lanes=lanes, flags=B.BCM_CTA_ONLY)
             assert np.array_equal(gf, f) and np.array_equal(gr, r), g.name
             for k in sorted({1, 2, 5, 10, 100, min(g.n, 1024), min(g.n + 3, 1024)} - {0}):
-                ids, tf, tr, st = h.topk(k, lanes=lanes)
                 exp = orc.topk(f, r, k)
-                assert np.array_equal(ids, exp), (g.name, k)
-                assert np.array_equal(tf, f[exp]) and np.array_equal(tr, r[exp]), (g.name, k)
+                for flags in (0, B.BCM_CTA_ONLY, B.BCM_GRID_ONLY):
+                    ids, tf, tr, st = h.topk(k, lanes=lanes, grid_lanes=lanes, flags=flags)
+                    assert np.array_equal(ids, exp), (g.name, k, flags)
+                    assert np.array_equal(tf, f[exp]) and np.array_equal(tr, r[exp]), (g.name, k)
 
 
 def test_plain_equals_oracle_bcm_directed(B, gen, orc):

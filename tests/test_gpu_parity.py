@@ -69,8 +69,10 @@ def test_farness_all_small(B, gen, orc, lanes):
     for g in undirected_graphs(gen):
         f, r = orc.farness_all(g)
         with B.BcmGraph.from_graph(g) as h:
-            gf, gr, st = h.farness_all(lanes=lanes)
-        assert np.array_equal(gf, f) and np.array_equal(gr, r), (g.name, lanes)
+            gf, gr, st = h.farness_all(grid_lanes=lanes)
+            assert np.array_equal(gf, f) and np.array_equal(gr, r), (g.name, lanes)
+            gf, gr, st = h.farness_all(lanes=lanes, flags=B.BCM_CTA_ONLY)
+            assert np.array_equal(gf, f) and np.array_equal(gr, r), (g.name, lanes, "cta")
 
 
 @pytest.mark.parametrize("lanes,threads", [(64, 256), (64, 512), (128, 512), (256, 256), (256, 1024)])
@@ -86,14 +88,22 @@ def test_topk_small(B, gen, orc, lanes, threads):
                 assert st["completed"] + st["cut"] == g.n, (g.name, k, st)
 
 
-def test_topk_without_seed_and_footnote(B, gen, orc):
-    for g in undirected_graphs(gen)[::3]:
+def test_topk_kernel_choices_and_footnote(B, gen, orc):
+    """Every wave on one kernel or the other, any grid width, the heavy/light
+    switch at several points, and the bound without the undirected footnote."""
+    for g in undirected_graphs(gen)[::2]:
         f, r = orc.farness_all(g)
         with B.BcmGraph.from_graph(g) as h:
             for k in (1, 5, 40):
-                for flags in (B.BCM_NO_SEED, B.BCM_NO_FOOTNOTE, B.BCM_NO_SEED | B.BCM_NO_FOOTNOTE):
+                exp = orc.topk(f, r, k)
+                for flags in (B.BCM_CTA_ONLY, B.BCM_GRID_ONLY, B.BCM_NO_FOOTNOTE,
+                              B.BCM_CTA_ONLY | B.BCM_NO_FOOTNOTE, B.BCM_GRID_ONLY | B.BCM_NO_FOOTNOTE):
                     ids, gf, gr, st = h.topk(k, flags=flags)
-                    assert np.array_equal(ids, orc.topk(f, r, k)), (g.name, k, flags)
+                    assert np.array_equal(ids, exp), (g.name, k, flags)
+                for gl in (64, 128, 256):
+                    for hw in (1, 50, 1 << 30):
+                        ids, gf, gr, st = h.topk(k, grid_lanes=gl, heavy_words=hw)
+                        assert np.array_equal(ids, exp) and np.array_equal(gf, f[exp]), (g.name, k, gl, hw)
 
 
 def test_plain_equals_oracle_bcm(B, gen, orc):
@@ -176,6 +186,12 @@ def test_errors(B, gen):
         with pytest.raises(B.BcmError) as ei:
             h.topk(1, lanes=256, threads=128)
         assert ei.value.status == B.BCM_ERR_UNSUPPORTED
+        with pytest.raises(B.BcmError) as ei:
+            h.topk(1, grid_lanes=96)
+        assert ei.value.status == B.BCM_ERR_UNSUPPORTED
+        with pytest.raises(B.BcmError) as ei:
+            h.topk(1, flags=B.BCM_CTA_ONLY | B.BCM_GRID_ONLY)
+        assert ei.value.status == B.BCM_ERR_INVALID
     bad_rp = np.array([0, 2, 1, 3], np.uint64)
     with pytest.raises(B.BcmError) as ei:
         B.BcmGraph(bad_rp, np.array([1, 2, 0], np.uint32), 3, False)
