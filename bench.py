@@ -115,10 +115,10 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def profile_traffic(kernel_src_hash):
-    """dram bytes per launch of the wave kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
-    p = os.path.join(ROOT, "profiles", "k_wave_cta_chunglu1m.md")
+def profile_traffic(kernel, kernel_src_hash):
+    """dram bytes per launch of `kernel` from the committed ncu summary, if
+    it was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "%s_chunglu1m.md" % kernel)
     if not os.path.exists(p):
         return None
     traffic, src = None, None
@@ -348,18 +348,23 @@ def main():
     h2d = int(g.row_ptr.nbytes + g.col.nbytes)
     d2h = int(kk * (4 + 8 + 4))
 
-    # roofline of the dominant kernel (per-CTA waves)
+    # roofline of the dominant kernel: the grid-wide or the per-CTA wave kernel,
+    # whichever took longer (one launch each per step)
     peak, peak_kind = load_peaks()
-    wave_s = st["wave_ms"] / 1e3
-    achieved = st["wave_bytes"] / wave_s / 1e9 if wave_s > 0 else None
+    if st["seed_ms"] >= st["wave_ms"]:
+        kname, kms, kbytes = "k_wave_grid", st["seed_ms"], st["grid_bytes"]
+    else:
+        kname, kms, kbytes = "k_wave_cta", st["wave_ms"], st["wave_bytes"]
+    achieved = kbytes / (kms / 1e3) / 1e9 if kms > 0 else None
     src_hash = kernel_source_hash()
-    traffic = profile_traffic(src_hash)
-    roofline = {"bound": "hbm", "kernel": "k_wave_cta", "achieved": achieved, "peak": peak, "unit": "GB/s",
+    traffic = profile_traffic(kname, src_hash)
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "peak_kind": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
                 else "fallback 6.8 TB/s",
-                "alg_bytes_per_launch": st["wave_bytes"], "launch_ms": st["wave_ms"],
-                "kernel_source": src_hash}
+                "alg_bytes_per_launch": kbytes, "launch_ms": kms, "kernel_source": src_hash,
+                "other_kernel": {"grid_ms": st["seed_ms"], "grid_bytes": st["grid_bytes"],
+                                 "cta_ms": st["wave_ms"], "cta_bytes": st["wave_bytes"]}}
 
     # oracle: CPU baseline and a bit-exactness check on sampled outputs
     cpu = None
@@ -417,7 +422,8 @@ def main():
         "m_vis": st["m_vis"], "m_tot": m_tot,
         "m_vis_over_m_tot": (st["m_vis"] / m_tot) if m_tot else None,
         "stats": {key: st[key] for key in ("completed", "cut", "waves", "levels", "max_level", "visits",
-                                            "kernel_ms", "preprocess_ms", "seed_ms", "wave_ms", "launches")},
+                                            "kernel_ms", "preprocess_ms", "seed_ms", "wave_ms", "launches",
+                                            "grid_waves", "grid_levels")},
         "per_k": per_k,
         "plain": plain,
         "speedup_vs_plain": (plain["s_per_graph"] / (total / args.steps)) if plain else None,

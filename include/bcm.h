@@ -68,20 +68,28 @@ typedef enum {
 #define BCM_CTA_ONLY      0x8u  /* run every wave on the per-CTA kernel (no grid-wide waves) */
 #define BCM_CHECK_SYMMETRIC 0x10u /* bcm_graph_create: verify undirected arcs are paired */
 #define BCM_GRID_ONLY     0x20u /* run every wave on the grid-wide kernel */
+#define BCM_NO_PULL       0x40u /* grid-wide waves expand every level by push */
 
 /* Sources are taken from the degree order in waves.  Waves run first on a
  * grid-wide kernel (all CTAs on one wave) while they are heavy, then on a
  * per-CTA kernel (each CTA its own wave).  A grid wave is light when its
  * frontiers held fewer than heavy_words (vertex, 64-lane word) entries in
  * all; the first light one ends the grid phase.  Exhaustive runs stay on
- * the grid kernel. */
+ * the grid kernel.  Levels of grid waves run by push (each frontier vertex
+ * sets its lanes' bits in its out-neighbours) or, when the frontier is a
+ * large share of the graph, by pull (each vertex with lanes still to reach
+ * gathers them from its in-neighbours' frontier bits, with no atomics). */
 typedef struct {
     uint32_t lanes;           /* sources per per-CTA wave: 64, 128 or 256; 0 = 64 */
-    uint32_t grid_lanes;      /* sources per grid-wide wave: 64, 128 or 256; 0 = 256 */
+    uint32_t grid_lanes;      /* sources per grid-wide wave: 64, 128 or 256; 0 = 128 */
     uint32_t flags;           /* BCM_* flags above */
     uint32_t blocks;          /* CTAs of the per-CTA kernel; 0 = all that fit on the GPU */
     uint32_t threads;         /* threads per CTA of the per-CTA kernel: 256, 512 or 1024; 0 = 512 */
     uint32_t heavy_words;     /* see above; 0 = default (16 per warp of the grid) */
+    uint32_t pull_div;        /* a grid-wave level whose frontier holds at least n*W/pull_div words
+                                 (W = grid_lanes/64) is expanded by pull; 0 = default
+                                 (64 for bcm_topk, 16 for bcm_farness_all) */
+    uint32_t reserved;        /* 0 */
     uint64_t wait_limit_ns;   /* limit of every in-kernel wait; 0 = default (20 s) */
 } bcm_options;
 
@@ -107,6 +115,9 @@ typedef struct {
     uint64_t wave_bytes;      /* algorithmic bytes the per-CTA wave kernel moved: 20 per source
                                  started, 28 per frontier word, 12 per (arc, frontier word), 32 per
                                  new frontier word, 28 per cleared word */
+    uint64_t grid_waves;      /* waves run by the grid-wide kernel */
+    uint64_t grid_levels;     /* levels those waves expanded */
+    uint64_t grid_bytes;      /* algorithmic bytes of the grid-wide kernel (same unit costs) */
 } bcm_stats;
 
 /*

@@ -29,6 +29,7 @@ BCM_PLAIN = 0x4
 BCM_CTA_ONLY = 0x8
 BCM_CHECK_SYMMETRIC = 0x10
 BCM_GRID_ONLY = 0x20
+BCM_NO_PULL = 0x40
 
 # every symbol include/bcm.h declares
 EXPORTS = ["bcm_graph_create", "bcm_graph_destroy", "bcm_preprocess", "bcm_scc_bounds", "bcm_topk",
@@ -38,7 +39,7 @@ EXPORTS = ["bcm_graph_create", "bcm_graph_destroy", "bcm_preprocess", "bcm_scc_b
 class bcm_options(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_uint32), ("grid_lanes", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("blocks", ctypes.c_uint32), ("threads", ctypes.c_uint32), ("heavy_words", ctypes.c_uint32),
-                ("wait_limit_ns", ctypes.c_uint64)]
+                ("pull_div", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("wait_limit_ns", ctypes.c_uint64)]
 
 
 class bcm_stats(ctypes.Structure):
@@ -49,7 +50,8 @@ class bcm_stats(ctypes.Structure):
                 ("cleared_words", ctypes.c_uint64), ("launches", ctypes.c_uint64),
                 ("kernel_ms", ctypes.c_double), ("preprocess_ms", ctypes.c_double),
                 ("total_ms", ctypes.c_double), ("seed_ms", ctypes.c_double), ("wave_ms", ctypes.c_double),
-                ("wave_bytes", ctypes.c_uint64)]
+                ("wave_bytes", ctypes.c_uint64), ("grid_waves", ctypes.c_uint64),
+                ("grid_levels", ctypes.c_uint64), ("grid_bytes", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -125,8 +127,8 @@ def bcm_launch_count() -> int:
 
 
 def make_options(lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0, grid_lanes=0,
-                 heavy_words=0) -> bcm_options:
-    return bcm_options(lanes, grid_lanes, flags, blocks, threads, heavy_words, wait_limit_ns)
+                 heavy_words=0, pull_div=0) -> bcm_options:
+    return bcm_options(lanes, grid_lanes, flags, blocks, threads, heavy_words, pull_div, 0, wait_limit_ns)
 
 
 def bcm_graph_create(row_ptr, col, n, m, directed, ptr_on_device=False, stream=None, flags=0):
@@ -219,21 +221,22 @@ class BcmGraph:
         nc = bcm_scc_bounds(self.h, comp, al, om)
         return comp[:self.n], al[:self.n], om[:self.n], nc
 
-    def topk(self, k, lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0, grid_lanes=0, heavy_words=0):
+    def topk(self, k, lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0, grid_lanes=0, heavy_words=0,
+             pull_div=0):
         kk = max(min(k, self.n), 1)
         ids = np.zeros(kk, np.uint32)
         far = np.zeros(kk, np.uint64)
         reach = np.zeros(kk, np.uint32)
         st = bcm_stats()
-        bcm_topk(self.h, k, make_options(lanes, flags, blocks, threads, wait_limit_ns, grid_lanes, heavy_words),
-                 ids, far, reach, st)
+        bcm_topk(self.h, k, make_options(lanes, flags, blocks, threads, wait_limit_ns, grid_lanes, heavy_words,
+                                         pull_div), ids, far, reach, st)
         kk = min(k, self.n)
         return ids[:kk], far[:kk], reach[:kk], st.as_dict()
 
-    def farness_all(self, lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0, grid_lanes=0):
+    def farness_all(self, lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0, grid_lanes=0, pull_div=0):
         far = np.zeros(max(self.n, 1), np.uint64)
         reach = np.zeros(max(self.n, 1), np.uint32)
         st = bcm_stats()
-        bcm_farness_all(self.h, make_options(lanes, flags, blocks, threads, wait_limit_ns, grid_lanes),
+        bcm_farness_all(self.h, make_options(lanes, flags, blocks, threads, wait_limit_ns, grid_lanes, 0, pull_div),
                         far, reach, st)
         return far[:self.n], reach[:self.n], st.as_dict()

@@ -148,6 +148,7 @@ struct Aux {
     uint32_t gcnt[1024];
     uint32_t glist_n[2];
     uint32_t glog_n;
+    uint32_t gchunk[2];
 };
 
 }  // namespace bcm
@@ -166,6 +167,8 @@ struct bcm_graph {
     uint32_t* d_xlo = nullptr;
     uint32_t* d_xhi = nullptr;
     uint32_t* d_comp = nullptr;    // component / SCC label, smallest-member order
+    uint32_t* d_rrp = nullptr;     // directed: in-arcs CSR
+    uint32_t* d_rcol = nullptr;
     uint32_t n_comp = 0;
     bool preprocessed = false;
     Aux* d_aux = nullptr;
@@ -182,6 +185,7 @@ constexpr uint64_t kDefaultLimitNs = 20ull * 1000 * 1000 * 1000;
 
 struct Cfg {
     int W, threads, blocks, grid_W, grid_blocks;
+    uint32_t pull_div;
     uint64_t heavy_words;
     uint64_t limit_ns;
     uint32_t flags;
@@ -206,7 +210,7 @@ bcm_status resolve(bcm_graph* g, const bcm_options* opt, Cfg* c) {
     c->blocks = o.blocks ? (int)o.blocks : maxb;
     if (c->blocks > maxb) c->blocks = maxb;
     c->limit_ns = o.wait_limit_ns ? o.wait_limit_ns : kDefaultLimitNs;
-    uint32_t glanes = o.grid_lanes ? o.grid_lanes : 256;
+    uint32_t glanes = o.grid_lanes ? o.grid_lanes : 128;
     if (glanes != 64 && glanes != 128 && glanes != 256)
         return fail(BCM_ERR_UNSUPPORTED, "grid_lanes must be 64, 128 or 256 (got %u)", glanes);
     c->grid_W = (int)(glanes / 64);
@@ -214,6 +218,7 @@ bcm_status resolve(bcm_graph* g, const bcm_options* opt, Cfg* c) {
     if (gb < 1) return fail(BCM_ERR_CUDA, "grid wave kernel does not fit on an SM");
     c->grid_blocks = gb;
     c->heavy_words = o.heavy_words ? o.heavy_words : (uint64_t)gb * 16 * 16;   // 16 entries per warp
+    c->pull_div = (c->flags & BCM_NO_PULL) ? 0u : o.pull_div;   // 0: per-mode default below
     if ((c->flags & BCM_CTA_ONLY) && (c->flags & BCM_GRID_ONLY))
         return fail(BCM_ERR_INVALID, "BCM_CTA_ONLY and BCM_GRID_ONLY exclude each other");
     return BCM_OK;
@@ -313,8 +318,19 @@ bcm_status preprocess(bcm_graph* g, double* ms) {
             }
         } else {
             uint32_t nscc = 0;
-            int rc = launch_scc_bounds(g->d_rp, g->d_col, n, g->m, g->d_comp, g->d_xlo, g->d_xhi, &nscc, d_scr,
-                                       scratch - 1024, d_err, s);
+            if (!g->d_rrp) {
+                if (cudaMalloc(&g->d_rrp, ((size_t)n + 1) * 4) != cudaSuccess ||
+                    cudaMalloc(&g->d_rcol, (g->m ? g->m : 1) * 4) != cudaSuccess) {
+                    st = fail(BCM_ERR_OOM, "in-arc CSR allocation");
+                    break;
+                }
+            }
+            if (launch_reverse_csr(g->d_rp, g->d_col, n, g->m, g->d_rrp, g->d_rcol, d_scr, scratch - 1024, s)) {
+                st = fail(BCM_ERR_CUDA, "in-arc CSR: %s", cudaGetErrorString(cudaGetLastError()));
+                break;
+            }
+            int rc = launch_scc_bounds(g->d_rp, g->d_col, g->d_rrp, g->d_rcol, n, g->m, g->d_comp, g->d_xlo,
+                                       g->d_xhi, &nscc, d_scr, scratch - 1024, d_err, s);
             if (rc == -2) { st = fail(BCM_ERR_UNSUPPORTED, "directed preprocessing is not available"); break; }
             if (rc) { st = fail(BCM_ERR_CUDA, "SCC kernels: %s", cudaGetErrorString(cudaGetLastError())); break; }
             g->n_comp = nscc;
@@ -353,6 +369,8 @@ WaveParams base_params(bcm_graph* g, const Cfg& c) {
     p.g.order = g->d_order;
     p.g.xlo = g->d_xlo;
     p.g.xhi = g->d_xhi;
+    p.g.rrp = g->directed ? g->d_rrp : g->d_rp;
+    p.g.rcol = g->directed ? g->d_rcol : g->d_col;
     p.footnote = (!g->directed && !(c.flags & BCM_NO_FOOTNOTE)) ? 1u : 0u;
     Aux* a = g->d_aux;
     p.head = &a->head;
@@ -374,6 +392,7 @@ WaveParams base_params(bcm_graph* g, const Cfg& c) {
     p.gcnt = a->gcnt;
     p.glist_n = a->glist_n;
     p.glog_n = &a->glog_n;
+    p.gchunk = a->gchunk;
     return p;
 }
 
@@ -409,7 +428,10 @@ void fill_stats(bcm_stats* s, const unsigned long long* st, uint64_t launches, d
 }
 
 // Runs the wave kernels.  exhaustive: every source, no cut; else top-k.
-struct RunTimes { double kernel_ms = 0, seed_ms = 0, wave_ms = 0; };
+struct RunTimes {
+    double kernel_ms = 0, seed_ms = 0, wave_ms = 0;
+    unsigned long long grid[ST_COUNT] = {0};
+};
 
 bcm_status run_waves(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, unsigned long long* stats_out,
                      unsigned long long* wave_stats_out, RunTimes* times) {
@@ -452,6 +474,9 @@ bcm_status run_waves(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, un
         if (!(c.flags & BCM_CTA_ONLY)) {
             p.max_grid_waves = 0xffffffffu;
             p.heavy_words = (exhaustive || (c.flags & BCM_GRID_ONLY)) ? 0 : c.heavy_words;
+            // defaults measured on the Chung-Lu workloads: top-k grid waves
+            // pull nearly every level, exhaustive ones only the dense ones
+            p.pull_div = (c.flags & BCM_NO_PULL) ? 0u : (c.pull_div ? c.pull_div : (exhaustive ? 16u : 64u));
             rc = launch_grid_waves(p, c.grid_W, c.grid_blocks, 512, s);
         }
         cudaEventRecord(em, s);
@@ -486,6 +511,7 @@ bcm_status run_waves(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, un
     times->kernel_ms = t;
     times->seed_ms = t0m;
     times->wave_ms = tm1;
+    for (int i = 0; i < ST_COUNT; ++i) times->grid[i] = seed_st[i];
     if (herr) {
         // a timed-out run may leave words set: do not reuse the region
         region_release(g->slots, false);
@@ -628,6 +654,8 @@ bcm_status bcm_graph_destroy(bcm_graph_t g) {
     cudaFree(g->d_plain);
     cudaFree(g->d_far);
     cudaFree(g->d_reach);
+    cudaFree(g->d_rrp);
+    cudaFree(g->d_rcol);
     region_release(g->slots, true);
     delete g;
     return BCM_OK;
@@ -702,6 +730,9 @@ bcm_status bcm_topk(bcm_graph_t g, uint32_t k, const bcm_options* opt, uint32_t*
         stats->seed_ms = rt.seed_ms;
         stats->wave_ms = rt.wave_ms;
         stats->wave_bytes = (c.flags & BCM_PLAIN) ? 0 : wave_alg_bytes(wv, wv[ST_COMPLETED] + wv[ST_CUT]);
+        stats->grid_waves = rt.grid[ST_WAVES];
+        stats->grid_levels = rt.grid[ST_LEVELS];
+        stats->grid_bytes = (c.flags & BCM_PLAIN) ? 0 : wave_alg_bytes(rt.grid, rt.grid[ST_COMPLETED] + rt.grid[ST_CUT]);
     }
     return BCM_OK;
 }
@@ -733,6 +764,9 @@ bcm_status bcm_farness_all(bcm_graph_t g, const bcm_options* opt, uint64_t* farn
         stats->seed_ms = rt.seed_ms;
         stats->wave_ms = rt.wave_ms;
         stats->wave_bytes = wave_alg_bytes(wv, wv[ST_COMPLETED] + wv[ST_CUT]);
+        stats->grid_waves = rt.grid[ST_WAVES];
+        stats->grid_levels = rt.grid[ST_LEVELS];
+        stats->grid_bytes = wave_alg_bytes(rt.grid, rt.grid[ST_COMPLETED] + rt.grid[ST_CUT]);
     }
     return BCM_OK;
 }

@@ -34,6 +34,8 @@ struct GraphDev {
     const uint32_t* order;   // [n] vertices by (degree desc, id asc)
     const uint32_t* xlo;     // [n] r(v) (undirected) or alpha(v)
     const uint32_t* xhi;     // [n] r(v) (undirected) or omega(v)
+    const uint32_t* rrp;     // in-arcs CSR (the graph itself when undirected)
+    const uint32_t* rcol;
 };
 
 // Per-slot working memory of one MS-BFS wave with W words (64W sources) per
@@ -65,8 +67,10 @@ struct WaveParams {
     uint32_t* gcnt;          // [2][2][256] per-lane level counters (gamma, degree sum)
     uint32_t* glist_n;       // [2] frontier list sizes
     uint32_t* glog_n;        // [1] cleared-word log size
+    uint32_t* gchunk;        // [2] chunk counters of the frontier lists
     uint32_t max_grid_waves;  // grid kernel: at most this many waves
     uint64_t heavy_words;   // grid kernel: a wave with fewer frontier words in total is light
+    uint32_t pull_div;      // grid kernel: pull a level whose frontier holds >= n*W/pull_div words (0: never)
 };
 
 // ---- preproc.cu
@@ -96,8 +100,10 @@ int launch_relabel(uint32_t* parent, const uint32_t* rank, uint32_t n, cudaStrea
 // ---- scc.cu
 struct SccResult { uint32_t n_scc; };
 size_t scc_scratch_bytes(uint32_t n, uint64_t m);
-int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, uint32_t n, uint64_t m,
-                      uint32_t* comp, uint32_t* xlo, uint32_t* xhi, uint32_t* n_scc_host,
+int launch_reverse_csr(const uint32_t* rp, const uint32_t* col, uint32_t n, uint64_t m, uint32_t* rrp,
+                       uint32_t* rcol, void* scratch, size_t scratch_bytes, cudaStream_t s);
+int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, const uint32_t* rrp, const uint32_t* rcol,
+                      uint32_t n, uint64_t m, uint32_t* comp, uint32_t* xlo, uint32_t* xhi, uint32_t* n_scc_host,
                       void* scratch, size_t scratch_bytes, int* err, cudaStream_t s);
 
 // ---- msbfs.cu

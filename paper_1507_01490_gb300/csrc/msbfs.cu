@@ -50,57 +50,157 @@ __device__ __forceinline__ SlotPtrs slot_ptrs(char* base, u32 n, int W) {
     return s;
 }
 
+// Counters of the expansion loops, per thread (kept small: they live in
+// registers through the hot loops).  Rare events (completions, cuts, waves,
+// levels, cleared words) go to a per-block shared array instead.
 struct LocalStats {
-    u64 mvis = 0, disc = 0, entries = 0, arcwords = 0, discwords = 0, cleared = 0;
-    u64 completed = 0, cut = 0, waves = 0, levels = 0, maxlevel = 0;
+    u64 mvis = 0;
+    u32 disc = 0, entries = 0, arcwords = 0, discwords = 0;
 };
 
-__device__ inline void flush_stats(const LocalStats& s, unsigned long long* g) {
-    // warp-reduce then one atomic per warp and counter
-    u64 v[ST_COUNT] = {s.mvis, s.disc, s.completed, s.cut, s.waves, s.levels, s.maxlevel,
-                       s.entries, s.arcwords, s.discwords, s.cleared};
+// per-block counters of rare events, indexed by Stat
+struct BlockStats { unsigned long long v[ST_COUNT]; };
+
+__device__ __forceinline__ void bstat_init(BlockStats& b) {
+    for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x) b.v[i] = 0;
+}
+__device__ __forceinline__ void bstat_add(BlockStats& b, int i, u64 x) { atomicAdd(&b.v[i], (unsigned long long)x); }
+__device__ __forceinline__ void bstat_max(BlockStats& b, int i, u64 x) { atomicMax(&b.v[i], (unsigned long long)x); }
+
+// Warp-reduces the per-thread counters, then one global atomic per counter
+// per warp; thread 0 adds the block's rare-event counters.  Call with the
+// whole block, after a __syncthreads that follows the last bstat update.
+__device__ inline void flush_stats(const LocalStats& s, const BlockStats& b, unsigned long long* g) {
+    u64 v[5] = {s.mvis, s.disc, s.entries, s.arcwords, s.discwords};
+    const int idx[5] = {ST_MVIS, ST_DISC, ST_ENTRIES, ST_ARCWORDS, ST_DISCWORDS};
 #pragma unroll
-    for (int i = 0; i < ST_COUNT; ++i) {
+    for (int i = 0; i < 5; ++i) {
         u64 x = v[i];
-        for (int o = 16; o; o >>= 1) {
-            u64 t = __shfl_xor_sync(0xffffffffu, x, o);
-            x = (i == ST_MAXLEVEL) ? (t > x ? t : x) : x + t;
-        }
-        if ((threadIdx.x & 31) == 0 && x) {
-            if (i == ST_MAXLEVEL) atomicMax(&g[i], x);
-            else atomicAdd(&g[i], x);
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0 && x) atomicAdd(&g[idx[i]], x);
+    }
+    if (threadIdx.x == 0) {
+        const int rare[6] = {ST_COMPLETED, ST_CUT, ST_WAVES, ST_LEVELS, ST_CLEARED, ST_MAXLEVEL};
+        for (int i = 0; i < 6; ++i) {
+            u64 x = b.v[rare[i]];
+            if (!x) continue;
+            if (rare[i] == ST_MAXLEVEL) atomicMax(&g[rare[i]], x);
+            else atomicAdd(&g[rare[i]], x);
         }
     }
 }
 
-// ------------------------------------------------------------ push step
-// Lanes F of word g reach x.  Returns bit 0: x's F-next word was empty
-// (append it to the next frontier); bit 1: x's vis word was empty (append it
-// to the clear log).  Discoveries are counted per lane in cg (gamma) and cs
-// (sum of deg, minus one under the undirected footnote).
-template <int W>
-__device__ __forceinline__ u32 push_word(const u32* __restrict__ rp, u64* vis, u64* Fnext, u32* cg, u32* cs,
-                                         u32 foot, u32 x, u64 F, u32 g, LocalStats& st) {
-    u32 word = x * W + g;
-    u64 nb = F & ~__ldcg(&vis[word]);
-    if (!nb) return 0;
-    u64 old = atomicOr(&vis[word], nb);
-    u32 fl = (old == 0) ? 2u : 0u;
-    nb &= ~old;
-    if (!nb) return fl;
-    u64 oldF = atomicOr(&Fnext[word], nb);
-    if (oldF == 0) { fl |= 1u; st.discwords++; }
-    u32 degp = __ldg(&rp[x + 1]) - __ldg(&rp[x]) - foot;
-    st.disc += __popcll(nb);
-    u32* cgg = cg + g * 64;
-    u32* csg = cs + g * 64;
-    while (nb) {
-        int j = __ffsll((long long)nb) - 1;
-        nb &= nb - 1;
-        atomicAdd(&cgg[j], 1u);
-        atomicAdd(&csg[j], degp);
+// ------------------------------------------------------- staged appends
+// Frontier and clear-log appends go first to a per-warp staging area in
+// shared memory and reach the list with one counter reservation per flush:
+// a dense level appends millions of words, and one global counter taking an
+// atomic per warp step serialises them.
+struct WarpQueue {
+    u32* sbuf;      // this warp's staging area (cap entries)
+    u32* dst;       // the list
+    u32* counter;   // its length
+    u32 cap;
+    u32 n;          // staged entries (the same in every lane)
+    __device__ __forceinline__ void push(bool want, u32 item) {
+        const u32 m = __ballot_sync(0xffffffffu, want);
+        if (want) sbuf[n + __popc(m & lanemask_lt())] = item;
+        n += __popc(m);
     }
-    return fl;
+    __device__ __forceinline__ void flush() {
+        if (n == 0) return;
+        __syncwarp();
+        u32 base = 0;
+        if ((threadIdx.x & 31) == 0) base = atomicAdd(counter, n);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (u32 i = threadIdx.x & 31; i < n; i += 32) dst[base + i] = sbuf[i];
+        __syncwarp();
+        n = 0;
+    }
+    // room for one more step of up to `need` entries
+    __device__ __forceinline__ void reserve(u32 need) {
+        if (n + need > cap) flush();
+    }
+};
+
+// ------------------------------------------------------------ push step
+// Lanes F of word g reach x: the bits of F not yet in vis[x] are x's
+// discoveries at this level.  push_begin loads what the step needs;
+// push_end issues the atomics.  Splitting them lets a thread keep two arcs'
+// memory operations in flight at once.
+struct Push {
+    u32 x, g, word, r0, r1;
+    u64 F, nb;
+    u32 fl;          // bit 0: word enters the next frontier; bit 1: vis word was empty (log it)
+    u32 degp;
+};
+
+template <int W>
+__device__ __forceinline__ void push_load(const u32* __restrict__ col, u32 e, u64 F, u32 g, Push& q) {
+    q.x = __ldg(&col[e]);
+    q.F = F;
+    q.g = g;
+}
+
+template <int W>
+__device__ __forceinline__ void push_check(const u32* __restrict__ rp, const u64* vis, Push& q) {
+    q.word = q.x * W + q.g;
+    q.nb = q.F & ~__ldcg(&vis[q.word]);
+    q.fl = 0;
+    q.degp = 0;
+    if (q.nb) {
+        q.r0 = __ldg(&rp[q.x]);
+        q.r1 = __ldg(&rp[q.x + 1]);
+    }
+}
+
+__device__ __forceinline__ void push_vis(u64* vis, Push& q, u64& old) {
+    old = q.nb ? atomicOr(&vis[q.word], q.nb) : ~0ull;
+}
+
+__device__ __forceinline__ void push_next(u64* Fnext, Push& q, u64 old, u32 foot, LocalStats& st) {
+    if (!q.nb) return;
+    q.fl = (old == 0) ? 2u : 0u;
+    q.nb &= ~old;
+    if (!q.nb) return;
+    u64 oldF = atomicOr(&Fnext[q.word], q.nb);
+    if (oldF == 0) { q.fl |= 1u; st.discwords++; }
+    q.degp = q.r1 - q.r0 - foot;
+    st.disc += __popcll(q.nb);
+}
+
+// Per-lane counts of this step's discoveries, summed across the warp with
+// ballots and reductions (one shared-memory update per lane bit present in
+// the warp, not one per discovery): cg[lane] += how many vertices the lane
+// discovered, cs[lane] += the sum of their degrees (minus the footnote).
+__device__ __forceinline__ void warp_count(u64 nb, u32 degp, u32 g, u32* cg, u32* cs) {
+    const u32 lane = threadIdx.x & 31;
+    u32 active = __ballot_sync(0xffffffffu, nb != 0);
+    while (active) {
+        const int l0 = __ffs(active) - 1;
+        const u32 g0 = __shfl_sync(0xffffffffu, g, l0);
+        const bool mine = nb != 0 && g == g0;
+        active &= ~__ballot_sync(0xffffffffu, mine);
+        const u64 m = mine ? nb : 0ull;
+        u64 bits = ((u64)__reduce_or_sync(0xffffffffu, (u32)(m >> 32)) << 32) |
+                   (u64)__reduce_or_sync(0xffffffffu, (u32)m);
+        while (bits) {
+            const int j = __ffsll((long long)bits) - 1;
+            bits &= bits - 1;
+            const bool has = (m >> j) & 1ull;
+            const u32 c = __popc(__ballot_sync(0xffffffffu, has));
+            const u32 sd = __reduce_add_sync(0xffffffffu, has ? degp : 0u);
+            if (lane == 0) {
+                atomicAdd(&cg[g0 * 64 + j], c);
+                atomicAdd(&cs[g0 * 64 + j], sd);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void push_finish(const Push& q, u32* cg, u32* cs, WarpQueue& nq, WarpQueue& lq) {
+    warp_count(q.nb, q.degp, q.g, cg, cs);
+    nq.push(q.fl & 1u, q.word);
+    lq.push(q.fl & 2u, q.word);
 }
 
 // Level 0: lane j's frontier is its source.  One warp per source, arcs in
@@ -108,46 +208,65 @@ __device__ __forceinline__ u32 push_word(const u32* __restrict__ rp, u64* vis, u
 template <int W>
 __device__ inline void expand_sources(const GraphDev& G, const u32* s_src, const u32* s_alive32, int L,
                                       u64* vis, u64* Fnext, u32* cg, u32* cs, u32 foot,
-                                      u32* next_list, u32* next_n, u32* clog, u32* log_n,
-                                      u32 wid, u32 nw, LocalStats& st) {
+                                      WarpQueue& nq, WarpQueue& lq, u32 wid, u32 nw, LocalStats& st) {
     const u32 lane = threadIdx.x & 31;
     for (u32 j = wid; j < (u32)L; j += nw) {
         if (!((s_alive32[j >> 5] >> (j & 31)) & 1u)) continue;
         u32 u = s_src[j], g = j >> 6;
         u64 F = 1ull << (j & 63);
         u32 beg = __ldg(&G.rp[u]), end = __ldg(&G.rp[u + 1]);
+        bool first = false;
         if (lane == 0) {
-            u64 old = atomicOr(&vis[u * W + g], F);
-            if (old == 0) clog[atomicAdd(log_n, 1u)] = u * W + g;
+            first = atomicOr(&vis[u * W + g], F) == 0;
             st.mvis += end - beg;
             st.arcwords += end - beg;
         }
+        lq.reserve(32);
+        lq.push(first, u * W + g);
         __syncwarp();
         for (u32 e0 = beg; e0 < end; e0 += 32) {
+            nq.reserve(32);
+            lq.reserve(32);
             u32 e = e0 + lane;
-            u32 fl = 0, word = 0;
+            Push q;
+            q.nb = 0; q.fl = 0; q.degp = 0; q.g = g; q.word = 0;
             if (e < end) {
-                u32 x = __ldg(&G.col[e]);
-                word = x * W + g;
-                fl = push_word<W>(G.rp, vis, Fnext, cg, cs, foot, x, F, g, st);
+                push_load<W>(G.col, e, F, g, q);
+                push_check<W>(G.rp, vis, q);
+                u64 old;
+                push_vis(vis, q, old);
+                push_next(Fnext, q, old, foot, st);
             }
-            warp_append(fl & 1u, word, next_list, next_n);
-            warp_append(fl & 2u, word, clog, log_n);
+            push_finish(q, cg, cs, nq, lq);
         }
     }
 }
 
-// Level >= 1: frontier words from `list`; each warp takes 32 entries, forms
-// the exclusive scan of their degrees, and walks the combined arc range 32
-// arcs at a time (balanced across high- and low-degree entries).
+// Level >= 1: frontier words from `list`.  Warps take chunks of 32 entries
+// from a shared counter (so a chunk holding a high-degree vertex does not
+// hold back the others), form the exclusive scan of the chunk's degrees and
+// walk the combined arc range 64 arcs at a time, two per thread.
 template <int W>
 __device__ inline void expand_entries(const GraphDev& G, const u32* list, u32 cnt, u64* Fcur,
                                       const u32* s_alive32, u64* vis, u64* Fnext, u32* cg, u32* cs,
-                                      u32 foot, u32* next_list, u32* next_n, u32* clog, u32* log_n,
-                                      u32 wid, u32 nw, LocalStats& st) {
+                                      u32 foot, WarpQueue& nq, WarpQueue& lq, u32* chunk_ctr, u32 nw,
+                                      LocalStats& st) {
     const u32 lane = threadIdx.x & 31;
-    for (u32 base = wid * 32; base < cnt; base += nw * 32) {
-        u32 e = base + lane;
+    // entries taken per counter reservation: 32 when the frontier is small,
+    // up to 256 when it is large enough to keep every warp busy anyway
+    u32 grab = cnt / (nw * 8u);
+    grab = grab < 32u ? 32u : (grab > 256u ? 256u : (grab & ~31u));
+    u32 base = 0, lim = 0;
+    for (;;) {
+        if (base >= lim) {
+            u32 b = 0;
+            if (lane == 0) b = atomicAdd(chunk_ctr, grab);
+            base = __shfl_sync(0xffffffffu, b, 0);
+            lim = base + grab < cnt ? base + grab : cnt;
+            if (base >= cnt) break;
+        }
+        const u32 e = base + lane;
+        base += 32;
         u32 g = 0, beg = 0, deg = 0;
         u64 F = 0;
         if (e < cnt) {
@@ -171,29 +290,128 @@ __device__ inline void expand_entries(const GraphDev& G, const u32* list, u32 cn
             u32 t = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= (u32)o) incl += t;
         }
-        u32 total = __shfl_sync(0xffffffffu, incl, 31);
-        u32 excl = incl - deg;
-        for (u32 t0 = 0; t0 < total; t0 += 32) {
-            u32 idx = t0 + lane;
-            int owner = 0;
+        const u32 total = __shfl_sync(0xffffffffu, incl, 31);
+        const u32 excl = incl - deg;
+        for (u32 t0 = 0; t0 < total; t0 += 64) {
+            Push q[2];
+            bool v[2];
 #pragma unroll
-            for (int step = 16; step; step >>= 1) {
-                u32 ex = __shfl_sync(0xffffffffu, excl, owner + step);
-                if (ex <= idx) owner += step;
+            for (int h = 0; h < 2; ++h) {
+                const u32 idx = t0 + 32 * h + lane;
+                int owner = 0;
+#pragma unroll
+                for (int step = 16; step; step >>= 1) {
+                    u32 ex = __shfl_sync(0xffffffffu, excl, owner + step);
+                    if (ex <= idx) owner += step;
+                }
+                const u32 o_beg = __shfl_sync(0xffffffffu, beg, owner);
+                const u32 o_excl = __shfl_sync(0xffffffffu, excl, owner);
+                const u64 o_F = __shfl_sync(0xffffffffu, F, owner);
+                const u32 o_g = __shfl_sync(0xffffffffu, g, owner);
+                v[h] = idx < total;
+                q[h].nb = 0; q[h].fl = 0; q[h].degp = 0; q[h].g = o_g; q[h].word = 0;
+                if (v[h]) push_load<W>(G.col, o_beg + idx - o_excl, o_F, o_g, q[h]);
             }
-            u32 o_beg = __shfl_sync(0xffffffffu, beg, owner);
-            u32 o_excl = __shfl_sync(0xffffffffu, excl, owner);
-            u64 o_F = __shfl_sync(0xffffffffu, F, owner);
-            u32 o_g = __shfl_sync(0xffffffffu, g, owner);
-            u32 fl = 0, word = 0;
-            if (idx < total) {
-                u32 x = __ldg(&G.col[o_beg + idx - o_excl]);
-                word = x * W + o_g;
-                fl = push_word<W>(G.rp, vis, Fnext, cg, cs, foot, x, o_F, o_g, st);
-            }
-            warp_append(fl & 1u, word, next_list, next_n);
-            warp_append(fl & 2u, word, clog, log_n);
+            nq.reserve(64);
+            lq.reserve(64);
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (v[h]) push_check<W>(G.rp, vis, q[h]);
+            u64 old[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) push_vis(vis, q[h], old[h]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) push_next(Fnext, q[h], old[h], foot, st);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) push_finish(q[h], cg, cs, nq, lq);
         }
+    }
+}
+
+// Level >= 1 by pull, for a frontier that covers much of the graph: each
+// vertex x whose vis words miss live lanes ("pending") ORs in the frontier
+// words of its in-neighbours, stopping once every pending lane is found.
+// A vertex is owned by one thread, so vis/F-next are written without
+// atomics.  The frontier words themselves are cleared afterwards
+// (pull_retire), once no thread can still be reading them.
+template <int W>
+__device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32* s_alive32, u64* vis, u64* Fnext,
+                                  u32* cg, u32* cs, u32 foot, WarpQueue& nq, WarpQueue& lq, u32 gw, u32 gnw,
+                                  LocalStats& st) {
+    const u32 lane = threadIdx.x & 31;
+    u64 alive[W];
+#pragma unroll
+    for (int g = 0; g < W; ++g) alive[g] = ((u64)s_alive32[2 * g + 1] << 32) | s_alive32[2 * g];
+    for (u32 x0 = gw * 32; x0 < G.n; x0 += gnw * 32) {
+        const u32 x = x0 + lane;
+        u64 nb[W], v0[W];
+#pragma unroll
+        for (int g = 0; g < W; ++g) { nb[g] = 0; v0[g] = 0; }
+        u32 degp = 0;
+        if (x < G.n) {
+            u64 pend[W];
+            bool any = false;
+#pragma unroll
+            for (int g = 0; g < W; ++g) {
+                v0[g] = __ldcg(&vis[(size_t)x * W + g]);
+                pend[g] = alive[g] & ~v0[g];
+                any = any || pend[g] != 0;
+            }
+            if (any) {
+                const u32 b = __ldg(&G.rrp[x]), e = __ldg(&G.rrp[x + 1]);
+                u64 acc[W];
+#pragma unroll
+                for (int g = 0; g < W; ++g) acc[g] = 0;
+                u32 i = b;
+                for (; i < e; ++i) {
+                    const u32 u = __ldg(&G.rcol[i]);
+                    bool done = true;
+#pragma unroll
+                    for (int g = 0; g < W; ++g) {
+                        if (pend[g] & ~acc[g]) acc[g] |= __ldcg(&Fcur[(size_t)u * W + g]);
+                        done = done && !(pend[g] & ~acc[g]);
+                    }
+                    if (done) { ++i; break; }
+                }
+                st.arcwords += i - b;
+                degp = __ldg(&G.rp[x + 1]) - __ldg(&G.rp[x]) - foot;
+#pragma unroll
+                for (int g = 0; g < W; ++g) {
+                    nb[g] = acc[g] & pend[g];
+                    if (nb[g]) {
+                        vis[(size_t)x * W + g] = v0[g] | nb[g];
+                        Fnext[(size_t)x * W + g] = nb[g];
+                        st.disc += __popcll(nb[g]);
+                        st.discwords++;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < W; ++g) {
+            nq.reserve(32);
+            lq.reserve(32);
+            warp_count(nb[g], degp, (u32)g, cg, cs);
+            nq.push(nb[g] != 0, x * W + g);
+            lq.push(nb[g] != 0 && v0[g] == 0, x * W + g);
+        }
+    }
+}
+
+// After a pulled level: clear the frontier words just consumed and count the
+// arcs a push would have scanned for them (m_vis is the push-equivalent
+// count whichever direction ran).
+template <int W>
+__device__ inline void pull_retire(const GraphDev& G, const u32* list, u32 cnt, u64* Fcur, const u32* s_alive32,
+                                   u32 gtid, u32 gthreads, LocalStats& st) {
+    for (u32 i = gtid; i < cnt; i += gthreads) {
+        const u32 word = __ldcg(&list[i]);
+        const u32 u = word / W, g = word - u * W;
+        u64 F = __ldcg(&Fcur[word]);
+        Fcur[word] = 0;
+        F &= ((u64)s_alive32[2 * g + 1] << 32) | s_alive32[2 * g];
+        st.entries++;
+        if (F) st.mvis += (u64)__popcll(F) * (__ldg(&G.rp[u + 1]) - __ldg(&G.rp[u]));
     }
 }
 
@@ -226,7 +444,7 @@ __device__ inline void flush_completions(const WaveParams& p, const u32* cid, co
 
 // --------------------------------------------------------- per-CTA waves
 template <int W, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_wave_cta(WaveParams p) {
+__global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREADS) : 1) k_wave_cta(WaveParams p) {
     constexpr int L = 64 * W;
     constexpr int NWARP = THREADS / 32;
     static_assert(THREADS >= L, "one thread per lane");
@@ -234,8 +452,11 @@ __global__ void __launch_bounds__(THREADS) k_wave_cta(WaveParams p) {
     __shared__ u64 s_f[L];
     __shared__ u32 s_cg[L], s_cs[L];
     __shared__ u32 s_alive32[2 * W];
-    __shared__ u32 s_ln[2], s_logn, s_base, s_nc, s_stop;
+    __shared__ u32 s_ln[2], s_logn, s_base, s_nc, s_stop, s_chunk;
     __shared__ ThrCache s_thr;
+    __shared__ BlockStats s_bst;
+    constexpr u32 QCAP = 4096 / NWARP;
+    __shared__ u32 s_stage[NWARP * 2 * QCAP];
     __shared__ u32 s_cid[L], s_cr[L];
     __shared__ u64 s_cf[L];
 
@@ -247,6 +468,7 @@ __global__ void __launch_bounds__(THREADS) k_wave_cta(WaveParams p) {
         s_thr.valid = 0; s_thr.N = 0; s_thr.F = 1; s_thr.id = 0;
         s_nc = 0; s_logn = 0; s_ln[0] = 0; s_ln[1] = 0;
     }
+    bstat_init(s_bst);
     __syncthreads();
 
     for (;;) {
@@ -257,7 +479,7 @@ __global__ void __launch_bounds__(THREADS) k_wave_cta(WaveParams p) {
         __syncthreads();
         if (s_stop) break;
         const u32 base = s_base;
-        if (tid == 0) st.waves++;
+        if (tid == 0) bstat_add(s_bst, ST_WAVES, 1);
         if (tid < L) {
             bool alive = false;
             s_cg[tid] = 0;
@@ -270,7 +492,7 @@ __global__ void __launch_bounds__(THREADS) k_wave_cta(WaveParams p) {
                 if (deg == 0) {          // R(v) = {v}: r = 1, f = 0
                     u32 c = atomicAdd(&s_nc, 1u);
                     s_cid[c] = v; s_cf[c] = 0; s_cr[c] = 1;
-                    st.completed++;
+                    bstat_add(s_bst, ST_COMPLETED, 1);
                 } else {
                     alive = true;
                 }
@@ -285,14 +507,17 @@ __global__ void __launch_bounds__(THREADS) k_wave_cta(WaveParams p) {
 
         u32 d = 0, cur = 0;
         for (;;) {
-            if (!p.exhaustive && tid == 0) read_threshold(p.topk.thr, s_thr);
+            if (tid == 0) {
+                if (!p.exhaustive) read_threshold(p.topk.thr, s_thr);
+                s_chunk = 0;
+            }
             __syncthreads();
             if (tid < L) {   // stopping rule at level d, before Gamma_d is expanded
                 bool a = (s_alive32[tid >> 5] >> lane) & 1u;
                 if (a && !p.exhaustive &&
                     bfscut_stops(s_f[tid], s_gt[tid], d, s_nd[tid], s_xlo[tid], s_xhi[tid], s_src[tid], s_thr)) {
                     a = false;
-                    st.cut++;
+                    bstat_add(s_bst, ST_CUT, 1);
                 }
                 u32 m = __ballot_sync(0xffffffffu, a);
                 if (lane == 0) s_alive32[tid >> 5] = m;
@@ -304,12 +529,18 @@ __global__ void __launch_bounds__(THREADS) k_wave_cta(WaveParams p) {
             if (!any) break;
 
             u64* Fnext = S.F[cur ^ 1];
-            if (d == 0)
-                expand_sources<W>(G, s_src, s_alive32, L, S.vis, Fnext, s_cg, s_cs, p.footnote,
-                                  S.list[cur ^ 1], &s_ln[cur ^ 1], S.clog, &s_logn, wid, NWARP, st);
-            else
-                expand_entries<W>(G, S.list[cur], s_ln[cur], S.F[cur], s_alive32, S.vis, Fnext, s_cg, s_cs,
-                                  p.footnote, S.list[cur ^ 1], &s_ln[cur ^ 1], S.clog, &s_logn, wid, NWARP, st);
+            {
+                WarpQueue nq{&s_stage[(2 * wid) * QCAP], S.list[cur ^ 1], &s_ln[cur ^ 1], QCAP, 0};
+                WarpQueue lq{&s_stage[(2 * wid + 1) * QCAP], S.clog, &s_logn, QCAP, 0};
+                if (d == 0)
+                    expand_sources<W>(G, s_src, s_alive32, L, S.vis, Fnext, s_cg, s_cs, p.footnote, nq, lq, wid,
+                                      NWARP, st);
+                else
+                    expand_entries<W>(G, S.list[cur], s_ln[cur], S.F[cur], s_alive32, S.vis, Fnext, s_cg, s_cs,
+                                      p.footnote, nq, lq, &s_chunk, NWARP, st);
+                nq.flush();
+                lq.flush();
+            }
             __syncthreads();
             if (tid < L) {   // level d+1 is known: gamma_{d+1} and its degree sum
                 bool a = (s_alive32[tid >> 5] >> lane) & 1u;
@@ -319,7 +550,7 @@ __global__ void __launch_bounds__(THREADS) k_wave_cta(WaveParams p) {
                         u32 c = atomicAdd(&s_nc, 1u);
                         s_cid[c] = s_src[tid]; s_cf[c] = s_f[tid]; s_cr[c] = s_nd[tid];
                         a = false;
-                        st.completed++;
+                        bstat_add(s_bst, ST_COMPLETED, 1);
                     } else {
                         s_nd[tid] += gam;
                         s_f[tid] += (u64)(d + 1) * gam;
@@ -340,8 +571,8 @@ __global__ void __launch_bounds__(THREADS) k_wave_cta(WaveParams p) {
             ++d;
         }
         if (tid == 0) {
-            st.levels += d;
-            if (d > st.maxlevel) st.maxlevel = d;
+            bstat_add(s_bst, ST_LEVELS, d);
+            bstat_max(s_bst, ST_MAXLEVEL, d);
         }
         // the wave's footprint: every word whose vis became non-zero
         const u32 nlog = s_logn;
@@ -351,11 +582,12 @@ __global__ void __launch_bounds__(THREADS) k_wave_cta(WaveParams p) {
             S.F[0][w] = 0;
             S.F[1][w] = 0;
         }
-        if (tid == 0) st.cleared += nlog;
+        if (tid == 0) bstat_add(s_bst, ST_CLEARED, nlog);
         __syncthreads();
         if (tid == 0) { s_logn = 0; s_ln[0] = 0; s_ln[1] = 0; }
     }
-    flush_stats(st, p.stats);
+    __syncthreads();
+    flush_stats(st, s_bst, p.stats);
 }
 
 // ------------------------------------------------------------ grid waves
@@ -369,7 +601,7 @@ __global__ void __launch_bounds__(THREADS) k_wave_cta(WaveParams p) {
 // per-CTA kernel continues; exhaustive runs (or max_grid_waves reached) end it
 // too.
 template <int W, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_wave_grid(WaveParams p) {
+__global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREADS) : 1) k_wave_grid(WaveParams p) {
     constexpr int L = 64 * W;
     constexpr int NWARP = THREADS / 32;
     static_assert(THREADS >= L, "one thread per lane");
@@ -379,6 +611,9 @@ __global__ void __launch_bounds__(THREADS) k_wave_grid(WaveParams p) {
     __shared__ u32 s_alive32[2 * W];
     __shared__ u32 s_nc, s_base;
     __shared__ ThrCache s_thr;
+    __shared__ BlockStats s_bst;
+    constexpr u32 QCAP = 4096 / NWARP;
+    __shared__ u32 s_stage[NWARP * 2 * QCAP];
     __shared__ u32 s_cid[L], s_cr[L];
     __shared__ u64 s_cf[L];
 
@@ -391,6 +626,7 @@ __global__ void __launch_bounds__(THREADS) k_wave_grid(WaveParams p) {
     LocalStats st;
     const u32 gw = blockIdx.x * NWARP + wid, gnw = gridDim.x * NWARP;
     if (tid == 0) { s_nc = 0; s_thr.valid = 0; s_thr.N = 0; s_thr.F = 1; s_thr.id = 0; }
+    bstat_init(s_bst);
     bool ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err);
 
     for (u32 wave = 0; ok && wave < p.max_grid_waves; ++wave) {
@@ -411,7 +647,7 @@ __global__ void __launch_bounds__(THREADS) k_wave_grid(WaveParams p) {
                     if (leader) {
                         u32 c = atomicAdd(&s_nc, 1u);
                         s_cid[c] = v; s_cf[c] = 0; s_cr[c] = 1;
-                        st.completed++;
+                        bstat_add(s_bst, ST_COMPLETED, 1);
                     }
                 } else {
                     alive = true;
@@ -428,6 +664,7 @@ __global__ void __launch_bounds__(THREADS) k_wave_grid(WaveParams p) {
 
         u32 d = 0, cur = 0;
         u64 wave_entries = 0;
+        bool pulled = false;
         for (;;) {
             if (!p.exhaustive && tid == 0) read_threshold(p.topk.thr, s_thr);
             __syncthreads();
@@ -436,7 +673,7 @@ __global__ void __launch_bounds__(THREADS) k_wave_grid(WaveParams p) {
                 if (a && !p.exhaustive &&
                     bfscut_stops(s_f[tid], s_gt[tid], d, s_nd[tid], s_xlo[tid], s_xhi[tid], s_src[tid], s_thr)) {
                     a = false;
-                    if (leader) st.cut++;
+                    if (leader) bstat_add(s_bst, ST_CUT, 1);
                 }
                 u32 m = __ballot_sync(0xffffffffu, a);
                 if (lane == 0) s_alive32[tid >> 5] = m;
@@ -450,14 +687,25 @@ __global__ void __launch_bounds__(THREADS) k_wave_grid(WaveParams p) {
             const u32 par = d & 1;
             u32* gcg = p.gcnt + par * 512;
             u32* gcs = gcg + 256;
-            if (d == 0) {
-                expand_sources<W>(G, s_src, s_alive32, L, S.vis, S.F[cur ^ 1], s_cg, s_cs, p.footnote,
-                                  S.list[cur ^ 1], &p.glist_n[cur ^ 1], S.clog, p.glog_n, gw, gnw, st);
-            } else {
-                const u32 cnt = vload(&p.glist_n[cur]);
-                wave_entries += cnt;
-                expand_entries<W>(G, S.list[cur], cnt, S.F[cur], s_alive32, S.vis, S.F[cur ^ 1], s_cg, s_cs,
-                                  p.footnote, S.list[cur ^ 1], &p.glist_n[cur ^ 1], S.clog, p.glog_n, gw, gnw, st);
+            {
+                WarpQueue nq{&s_stage[(2 * wid) * QCAP], S.list[cur ^ 1], &p.glist_n[cur ^ 1], QCAP, 0};
+                WarpQueue lq{&s_stage[(2 * wid + 1) * QCAP], S.clog, p.glog_n, QCAP, 0};
+                if (d == 0) {
+                    expand_sources<W>(G, s_src, s_alive32, L, S.vis, S.F[cur ^ 1], s_cg, s_cs, p.footnote, nq, lq,
+                                      gw, gnw, st);
+                } else {
+                    const u32 cnt = vload(&p.glist_n[cur]);
+                    wave_entries += cnt;
+                    pulled = p.pull_div && (u64)cnt * p.pull_div >= (u64)G.n * W;
+                    if (pulled)
+                        pull_level<W>(G, S.F[cur], s_alive32, S.vis, S.F[cur ^ 1], s_cg, s_cs, p.footnote, nq, lq,
+                                      gw, gnw, st);
+                    else
+                        expand_entries<W>(G, S.list[cur], cnt, S.F[cur], s_alive32, S.vis, S.F[cur ^ 1], s_cg,
+                                          s_cs, p.footnote, nq, lq, &p.gchunk[cur], gnw, st);
+                }
+                nq.flush();
+                lq.flush();
             }
             __syncthreads();
             if (tid < L) {
@@ -466,6 +714,12 @@ __global__ void __launch_bounds__(THREADS) k_wave_grid(WaveParams p) {
                 s_cs[tid] = 0;
             }
             if (!(ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err))) break;
+            if (pulled) {   // every block is past the pull: retire the frontier words
+                pull_retire<W>(G, S.list[cur], vload(&p.glist_n[cur]), S.F[cur], s_alive32,
+                               blockIdx.x * THREADS + tid, gridDim.x * THREADS, st);
+                pulled = false;
+                __syncthreads();
+            }
             if (tid < L) {
                 bool a = (s_alive32[tid >> 5] >> lane) & 1u;
                 if (a) {
@@ -474,7 +728,7 @@ __global__ void __launch_bounds__(THREADS) k_wave_grid(WaveParams p) {
                         if (leader) {
                             u32 c = atomicAdd(&s_nc, 1u);
                             s_cid[c] = s_src[tid]; s_cf[c] = s_f[tid]; s_cr[c] = s_nd[tid];
-                            st.completed++;
+                            bstat_add(s_bst, ST_COMPLETED, 1);
                         }
                         a = false;
                     } else {
@@ -486,10 +740,13 @@ __global__ void __launch_bounds__(THREADS) k_wave_grid(WaveParams p) {
                 u32 m = __ballot_sync(0xffffffffu, a);
                 if (lane == 0) s_alive32[tid >> 5] = m;
             }
-            if (leader) {   // buffers of the next level: counters par^1, list count cur
+            if (leader) {   // buffers of the next level: counters par^1, list count and chunk counter
                 u32* nx = p.gcnt + (par ^ 1) * 512;
                 for (u32 i = tid; i < 512; i += THREADS) nx[i] = 0;
-                if (tid == 0) p.glist_n[cur] = 0;
+                if (tid == 0) {
+                    p.glist_n[cur] = 0;
+                    p.gchunk[cur ^ 1] = 0;
+                }
             }
             __syncthreads();
             if (leader) flush_completions(p, s_cid, s_cf, s_cr, s_nc, s_thr, THREADS);
@@ -501,9 +758,9 @@ __global__ void __launch_bounds__(THREADS) k_wave_grid(WaveParams p) {
         }
         if (!ok) break;
         if (leader && tid == 0) {
-            st.waves++;
-            st.levels += d;
-            if (d > st.maxlevel) st.maxlevel = d;
+            bstat_add(s_bst, ST_WAVES, 1);
+            bstat_add(s_bst, ST_LEVELS, d);
+            bstat_max(s_bst, ST_MAXLEVEL, d);
         }
         // clear the wave's footprint: every block has finished expanding
         // (the level loop ends at a barrier or on a decision all blocks share)
@@ -515,13 +772,15 @@ __global__ void __launch_bounds__(THREADS) k_wave_grid(WaveParams p) {
             S.F[0][w] = 0;
             S.F[1][w] = 0;
         }
-        if (leader && tid == 0) st.cleared += nlog;
+        if (leader && tid == 0) bstat_add(s_bst, ST_CLEARED, nlog);
         if (!(ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err))) break;
         if (leader) {   // reset per-wave counters and advance the queue
             for (u32 i = tid; i < 1024; i += THREADS) p.gcnt[i] = 0;
             if (tid == 0) {
                 p.glist_n[0] = 0;
                 p.glist_n[1] = 0;
+                p.gchunk[0] = 0;
+                p.gchunk[1] = 0;
                 *p.glog_n = 0;
                 *p.head = base + L;
             }
@@ -529,7 +788,8 @@ __global__ void __launch_bounds__(THREADS) k_wave_grid(WaveParams p) {
         if (!(ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err))) break;
         if (!p.exhaustive && wave_entries < p.heavy_words) break;   // light: hand over to the CTAs
     }
-    flush_stats(st, p.stats);
+    __syncthreads();
+    flush_stats(st, s_bst, p.stats);
 }
 
 // --------------------------------------------------- plain, one source
@@ -541,6 +801,7 @@ __global__ void __launch_bounds__(THREADS) k_plain(WaveParams p, u32 it, u32* st
     __shared__ u32 s_cg, s_cs;
     __shared__ ThrCache s_thr;
     __shared__ int s_go;
+    __shared__ BlockStats s_bst;
     const u32 tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const bool leader = blockIdx.x == 0;
     const GraphDev& G = p.g;
@@ -553,6 +814,7 @@ __global__ void __launch_bounds__(THREADS) k_plain(WaveParams p, u32 it, u32* st
         s_thr.valid = 0; s_thr.N = 0; s_thr.F = 1; s_thr.id = 0;
         read_threshold(p.topk.thr, s_thr);   // fixed for this launch: only its end inserts
     }
+    bstat_init(s_bst);
     __syncthreads();
     const u32 xlo = __ldg(&G.xlo[v]), xhi = __ldg(&G.xhi[v]);
     u32 d = 0, cur = 0, nd = 1;
@@ -649,12 +911,12 @@ __global__ void __launch_bounds__(THREADS) k_plain(WaveParams p, u32 it, u32* st
     if (leader && tid == 0) {
         p.gcnt[0] = 0; p.gcnt[256] = 0; p.gcnt[512] = 0; p.gcnt[768] = 0;
         p.glist_n[0] = 0; p.glist_n[1] = 0;
-        st.levels = d;
-        st.maxlevel = d;
-        st.waves = 1;
-        if (cut) st.cut = 1;
+        bstat_add(s_bst, ST_LEVELS, d);
+        bstat_max(s_bst, ST_MAXLEVEL, d);
+        bstat_add(s_bst, ST_WAVES, 1);
+        if (cut) bstat_add(s_bst, ST_CUT, 1);
         if (done && ok) {
-            st.completed = 1;
+            bstat_add(s_bst, ST_COMPLETED, 1);
             if (lock_acquire(p.topk.lock, p.lock_limit_ns, p.err)) {
                 topk_insert_locked(p.topk, v, f, nd);
                 topk_publish_locked(p.topk);
@@ -663,7 +925,8 @@ __global__ void __launch_bounds__(THREADS) k_plain(WaveParams p, u32 it, u32* st
         }
     }
     (void)s_go;
-    flush_stats(st, p.stats);
+    __syncthreads();
+    flush_stats(st, s_bst, p.stats);
 }
 
 // ------------------------------------------------------------- launchers

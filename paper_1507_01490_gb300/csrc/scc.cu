@@ -286,8 +286,8 @@ static inline size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
 size_t scc_scratch_bytes(uint32_t n, uint64_t m) {
     size_t nb = al(((size_t)n + 1) * 4), mb = al((m ? m : 1) * 4), m8 = al((m ? m : 1) * 8);
     size_t s = 0;
-    s += nb * 12;                 // rrp, cursor, color, fw, bw, lists x2, minv, flags, A, Om, wsz/outcnt
-    s += mb * 4;                  // rcol, dsrc, ddst, pred
+    s += nb * 12;                 // cursor, drp, color, fw, bw, lists x2, minv, flags, ...
+    s += mb * 4;                  // pred, dsrc, ddst, flags
     s += m8 * 2;                  // keys, keys_tmp
     s += al(scan_scratch_bytes((m > n ? m : n) + 1));
     s += al(radix_scratch_bytes(m ? m : 1));
@@ -321,14 +321,33 @@ int read_u32(const uint32_t* d, uint32_t* h, cudaStream_t s) {
         if (cudaGetLastError() != cudaSuccess) return -1;            \
     } while (0)
 
-int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, uint32_t n, uint64_t m, uint32_t* comp,
-                      uint32_t* xlo, uint32_t* xhi, uint32_t* n_scc_host, void* scratch, size_t scratch_bytes,
-                      int* err, cudaStream_t s) {
+// In-arcs as a CSR: rrp[n+1], rcol[m] (rows unsorted).
+int launch_reverse_csr(const uint32_t* rp, const uint32_t* col, uint32_t n, uint64_t m, uint32_t* rrp,
+                       uint32_t* rcol, void* scratch, size_t scratch_bytes, cudaStream_t s) {
+    if (n == 0) return 0;
+    Bump B{(char*)scratch, scratch_bytes};
+    uint32_t* cursor = (uint32_t*)B.take(((size_t)n + 1) * 4);
+    uint32_t* total = (uint32_t*)B.take(64);
+    void* scan_scr = B.take(scan_scratch_bytes((size_t)n + 1));
+    if (!cursor || !total || !scan_scr) return -1;
+    const unsigned gw = grid_for((size_t)n * 32);
+    cudaMemsetAsync(cursor, 0, ((size_t)n + 1) * 4, s);
+    LAUNCH(k_count_in<<<gw, 256, 0, s>>>(rp, col, n, cursor));
+    if (exclusive_scan_u32(cursor, rrp, n, total, scan_scr, s)) return -1;
+    LAUNCH(k_set_last<<<1, 1, 0, s>>>(rrp, n, (uint32_t)m));
+    cudaMemcpyAsync(cursor, rrp, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
+    LAUNCH(k_fill_rev<<<gw, 256, 0, s>>>(rp, col, n, cursor, rcol));
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, const uint32_t* rrp, const uint32_t* rcol,
+                      uint32_t n, uint64_t m, uint32_t* comp, uint32_t* xlo, uint32_t* xhi, uint32_t* n_scc_host,
+                      void* scratch, size_t scratch_bytes, int* err, cudaStream_t s) {
     if (n == 0) { *n_scc_host = 0; return 0; }
     Bump B{(char*)scratch, scratch_bytes};
-    uint32_t* rrp = (uint32_t*)B.take(((size_t)n + 1) * 4);
     uint32_t* cursor = (uint32_t*)B.take(((size_t)n + 1) * 4);
-    uint32_t* rcol = (uint32_t*)B.take((m ? m : 1) * 4);
+    uint32_t* drp_buf = (uint32_t*)B.take(((size_t)n + 1) * 4);
+    uint32_t* pred_buf = (uint32_t*)B.take((m ? m : 1) * 4);
     uint32_t* sccv = comp;        // representative per vertex until the final labels
     uint32_t* color = (uint32_t*)B.take(((size_t)n + 1) * 4);
     uint32_t* fw = (uint32_t*)B.take(((size_t)n + 1) * 4);
@@ -340,19 +359,11 @@ int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, uint32_t n, uint6
     uint32_t* cnts = (uint32_t*)B.take(256);     // [0] changed, [1],[2] list counts, [3] total, [4] remaining
     unsigned long long* best = (unsigned long long*)B.take(64);
     void* scan_scr = B.take(scan_scratch_bytes((m > n ? m : n) + 1));
-    if (!rrp || !cursor || !rcol || !color || !fw || !bw || !L0 || !L1 || !minv || !flags || !cnts || !best ||
-        !scan_scr)
+    if (!cursor || !drp_buf || !pred_buf || !color || !fw || !bw || !L0 || !L1 || !minv || !flags || !cnts ||
+        !best || !scan_scr)
         return -1;
     const unsigned gv = grid_for(n), gw = grid_for((size_t)n * 32);
     (void)err;
-
-    // reverse CSR
-    cudaMemsetAsync(cursor, 0, ((size_t)n + 1) * 4, s);
-    LAUNCH(k_count_in<<<gw, 256, 0, s>>>(rp, col, n, cursor));
-    if (exclusive_scan_u32(cursor, rrp, n, &cnts[3], scan_scr, s)) return -1;
-    LAUNCH(k_set_last<<<1, 1, 0, s>>>(rrp, n, (uint32_t)m));
-    cudaMemcpyAsync(cursor, rrp, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
-    LAUNCH(k_fill_rev<<<gw, 256, 0, s>>>(rp, col, n, cursor, rcol));
     LAUNCH(k_fill<<<gv, 256, 0, s>>>(sccv, n, UNSET));
 
     uint32_t h = 0;
@@ -441,7 +452,7 @@ int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, uint32_t n, uint6
     uint32_t* A = fw;
     uint32_t* Om = bw;
     uint32_t* outcnt = cursor;
-    uint32_t* drp = rrp;          // reverse CSR no longer needed
+    uint32_t* drp = drp_buf;
     uint32_t* prp = L1;
     uint32_t ndag = 0;
     uint32_t* dsrc = nullptr;
@@ -452,7 +463,7 @@ int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, uint32_t n, uint6
         unsigned long long* ktmp = (unsigned long long*)B.take(m * 8);
         dsrc = (uint32_t*)B.take(m * 4);
         ddst = (uint32_t*)B.take(m * 4);
-        pred = rcol;
+        pred = pred_buf;
         void* rscr = B.take(radix_scratch_bytes(m));
         if (!keys || !ktmp || !dsrc || !ddst || !rscr) return -1;
         LAUNCH(k_dag_keys<<<gw, 256, 0, s>>>(rp, col, n, comp, b, keys));

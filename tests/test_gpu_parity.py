@@ -73,6 +73,10 @@ def test_farness_all_small(B, gen, orc, lanes):
             assert np.array_equal(gf, f) and np.array_equal(gr, r), (g.name, lanes)
             gf, gr, st = h.farness_all(lanes=lanes, flags=B.BCM_CTA_ONLY)
             assert np.array_equal(gf, f) and np.array_equal(gr, r), (g.name, lanes, "cta")
+            gf, gr, st = h.farness_all(grid_lanes=lanes, pull_div=1 << 30)
+            assert np.array_equal(gf, f) and np.array_equal(gr, r), (g.name, lanes, "pull")
+            gf, gr, st = h.farness_all(grid_lanes=lanes, flags=B.BCM_NO_PULL)
+            assert np.array_equal(gf, f) and np.array_equal(gr, r), (g.name, lanes, "push")
 
 
 @pytest.mark.parametrize("lanes,threads", [(64, 256), (64, 512), (128, 512), (256, 256), (256, 1024)])
@@ -104,6 +108,10 @@ def test_topk_kernel_choices_and_footnote(B, gen, orc):
                     for hw in (1, 50, 1 << 30):
                         ids, gf, gr, st = h.topk(k, grid_lanes=gl, heavy_words=hw)
                         assert np.array_equal(ids, exp) and np.array_equal(gf, f[exp]), (g.name, k, gl, hw)
+                    # every grid level by pull, then every one by push
+                    for flags, pd in ((B.BCM_GRID_ONLY, 1 << 30), (B.BCM_GRID_ONLY | B.BCM_NO_PULL, 0)):
+                        ids, gf, gr, st = h.topk(k, grid_lanes=gl, flags=flags, pull_div=pd)
+                        assert np.array_equal(ids, exp) and np.array_equal(gf, f[exp]), (g.name, k, gl, pd)
 
 
 def test_plain_equals_oracle_bcm(B, gen, orc):
