@@ -186,6 +186,29 @@ bcm_status bcm_topk(bcm_graph_t g, uint32_t k, const bcm_options* opt, uint32_t*
 bcm_status bcm_farness_all(bcm_graph_t g, const bcm_options* opt, uint64_t* farness, uint32_t* reach,
                            bcm_stats* stats);
 
+/*
+ * bcm_farness_all_noalloc -- the same f(v) and r(v) as bcm_farness_all,
+ * computed without allocating any memory.  The paper has no counterpart;
+ * this serves callers that cannot allocate device memory when they need the
+ * result: code under a host framework that owns all device memory, request
+ * paths where an allocation's device synchronisation is not acceptable, and
+ * programs with a fixed memory budget.
+ *   row_ptr, col     : CSR in DEVICE memory (as for bcm_graph_create), not retained.
+ *   n, m             : n <= 1,500,000 vertices (else BCM_ERR_UNSUPPORTED), m < 2^32.
+ *   stream           : cudaStream_t for the work (NULL = legacy default); the call
+ *                      returns once it has finished.
+ *   farness, reach   : DEVICE outputs, n entries each, indexed by vertex id.
+ * All working memory is one fixed 64 MiB device array inside the library,
+ * looked up on the first call on each device (make that first call before
+ * any stream capture).  Every call on a device shares that array and clears
+ * what it needs; calls whose GPU work overlaps (other streams or threads on
+ * the same device) race on it and must be serialised by the caller.
+ * Errors: BCM_ERR_INVALID (NULL pointer, malformed CSR), BCM_ERR_UNSUPPORTED,
+ * BCM_ERR_CUDA, BCM_ERR_TIMEOUT; the message is in bcm_last_error().
+ */
+bcm_status bcm_farness_all_noalloc(const uint64_t* row_ptr, const uint32_t* col, uint32_t n, uint64_t m,
+                                   void* stream, uint64_t* farness, uint32_t* reach);
+
 /* Thread-local message for the last failing call ("" if none). */
 const char* bcm_last_error(void);
 

@@ -33,7 +33,8 @@ BCM_NO_PULL = 0x40
 
 # every symbol include/bcm.h declares
 EXPORTS = ["bcm_graph_create", "bcm_graph_destroy", "bcm_preprocess", "bcm_scc_bounds", "bcm_topk",
-           "bcm_farness_all", "bcm_last_error", "bcm_launch_count", "bcm_workspace_bytes"]
+           "bcm_farness_all", "bcm_farness_all_noalloc", "bcm_last_error", "bcm_launch_count",
+           "bcm_workspace_bytes"]
 
 
 class bcm_options(ctypes.Structure):
@@ -85,6 +86,7 @@ def load():
         "bcm_scc_bounds": (i32, [vp, vp, vp, vp, vp, i32]),
         "bcm_topk": (i32, [vp, u32, ctypes.POINTER(bcm_options), vp, vp, vp, ctypes.POINTER(bcm_stats)]),
         "bcm_farness_all": (i32, [vp, ctypes.POINTER(bcm_options), vp, vp, ctypes.POINTER(bcm_stats)]),
+        "bcm_farness_all_noalloc": (i32, [vp, vp, u32, u64, vp, vp, vp]),
         "bcm_last_error": (ctypes.c_char_p, []),
         "bcm_launch_count": (u64, []),
         "bcm_workspace_bytes": (u64, [vp, ctypes.POINTER(bcm_options)]),
@@ -166,6 +168,14 @@ def bcm_topk(h, k, options, ids, farness, reach, stats=None):
 def bcm_farness_all(h, options, farness, reach, stats=None):
     _check(load().bcm_farness_all(h, ctypes.byref(options) if options is not None else None, _ptr(farness),
                                   _ptr(reach), ctypes.byref(stats) if stats is not None else None))
+
+
+def bcm_farness_all_noalloc(row_ptr, col, n, m, stream, farness, reach):
+    """f(v), r(v) of every vertex without any allocation by the library (all
+    pointers device memory; see include/bcm.h for the limits)."""
+    _check(load().bcm_farness_all_noalloc(_ptr(row_ptr), _ptr(col), n, m,
+                                          _ptr(stream) if stream is not None else None, _ptr(farness),
+                                          _ptr(reach)))
 
 
 def bcm_workspace_bytes(h, options=None) -> int:

@@ -21,6 +21,8 @@ void note_launch(int count) { g_launches.fetch_add((uint64_t)count, std::memory_
 
 static thread_local std::string t_err;
 
+void set_error_message(const char* msg) { t_err = msg; }
+
 static bcm_status fail(bcm_status st, const char* fmt, ...) {
     char buf[512];
     va_list ap;

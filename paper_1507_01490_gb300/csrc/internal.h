@@ -116,5 +116,7 @@ int cta_blocks_per_sm(int W, int threads);
 
 // launch bookkeeping (api.cu)
 void note_launch(int count = 1);
+// sets the calling thread's bcm_last_error() message (api.cu)
+void set_error_message(const char* msg);
 
 }  // namespace bcm
