@@ -72,10 +72,10 @@ typedef enum {
 
 /* Sources are taken from the degree order in waves.  Waves run first on a
  * grid-wide kernel (all CTAs on one wave) while they are heavy, then on a
- * per-CTA kernel (each CTA its own wave).  A grid wave is light when its
- * frontiers held fewer than heavy_words (vertex, 64-lane word) entries in
- * all; the first light one ends the grid phase.  Exhaustive runs stay on
- * the grid kernel.  Levels of grid waves run by push (each frontier vertex
+ * per-CTA kernel (each CTA its own wave).  A grid wave is narrow when its
+ * frontiers averaged fewer than heavy_words (vertex, 64-lane word) entries
+ * per level; the first narrow one ends the grid phase.  Exhaustive runs
+ * stay on the grid kernel.  Levels of grid waves run by push (each frontier vertex
  * sets its lanes' bits in its out-neighbours) or, when the frontier is a
  * large share of the graph, by pull (each vertex with lanes still to reach
  * gathers them from its in-neighbours' frontier bits, with no atomics). */
@@ -85,7 +85,7 @@ typedef struct {
     uint32_t flags;           /* BCM_* flags above */
     uint32_t blocks;          /* CTAs of the per-CTA kernel; 0 = all that fit on the GPU */
     uint32_t threads;         /* threads per CTA of the per-CTA kernel: 256, 512 or 1024; 0 = 512 */
-    uint32_t heavy_words;     /* see above; 0 = default (16 per warp of the grid) */
+    uint32_t heavy_words;     /* see above; 0 = default (4 per warp of the grid) */
     uint32_t pull_div;        /* a grid-wave level whose frontier holds at least n*W/pull_div words
                                  (W = grid_lanes/64) is expanded by pull; 0 = default
                                  (64 for bcm_topk, 16 for bcm_farness_all) */

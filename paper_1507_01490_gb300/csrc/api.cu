@@ -219,7 +219,7 @@ bcm_status resolve(bcm_graph* g, const bcm_options* opt, Cfg* c) {
     int gb = max_coop_blocks(0, c->grid_W, 512);
     if (gb < 1) return fail(BCM_ERR_CUDA, "grid wave kernel does not fit on an SM");
     c->grid_blocks = gb;
-    c->heavy_words = o.heavy_words ? o.heavy_words : (uint64_t)gb * 16 * 16;   // 16 entries per warp
+    c->heavy_words = o.heavy_words ? o.heavy_words : (uint64_t)gb * 16 * 4;   // 4 words per warp and level
     c->pull_div = (c->flags & BCM_NO_PULL) ? 0u : o.pull_div;   // 0: per-mode default below
     if ((c->flags & BCM_CTA_ONLY) && (c->flags & BCM_GRID_ONLY))
         return fail(BCM_ERR_INVALID, "BCM_CTA_ONLY and BCM_GRID_ONLY exclude each other");

@@ -596,10 +596,11 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
 // state; per-level counters are summed in global memory between two grid
 // barriers; block 0 owns the top-k.  After each wave the grid decides, from
 // values every block read after the same barriers, whether the wave was
-// heavy (its frontiers held more than p.heavy_words words in total).  On
-// the first light wave the kernel returns and leaves *head where the
-// per-CTA kernel continues; exhaustive runs (or max_grid_waves reached) end it
-// too.
+// wide (its frontiers averaged at least p.heavy_words words per level):
+// only wide levels use the whole GPU well, while a long thin wave (a
+// high-diameter graph) is better left to one CTA.  On the first narrow wave
+// the kernel returns and leaves *head where the per-CTA kernel continues;
+// exhaustive runs stay until the queue is empty.
 template <int W, int THREADS>
 __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREADS) : 1) k_wave_grid(WaveParams p) {
     constexpr int L = 64 * W;
@@ -786,7 +787,9 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
             }
         }
         if (!(ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err))) break;
-        if (!p.exhaustive && wave_entries < p.heavy_words) break;   // light: hand over to the CTAs
+        // light (its levels averaged fewer than heavy_words frontier words):
+        // hand the rest of the queue over to the CTAs
+        if (!p.exhaustive && wave_entries < p.heavy_words * (u64)(d ? d : 1)) break;
     }
     __syncthreads();
     flush_stats(st, s_bst, p.stats);
