@@ -194,7 +194,7 @@ bcm_status bcm_farness_all(bcm_graph_t g, const bcm_options* opt, uint64_t* farn
  * paths where an allocation's device synchronisation is not acceptable, and
  * programs with a fixed memory budget.
  *   row_ptr, col     : CSR in DEVICE memory (as for bcm_graph_create), not retained.
- *   n, m             : n <= 1,500,000 vertices (else BCM_ERR_UNSUPPORTED), m < 2^32.
+ *   n, m             : n <= 1,250,000 vertices (else BCM_ERR_UNSUPPORTED), m < 2^32.
  *   stream           : cudaStream_t for the work (NULL = legacy default); the call
  *                      returns once it has finished.
  *   farness, reach   : DEVICE outputs, n entries each, indexed by vertex id.

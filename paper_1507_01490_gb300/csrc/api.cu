@@ -172,6 +172,7 @@ struct bcm_graph {
     uint32_t* d_rrp = nullptr;     // directed: in-arcs CSR
     uint32_t* d_rcol = nullptr;
     uint32_t n_comp = 0;
+    bool labels_ready = false;     // d_comp holds labels (else component roots)
     bool preprocessed = false;
     Aux* d_aux = nullptr;
     uint32_t* d_plain = nullptr;   // stamps [n], two vertex queues [2n]
@@ -305,19 +306,9 @@ bcm_status preprocess(bcm_graph* g, double* ms) {
                 st = fail(BCM_ERR_CUDA, "component kernels: %s", cudaGetErrorString(cudaGetLastError()));
                 break;
             }
-            // labels: rank of the component's smallest vertex among all such
-            uint32_t* flags = size;   // reuse: size no longer needed after reach
-            uint32_t* total = (uint32_t*)(d_scr + scratch - 512);
-            if (launch_root_flags(parent, n, flags, s) ||
-                exclusive_scan_u32(flags, flags, n, total, d_scr + nb, s) ||
-                launch_relabel(parent, flags, n, s)) {
-                st = fail(BCM_ERR_CUDA, "component labels");
-                break;
-            }
-            if (cudaMemcpyAsync(&g->n_comp, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) {
-                st = fail(BCM_ERR_CUDA, "copy");
-                break;
-            }
+            // d_comp now holds each vertex's component root (its smallest
+            // vertex); bcm_scc_bounds turns roots into labels when asked
+            g->labels_ready = false;
         } else {
             uint32_t nscc = 0;
             if (!g->d_rrp) {
@@ -336,6 +327,7 @@ bcm_status preprocess(bcm_graph* g, double* ms) {
             if (rc == -2) { st = fail(BCM_ERR_UNSUPPORTED, "directed preprocessing is not available"); break; }
             if (rc) { st = fail(BCM_ERR_CUDA, "SCC kernels: %s", cudaGetErrorString(cudaGetLastError())); break; }
             g->n_comp = nscc;
+            g->labels_ready = true;
         }
         if (launch_degree_order(g->d_rp, n, g->d_order, d_scr, scratch - 1024, s)) {
             st = fail(BCM_ERR_CUDA, "degree order: %s", cudaGetErrorString(cudaGetLastError()));
@@ -358,6 +350,34 @@ bcm_status preprocess(bcm_graph* g, double* ms) {
     if (herr) return check_dev_err(herr);
     g->preprocessed = true;
     if (ms) *ms += t;
+    return BCM_OK;
+}
+
+// Undirected graphs: component roots -> labels ordered by smallest member
+// (a root is its component's smallest vertex, so the label is the root's rank
+// among roots).
+bcm_status ensure_labels(bcm_graph* g) {
+    if (g->labels_ready || g->n == 0) { g->labels_ready = true; return BCM_OK; }
+    cudaStream_t s = g->stream;
+    const uint32_t n = g->n;
+    size_t nb = ((size_t)n * sizeof(uint32_t) + 255) & ~(size_t)255;
+    size_t bytes = nb + scan_scratch_bytes(n) + 512;
+    char* d_scr = nullptr;
+    CU(cudaMalloc(&d_scr, bytes), "label scratch");
+    uint32_t* flags = (uint32_t*)d_scr;
+    uint32_t* total = (uint32_t*)(d_scr + bytes - 256);
+    bcm_status st = BCM_OK;
+    if (launch_root_flags(g->d_comp, n, flags, s) || exclusive_scan_u32(flags, flags, n, total, d_scr + nb, s) ||
+        launch_relabel(g->d_comp, flags, n, s))
+        st = fail(BCM_ERR_CUDA, "component labels");
+    if (st == BCM_OK &&
+        cudaMemcpyAsync(&g->n_comp, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        st = fail(BCM_ERR_CUDA, "copy");
+    cudaError_t e = cudaStreamSynchronize(s);
+    cudaFree(d_scr);
+    if (st) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "component labels");
+    g->labels_ready = true;
     return BCM_OK;
 }
 
@@ -684,6 +704,7 @@ bcm_status bcm_scc_bounds(bcm_graph_t g, uint32_t* comp, uint32_t* alpha, uint32
     if (!g) return fail(BCM_ERR_INVALID, "graph is NULL");
     bcm_status st = preprocess(g, nullptr);
     if (st) return st;
+    if ((st = ensure_labels(g))) return st;
     size_t b = (size_t)g->n * sizeof(uint32_t);
     if (b) {
         if (comp && (st = copy_out(comp, g->d_comp, b, out_on_device, g->stream))) return st;

@@ -39,10 +39,12 @@ struct GraphDev {
 };
 
 // Per-slot working memory of one MS-BFS wave with W words (64W sources) per
-// vertex.  Word index of (vertex v, word g) is v*W + g.
+// vertex.  Word index of (vertex v, word g) is v*W + g; each word has a
+// 32-byte record (vis, F[0], F[1], padding), then two frontier lists and a
+// clear log of 4-byte word indices.
 inline size_t slot_bytes(uint32_t n, int W) {
     size_t nw = (size_t)n * W;
-    size_t b = nw * (3 * sizeof(uint64_t) + 3 * sizeof(uint32_t));
+    size_t b = nw * (4 * sizeof(uint64_t) + 3 * sizeof(uint32_t));
     return (b + 255) & ~(size_t)255;
 }
 

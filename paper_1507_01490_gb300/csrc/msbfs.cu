@@ -31,6 +31,14 @@
 
 namespace bcm {
 
+// The three bit words of one (vertex, 64-lane word) pair -- vis, F[0], F[1]
+// -- sit in one 32-byte record, so a push's check and atomics and the
+// wave-end clear touch a single sector.  vis, F[0] and F[1] below are
+// pointers to the fields; ri(word) is the stride to a word's record.
+constexpr int REC = 4;   // u64 per record (the fourth is padding)
+
+__device__ __forceinline__ size_t ri(u32 word) { return (size_t)word * REC; }
+
 struct SlotPtrs {
     u64* vis;
     u64* F[2];
@@ -42,12 +50,18 @@ __device__ __forceinline__ SlotPtrs slot_ptrs(char* base, u32 n, int W) {
     size_t nw = (size_t)n * W;
     SlotPtrs s;
     s.vis = (u64*)base;
-    s.F[0] = s.vis + nw;
-    s.F[1] = s.F[0] + nw;
-    s.list[0] = (u32*)(s.F[1] + nw);
+    s.F[0] = s.vis + 1;
+    s.F[1] = s.vis + 2;
+    s.list[0] = (u32*)(s.vis + REC * nw);
     s.list[1] = s.list[0] + nw;
     s.clog = s.list[1] + nw;
     return s;
+}
+
+__device__ __forceinline__ void clear_record(u64* vis, u32 word) {
+    ulonglong2* r = (ulonglong2*)&vis[ri(word)];
+    r[0] = make_ulonglong2(0, 0);
+    r[1] = make_ulonglong2(0, 0);
 }
 
 // Counters of the expansion loops, per thread (kept small: they live in
@@ -144,7 +158,7 @@ __device__ __forceinline__ void push_load(const u32* __restrict__ col, u32 e, u6
 template <int W>
 __device__ __forceinline__ void push_check(const u32* __restrict__ rp, const u64* vis, Push& q) {
     q.word = q.x * W + q.g;
-    q.nb = q.F & ~__ldcg(&vis[q.word]);
+    q.nb = q.F & ~__ldcg(&vis[ri(q.word)]);
     q.fl = 0;
     q.degp = 0;
     if (q.nb) {
@@ -154,7 +168,7 @@ __device__ __forceinline__ void push_check(const u32* __restrict__ rp, const u64
 }
 
 __device__ __forceinline__ void push_vis(u64* vis, Push& q, u64& old) {
-    old = q.nb ? atomicOr(&vis[q.word], q.nb) : ~0ull;
+    old = q.nb ? atomicOr(&vis[ri(q.word)], q.nb) : ~0ull;
 }
 
 __device__ __forceinline__ void push_next(u64* Fnext, Push& q, u64 old, u32 foot, LocalStats& st) {
@@ -162,7 +176,7 @@ __device__ __forceinline__ void push_next(u64* Fnext, Push& q, u64 old, u32 foot
     q.fl = (old == 0) ? 2u : 0u;
     q.nb &= ~old;
     if (!q.nb) return;
-    u64 oldF = atomicOr(&Fnext[q.word], q.nb);
+    u64 oldF = atomicOr(&Fnext[ri(q.word)], q.nb);
     if (oldF == 0) { q.fl |= 1u; st.discwords++; }
     q.degp = q.r1 - q.r0 - foot;
     st.disc += __popcll(q.nb);
@@ -217,7 +231,7 @@ __device__ inline void expand_sources(const GraphDev& G, const u32* s_src, const
         u32 beg = __ldg(&G.rp[u]), end = __ldg(&G.rp[u + 1]);
         bool first = false;
         if (lane == 0) {
-            first = atomicOr(&vis[u * W + g], F) == 0;
+            first = atomicOr(&vis[ri(u * W + g)], F) == 0;
             st.mvis += end - beg;
             st.arcwords += end - beg;
         }
@@ -273,8 +287,8 @@ __device__ inline void expand_entries(const GraphDev& G, const u32* list, u32 cn
             u32 word = __ldcg(&list[e]);
             u32 u = word / W;
             g = word - u * W;
-            F = __ldcg(&Fcur[word]);
-            Fcur[word] = 0;
+            F = __ldcg(&Fcur[ri(word)]);
+            Fcur[ri(word)] = 0;
             F &= ((u64)s_alive32[2 * g + 1] << 32) | s_alive32[2 * g];
             st.entries++;
             if (F) {
@@ -353,7 +367,7 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
             bool any = false;
 #pragma unroll
             for (int g = 0; g < W; ++g) {
-                v0[g] = __ldcg(&vis[(size_t)x * W + g]);
+                v0[g] = __ldcg(&vis[ri(x * W + g)]);
                 pend[g] = alive[g] & ~v0[g];
                 any = any || pend[g] != 0;
             }
@@ -368,7 +382,7 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
                     bool done = true;
 #pragma unroll
                     for (int g = 0; g < W; ++g) {
-                        if (pend[g] & ~acc[g]) acc[g] |= __ldcg(&Fcur[(size_t)u * W + g]);
+                        if (pend[g] & ~acc[g]) acc[g] |= __ldcg(&Fcur[ri(u * W + g)]);
                         done = done && !(pend[g] & ~acc[g]);
                     }
                     if (done) { ++i; break; }
@@ -379,8 +393,8 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
                 for (int g = 0; g < W; ++g) {
                     nb[g] = acc[g] & pend[g];
                     if (nb[g]) {
-                        vis[(size_t)x * W + g] = v0[g] | nb[g];
-                        Fnext[(size_t)x * W + g] = nb[g];
+                        vis[ri(x * W + g)] = v0[g] | nb[g];
+                        Fnext[ri(x * W + g)] = nb[g];
                         st.disc += __popcll(nb[g]);
                         st.discwords++;
                     }
@@ -407,8 +421,8 @@ __device__ inline void pull_retire(const GraphDev& G, const u32* list, u32 cnt, 
     for (u32 i = gtid; i < cnt; i += gthreads) {
         const u32 word = __ldcg(&list[i]);
         const u32 u = word / W, g = word - u * W;
-        u64 F = __ldcg(&Fcur[word]);
-        Fcur[word] = 0;
+        u64 F = __ldcg(&Fcur[ri(word)]);
+        Fcur[ri(word)] = 0;
         F &= ((u64)s_alive32[2 * g + 1] << 32) | s_alive32[2 * g];
         st.entries++;
         if (F) st.mvis += (u64)__popcll(F) * (__ldg(&G.rp[u + 1]) - __ldg(&G.rp[u]));
@@ -578,9 +592,7 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
         const u32 nlog = s_logn;
         for (u32 i = tid; i < nlog; i += THREADS) {
             u32 w = S.clog[i];
-            S.vis[w] = 0;
-            S.F[0][w] = 0;
-            S.F[1][w] = 0;
+            clear_record(S.vis, w);
         }
         if (tid == 0) bstat_add(s_bst, ST_CLEARED, nlog);
         __syncthreads();
@@ -769,9 +781,7 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
         const u32 nlog = vload(p.glog_n);
         for (u32 i = blockIdx.x * THREADS + tid; i < nlog; i += gridDim.x * THREADS) {
             u32 w = __ldcg(&S.clog[i]);
-            S.vis[w] = 0;
-            S.F[0][w] = 0;
-            S.F[1][w] = 0;
+            clear_record(S.vis, w);
         }
         if (leader && tid == 0) bstat_add(s_bst, ST_CLEARED, nlog);
         if (!(ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err))) break;

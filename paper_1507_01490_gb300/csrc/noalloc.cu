@@ -27,9 +27,9 @@
 namespace bcm {
 
 // 64 MiB: the CSR offsets narrowed to 32 bits, a source order, and the
-// per-CTA wave slots (36 bytes per vertex each) for as many CTAs as fit.
+// per-CTA wave slots (44 bytes per vertex each) for as many CTAs as fit.
 constexpr size_t kNoAllocBytes = 64ull << 20;
-constexpr uint32_t kNoAllocMaxN = 1500000;   // at least one CTA slot fits below this
+constexpr uint32_t kNoAllocMaxN = 1250000;   // at least one CTA slot (44 bytes per vertex) fits
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 

@@ -69,36 +69,88 @@ __global__ void k_uf_init(uint32_t* parent, uint32_t* size, uint32_t n) {
     }
 }
 
-// One warp per vertex u; its arcs to larger ids are united with u.
-__global__ void k_uf_hook(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t* parent, int* err) {
+__device__ __forceinline__ void uf_union(uint32_t* parent, uint32_t a, uint32_t b, int* err) {
+    for (int it = 0;; ++it) {
+        if (it > (1 << 20)) { atomicOr(err, DEV_ERR_RETRY_LIMIT); return; }
+        a = uf_find(parent, a);
+        b = uf_find(parent, b);
+        if (a == b) return;
+        uint32_t hi = a > b ? a : b, lo = a > b ? b : a;
+        if (atomicCAS(&parent[hi], hi, lo) == hi) return;
+    }
+}
+
+// Components after Afforest (Sutton, Ben-Nun, Barak, IPDPS 2018): link every
+// vertex to its first kLink neighbours, compress, take the component of the
+// highest-degree vertex as the giant one, then link the remaining arcs only
+// of vertices outside it.  For a symmetric arc set a skipped arc (u,w) of a
+// giant-component u is either linked from w's side or joins two vertices
+// already in the giant set, so the components are exact.
+constexpr uint32_t kLink = 2;
+
+__global__ void k_uf_link_first(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t* parent, int* err) {
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < n; u += stride) {
+        uint32_t beg = rp[u], end = rp[u + 1];
+        for (uint32_t e = beg; e < end && e < beg + kLink; ++e) uf_union(parent, (uint32_t)u, col[e], err);
+    }
+}
+
+__global__ void k_uf_flatten(uint32_t* parent, uint32_t n) {
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += stride)
+        parent[v] = uf_find(parent, (uint32_t)v);
+}
+
+__global__ void k_argmax_degree(const uint32_t* rp, uint32_t n, unsigned long long* best) {
+    unsigned long long b = 0;
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += stride) {
+        unsigned long long key = ((unsigned long long)(rp[v + 1] - rp[v]) << 32) | (0xffffffffull - v);
+        b = key > b ? key : b;
+    }
+    for (int o = 16; o; o >>= 1) {
+        unsigned long long t = __shfl_xor_sync(0xffffffffu, b, o);
+        b = t > b ? t : b;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(best, b);
+}
+
+// One warp per vertex outside the giant component: link its arcs beyond the
+// first kLink.
+__global__ void k_uf_link_rest(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t* parent,
+                               const unsigned long long* best, int* err) {
+    const uint32_t giant = uf_find(parent, 0xffffffffu - (uint32_t)(*best & 0xffffffffull));
     const uint32_t lane = threadIdx.x & 31;
     size_t warp = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5;
     size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
     for (size_t u = warp; u < n; u += nwarps) {
         uint32_t beg = rp[u], end = rp[u + 1];
-        for (uint32_t e = beg + lane; e < end; e += 32) {
-            uint32_t w = col[e];
-            if (w <= u) continue;
-            uint32_t a = (uint32_t)u, b = w;
-            for (int it = 0;; ++it) {
-                if (it > (1 << 20)) { atomicOr(err, DEV_ERR_RETRY_LIMIT); break; }
-                a = uf_find(parent, a);
-                b = uf_find(parent, b);
-                if (a == b) break;
-                uint32_t hi = a > b ? a : b, lo = a > b ? b : a;
-                if (atomicCAS(&parent[hi], hi, lo) == hi) break;
-            }
-        }
+        if (end - beg <= kLink) continue;
+        if (uf_find(parent, (uint32_t)u) == giant) continue;
+        for (uint32_t e = beg + kLink + lane; e < end; e += 32) uf_union(parent, (uint32_t)u, col[e], err);
     }
 }
 
+// Final roots and component sizes; lanes holding the same root add their
+// count with one atomic (most vertices share the giant component's root).
 __global__ void k_uf_compress_count(uint32_t* parent, uint32_t* size, uint32_t n) {
     size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += stride) {
-        uint32_t r = uf_find(parent, (uint32_t)v);
-        atomicAdd(&size[r], 1u);
+    for (size_t v0 = (blockIdx.x * (size_t)blockDim.x) + (threadIdx.x & ~31u); v0 < n; v0 += stride) {
+        size_t v = v0 + (threadIdx.x & 31);
+        uint32_t r = v < n ? uf_find(parent, (uint32_t)v) : 0xffffffffu;
+        uint32_t peers = __match_any_sync(0xffffffffu, r);
+        if (r != 0xffffffffu && (threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1))
+            atomicAdd(&size[r], (uint32_t)__popc(peers));
     }
 }
+
+// ------------------------------------------------------------------ scan
+// Exclusive scan in tiles of SCAN_TILE: tile sums, a one-block scan of the
+// sums (chunked, any length), then each tile rescans with its offset.
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
 __global__ void k_uf_reach(uint32_t* parent, const uint32_t* size, uint32_t n, uint32_t* xlo, uint32_t* xhi) {
     size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -115,20 +167,18 @@ int launch_cc_reach(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_
                     uint32_t* size, uint32_t* xlo, uint32_t* xhi, int* err, cudaStream_t s) {
     if (n == 0) return 0;
     int b = blocks_for(n, 256);
+    unsigned long long* best = (unsigned long long*)(size + (((size_t)n + 63) & ~(size_t)63));
+    cudaMemsetAsync(best, 0, sizeof(unsigned long long), s);
     k_uf_init<<<b, 256, 0, s>>>(parent, size, n);
-    k_uf_hook<<<blocks_for((size_t)n * 32, 256), 256, 0, s>>>(rp, col, n, parent, err);
+    k_argmax_degree<<<b, 256, 0, s>>>(rp, n, best);
+    k_uf_link_first<<<b, 256, 0, s>>>(rp, col, n, parent, err);
+    k_uf_flatten<<<b, 256, 0, s>>>(parent, n);
+    k_uf_link_rest<<<blocks_for((size_t)n * 32, 256), 256, 0, s>>>(rp, col, n, parent, best, err);
     k_uf_compress_count<<<b, 256, 0, s>>>(parent, size, n);
     k_uf_reach<<<b, 256, 0, s>>>(parent, size, n, xlo, xhi);
-    note_launch(4);
+    note_launch(7);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
-
-// ------------------------------------------------------------------ scan
-// Exclusive scan in tiles of SCAN_TILE: tile sums, a one-block scan of the
-// sums (chunked, any length), then each tile rescans with its offset.
-constexpr int SCAN_THREADS = 256;
-constexpr int SCAN_ITEMS = 8;
-constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
     __shared__ uint32_t s_warp[32];

@@ -55,6 +55,6 @@ def test_rejects_graphs_beyond_its_limit(B):
     col = torch.zeros(4, dtype=torch.int32, device="cuda")
     out = torch.zeros(4, dtype=torch.int64, device="cuda")
     with pytest.raises(B.BcmError) as ei:
-        B.bcm_farness_all_noalloc(rp, col, 1_500_001, 0, None, out, col)
+        B.bcm_farness_all_noalloc(rp, col, 1_250_001, 0, None, out, col)
     assert ei.value.status == B.BCM_ERR_UNSUPPORTED
-    assert "1500000" in str(ei.value)
+    assert "1250000" in str(ei.value)
