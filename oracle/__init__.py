@@ -11,7 +11,8 @@ Simple Computation of Top-k Closeness Centralities" (arXiv 1507.01490):
 
 * ``farness_all``   Table 1 / Section 1 definitions, one BFS per source.
 * ``topk``          the textbook top-k (Section 2.1), ties by smaller id.
-* ``scc``, ``alpha_omega``  Section 1.3's SCC DAG, Section 2.3's programme.
+* ``scc``, ``alpha_omega``  Section 1.3's SCC DAG, Section 2.3's programme;
+  ``alpha_omega_refined``  the same with Section 2.3's biggest-SCC refinement.
 * ``bound_trace``   Lemma 1's lower bound f~_d(v, x) along one BFS.
 * ``bcm``           Algorithm 1 with BFSCut (Algorithm 2), sequential.
 
@@ -74,6 +75,12 @@ def _get():
         lib.oracle_scc.argtypes = [ctypes.c_uint32, _u64p, _u32p, _u32p]
         lib.oracle_alpha_omega.restype = ctypes.c_int64
         lib.oracle_alpha_omega.argtypes = [ctypes.c_uint32, _u64p, _u32p, _u32p, _u32p, _u32p]
+        lib.oracle_alpha_omega_refined.restype = ctypes.c_int64
+        lib.oracle_alpha_omega_refined.argtypes = [ctypes.c_uint32, _u64p, _u32p, _u32p, _u32p, _u32p]
+        lib.oracle_bcm2.restype = ctypes.c_int64
+        lib.oracle_bcm2.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int, ctypes.c_uint32,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, _u32p, _u64p, _u32p,
+                                    ctypes.POINTER(_Stats)]
         lib.oracle_bound_trace.restype = ctypes.c_int64
         lib.oracle_bound_trace.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_uint32,
                                            ctypes.c_int, ctypes.c_uint64, _i64p, ctypes.c_uint64]
@@ -171,6 +178,19 @@ def alpha_omega(g):
     return comp[:g.n], al[:g.n], om[:g.n], int(nc)
 
 
+def alpha_omega_refined(g):
+    """(comp, alpha, omega, n_scc) with Section 2.3's biggest-SCC refinement."""
+    rp, col = _csr(g)
+    comp = np.zeros(max(g.n, 1), np.uint32)
+    al = np.zeros(max(g.n, 1), np.uint32)
+    om = np.zeros(max(g.n, 1), np.uint32)
+    nc = _get().oracle_alpha_omega_refined(g.n, _p(rp, _u64p), _p(col, _u32p), _p(comp, _u32p),
+                                           _p(al, _u32p), _p(om, _u32p))
+    if nc < 0:
+        raise MemoryError("oracle_alpha_omega_refined failed")
+    return comp[:g.n], al[:g.n], om[:g.n], int(nc)
+
+
 def order(g):
     """Algorithm 1's processing order: degree descending, ids ascending on ties."""
     rp, _ = _csr(g)
@@ -190,8 +210,9 @@ def bound_trace(g, v, x, mode=GT_TABLE1):
     return out[:k]
 
 
-def bcm(g, k, gamma_mode=None, early_test=True):
-    """Algorithm 1 (sequential).  Returns (ids, farness, reach, stats dict)."""
+def bcm(g, k, gamma_mode=None, early_test=True, refined=False):
+    """Algorithm 1 (sequential).  Returns (ids, farness, reach, stats dict).
+    refined: digraph bounds from the biggest-SCC refinement (Section 2.3)."""
     if gamma_mode is None:
         gamma_mode = GT_TABLE1 if g.directed else GT_FOOTNOTE
     rp, col = _csr(g)
@@ -200,9 +221,9 @@ def bcm(g, k, gamma_mode=None, early_test=True):
     f = np.zeros(kk, np.uint64)
     r = np.zeros(kk, np.uint32)
     st = _Stats()
-    got = _get().oracle_bcm(g.n, _p(rp, _u64p), _p(col, _u32p), int(g.directed), k, gamma_mode,
-                            int(bool(early_test)), _p(ids, _u32p), _p(f, _u64p), _p(r, _u32p),
-                            ctypes.byref(st))
+    got = _get().oracle_bcm2(g.n, _p(rp, _u64p), _p(col, _u32p), int(g.directed), k, gamma_mode,
+                             int(bool(early_test)), int(bool(refined)), _p(ids, _u32p), _p(f, _u64p),
+                             _p(r, _u32p), ctypes.byref(st))
     if got < 0:
         raise MemoryError("oracle_bcm failed")
     stats = {"m_vis": st.m_vis, "completed": st.completed, "cut": st.cut, "max_level": st.max_level}

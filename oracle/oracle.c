@@ -311,6 +311,95 @@ int64_t oracle_alpha_omega(uint32_t n, const uint64_t *row_ptr, const uint32_t *
     return nc;
 }
 
+/* Section 2.3, second paragraph: the largest SCC C~ is not bounded by the
+ * programme but measured, R~ = sum of w(D) over the SCCs D reachable from C~
+ * (what one BFS from a vertex of C~ counts), so alpha(C~) = omega(C~) = R~,
+ * and alpha improves for every SCC that reaches C~ through the max.  For
+ * those SCCs omega is also taken from the programme run on the DAG without
+ * the SCCs reachable from C~, plus R~; the smaller of that and the plain
+ * omega is kept (both bound r from above).  C~ is the largest SCC, on ties
+ * the one with the smallest vertex id.  Returns n_scc or -1. */
+int64_t oracle_alpha_omega_refined(uint32_t n, const uint64_t *row_ptr, const uint32_t *col,
+                                   uint32_t *comp, uint32_t *alpha, uint32_t *omega) {
+    int64_t nc = oracle_scc(n, row_ptr, col, comp);
+    if (nc < 0) return -1;
+    if (nc == 0) return 0;
+    uint64_t m = n ? row_ptr[n] : 0;
+    uint64_t *arc = (uint64_t *)malloc(sizeof(uint64_t) * (m ? m : 1));
+    uint64_t *w = (uint64_t *)calloc(nc, sizeof(uint64_t));
+    uint32_t *minv = (uint32_t *)malloc(sizeof(uint32_t) * nc);
+    uint64_t *dptr = (uint64_t *)calloc((size_t)nc + 1, sizeof(uint64_t));
+    uint32_t *indeg = (uint32_t *)calloc(nc, sizeof(uint32_t));
+    uint32_t *topo = (uint32_t *)malloc(sizeof(uint32_t) * nc);
+    uint8_t *desc = (uint8_t *)calloc(nc, 1), *anc = (uint8_t *)calloc(nc, 1);
+    uint64_t *A = (uint64_t *)malloc(sizeof(uint64_t) * nc), *Wf = (uint64_t *)malloc(sizeof(uint64_t) * nc);
+    uint64_t *Wm = (uint64_t *)malloc(sizeof(uint64_t) * nc);
+    if (!arc || !w || !minv || !dptr || !indeg || !topo || !desc || !anc || !A || !Wf || !Wm) {
+        free(arc); free(w); free(minv); free(dptr); free(indeg); free(topo); free(desc); free(anc);
+        free(A); free(Wf); free(Wm);
+        return -1;
+    }
+    for (int64_t c = 0; c < nc; ++c) minv[c] = 0xffffffffu;
+    for (uint32_t v = 0; v < n; ++v) { w[comp[v]]++; if (v < minv[comp[v]]) minv[comp[v]] = v; }
+    uint64_t na = 0;
+    for (uint32_t u = 0; u < n; ++u)
+        for (uint64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e)
+            if (comp[u] != comp[col[e]]) arc[na++] = ((uint64_t)comp[u] << 32) | comp[col[e]];
+    qsort(arc, na, sizeof(uint64_t), cmp_u64);
+    uint64_t nu = 0;
+    for (uint64_t i = 0; i < na; ++i) if (i == 0 || arc[i] != arc[i - 1]) arc[nu++] = arc[i];
+    for (uint64_t i = 0; i < nu; ++i) { dptr[(arc[i] >> 32) + 1]++; indeg[arc[i] & 0xffffffffu]++; }
+    for (int64_t c = 0; c < nc; ++c) dptr[c + 1] += dptr[c];
+    uint64_t qh = 0, qt = 0;
+    for (int64_t c = 0; c < nc; ++c) if (indeg[c] == 0) topo[qt++] = (uint32_t)c;
+    while (qh < qt) {
+        uint32_t c = topo[qh++];
+        for (uint64_t i = dptr[c]; i < dptr[c + 1]; ++i) {
+            uint32_t d = (uint32_t)(arc[i] & 0xffffffffu);
+            if (--indeg[d] == 0) topo[qt++] = d;
+        }
+    }
+    uint32_t big = 0;                       /* C~ */
+    for (int64_t c = 1; c < nc; ++c)
+        if (w[c] > w[big] || (w[c] == w[big] && minv[c] < minv[big])) big = (uint32_t)c;
+    /* SCCs reachable from C~: in topological order, a successor of a marked SCC is marked */
+    desc[big] = 1;
+    for (uint64_t t = 0; t < qt; ++t) {
+        uint32_t c = topo[t];
+        if (!desc[c]) continue;
+        for (uint64_t i = dptr[c]; i < dptr[c + 1]; ++i) desc[arc[i] & 0xffffffffu] = 1;
+    }
+    uint64_t R = 0;
+    for (int64_t c = 0; c < nc; ++c) if (desc[c]) R += w[c];
+    /* SCCs that reach C~: in reverse topological order, an SCC with a marked successor is marked */
+    for (int64_t t = (int64_t)qt - 1; t >= 0; --t) {
+        uint32_t c = topo[t];
+        for (uint64_t i = dptr[c]; i < dptr[c + 1]; ++i) {
+            uint32_t d = (uint32_t)(arc[i] & 0xffffffffu);
+            if (d == big || anc[d]) anc[c] = 1;
+        }
+    }
+    for (int64_t t = (int64_t)qt - 1; t >= 0; --t) {
+        uint32_t c = topo[t];
+        uint64_t amax = 0, fs = 0, ms = 0;
+        for (uint64_t i = dptr[c]; i < dptr[c + 1]; ++i) {
+            uint32_t d = (uint32_t)(arc[i] & 0xffffffffu);
+            if (A[d] > amax) amax = A[d];
+            fs += Wf[d]; if (fs > n) fs = n;
+            if (!desc[d]) { ms += Wm[d]; if (ms > n) ms = n; }
+        }
+        if (c == big) { A[c] = R; Wf[c] = R; Wm[c] = 0; continue; }
+        A[c] = w[c] + amax;
+        Wf[c] = w[c] + fs; if (Wf[c] > n) Wf[c] = n;
+        Wm[c] = desc[c] ? 0 : w[c] + ms; if (Wm[c] > n) Wm[c] = n;
+        if (anc[c] && Wm[c] + R < Wf[c]) Wf[c] = Wm[c] + R;
+    }
+    for (uint32_t v = 0; v < n; ++v) { alpha[v] = (uint32_t)A[comp[v]]; omega[v] = (uint32_t)Wf[comp[v]]; }
+    free(arc); free(w); free(minv); free(dptr); free(indeg); free(topo); free(desc); free(anc);
+    free(A); free(Wf); free(Wm);
+    return nc;
+}
+
 /* ------------------------------------------------- Lemma 1's bound */
 
 /* f~_d(v, x) = f_d - g + (d+2)(x - n_d)   (Table 1; Lemma 1), where g is the
@@ -462,9 +551,21 @@ void oracle_order(uint32_t n, const uint64_t *row_ptr, uint32_t *order) {
  *               1 = the same bound tested before those arcs are scanned.
  * Writes min(k, n) entries to ids/f/r in rank order; returns their count or
  * a negative value on failure. */
+int64_t oracle_bcm2(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, int directed,
+                    uint32_t k, int gamma_mode, int early_test, int refined,
+                    uint32_t *ids, uint64_t *f_out, uint32_t *r_out, bcm_oracle_stats *st);
+
 int64_t oracle_bcm(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, int directed,
                    uint32_t k, int gamma_mode, int early_test,
                    uint32_t *ids, uint64_t *f_out, uint32_t *r_out, bcm_oracle_stats *st) {
+    return oracle_bcm2(n, row_ptr, col, directed, k, gamma_mode, early_test, 0, ids, f_out, r_out, st);
+}
+
+/* As oracle_bcm; refined != 0 takes alpha/omega from the biggest-SCC
+ * refinement on digraphs. */
+int64_t oracle_bcm2(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, int directed,
+                    uint32_t k, int gamma_mode, int early_test, int refined,
+                    uint32_t *ids, uint64_t *f_out, uint32_t *r_out, bcm_oracle_stats *st) {
     if (k == 0 || n == 0) { if (st) memset(st, 0, sizeof(*st)); return 0; }
     if (gamma_mode == GT_FOOTNOTE && directed) gamma_mode = GT_TABLE1;
     uint32_t *xa = (uint32_t *)malloc(sizeof(uint32_t) * n);
@@ -500,7 +601,10 @@ int64_t oracle_bcm(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, int
         free(size);
     } else {
         uint32_t *comp = (uint32_t *)malloc(sizeof(uint32_t) * n);
-        if (!comp || oracle_alpha_omega(n, row_ptr, col, comp, xa, xb) < 0) { free(comp); ok = 0; goto done; }
+        if (!comp || (refined ? oracle_alpha_omega_refined(n, row_ptr, col, comp, xa, xb)
+                              : oracle_alpha_omega(n, row_ptr, col, comp, xa, xb)) < 0) {
+            free(comp); ok = 0; goto done;
+        }
         free(comp);
     }
 

@@ -138,3 +138,21 @@ def test_arcs_scanned_complete_ties(orc, gen, n):
     assert st["m_vis"] == n * (n - 1) + (n - 1) ** 2
     ids, f, r, st = orc.bcm(g, 2, early_test=True)
     assert ids.tolist() == [0, 1] and st["m_vis"] == 2 * n * (n - 1)
+
+
+def test_bcm_refined_bounds_equal_exhaustive(orc, gen):
+    for s in range(8):
+        g = gen.gnp(60 + 20 * s, 0.02 + 0.005 * (s % 3), seed=400 + s, directed=True)
+        f_all, r_all = orc.farness_all(g)
+        for k in (1, 3, 10):
+            ids = orc.topk(f_all, r_all, k)
+            for early in (True, False):
+                bi, bf, br, st = orc.bcm(g, k, early_test=early, refined=True)
+                assert bi.tolist() == ids.tolist()
+    g = gen.rmat(11, 8, seed=3)
+    f_all, r_all = orc.farness_all(g)
+    ids = orc.topk(f_all, r_all, 10)
+    a = orc.bcm(g, 10, refined=False)
+    b = orc.bcm(g, 10, refined=True)
+    assert a[0].tolist() == ids.tolist() == b[0].tolist()
+    assert b[3]["m_vis"] <= a[3]["m_vis"]

@@ -97,3 +97,45 @@ def test_strongly_connected(orc, gen):
     g = gen.dcycle(9)
     comp, al, om, nc = orc.alpha_omega(g)
     assert nc == 1 and (al == 9).all() and (om == 9).all()
+
+
+def test_refined_golden_example(orc, gen):
+    ex = json.load(open(os.path.join(GOLDEN, "scc_refined_example.json")))
+    a = np.array(ex["arcs"])
+    g = gen.csr_from_arcs(ex["n"], a[:, 0], a[:, 1], directed=True)
+    comp, al, om, nc = orc.alpha_omega(g)
+    assert al.tolist() == ex["alpha_plain"] and om.tolist() == ex["omega_plain"]
+    comp, al, om, nc = orc.alpha_omega_refined(g)
+    assert al.tolist() == ex["alpha_refined"] and om.tolist() == ex["omega_refined"]
+    assert orc.farness_all(g)[1].tolist() == ex["reach"]
+    # the first fixture: its largest SCC reaches everything, so the bounds become exact
+    ex1 = json.load(open(os.path.join(GOLDEN, "scc_dag_example.json")))
+    a1 = np.array(ex1["arcs"])
+    g1 = gen.csr_from_arcs(ex1["n"], a1[:, 0], a1[:, 1], directed=True)
+    comp, al, om, nc = orc.alpha_omega_refined(g1)
+    assert al.tolist() == ex1["reach"] and om.tolist() == ex1["reach"]
+
+
+@pytest.mark.parametrize("seed,n,p", [(1, 40, .04), (2, 80, .02), (3, 150, .01), (4, 300, .006),
+                                      (5, 60, .08), (6, 25, .15), (7, 500, .004)])
+def test_refined_bounds_valid_and_tighter(orc, gen, seed, n, p):
+    g = gen.gnp(n, p, seed=seed, directed=True)
+    _, al0, om0, _ = orc.alpha_omega(g)
+    comp, al, om, nc = orc.alpha_omega_refined(g)
+    f, r = orc.farness_all(g)
+    assert (al <= r).all() and (r <= om).all()
+    assert (al >= al0).all() and (om <= om0).all()
+    # the largest SCC (smallest member on ties) is measured exactly
+    sizes = np.bincount(comp, minlength=nc)
+    best = max(range(nc), key=lambda c: (sizes[c], -int(np.nonzero(comp == c)[0].min())))
+    vs = np.nonzero(comp == best)[0]
+    assert (al[vs] == r[vs]).all() and (om[vs] == r[vs]).all()
+
+
+def test_refined_rmat(orc, gen):
+    g = gen.rmat(12, 8, seed=7)
+    _, al0, om0, _ = orc.alpha_omega(g)
+    comp, al, om, nc = orc.alpha_omega_refined(g)
+    f, r = orc.farness_all(g)
+    assert (al <= r).all() and (r <= om).all()
+    assert (om < om0).sum() > 0.1 * g.n          # it tightens a good share of the graph
