@@ -69,6 +69,8 @@ typedef enum {
 #define BCM_CHECK_SYMMETRIC 0x10u /* bcm_graph_create: verify undirected arcs are paired */
 #define BCM_GRID_ONLY     0x20u /* run every wave on the grid-wide kernel */
 #define BCM_NO_PULL       0x40u /* grid-wide waves expand every level by push */
+#define BCM_PLAIN_BOUNDS  0x80u /* bcm_graph_create, digraphs: alpha/omega from the plain programme of
+                                   Section 2.3, without its biggest-SCC refinement (results are the same) */
 
 /* Sources are taken from the degree order in waves.  Waves run first on a
  * grid-wide kernel (all CTAs on one wave) while they are heavy, then on a
@@ -127,7 +129,7 @@ typedef struct {
  *   n, m         : vertex and arc counts.
  *   directed     : 0 = undirected (both arcs of each edge present), 1 = directed.
  *   stream       : cudaStream_t used for all work on this graph (NULL = legacy default).
- *   flags        : BCM_CHECK_SYMMETRIC or 0.
+ *   flags        : BCM_CHECK_SYMMETRIC, BCM_PLAIN_BOUNDS, or 0.
  *   out          : receives the handle; release it with bcm_graph_destroy.
  * Errors: BCM_ERR_INVALID (NULL pointer, row_ptr not monotone from 0 to m,
  * a column >= n), BCM_ERR_NOT_SYMMETRIC, BCM_ERR_UNSUPPORTED (n >= 2^30 or
@@ -145,7 +147,9 @@ bcm_status bcm_graph_destroy(bcm_graph_t g);
  * bcm_preprocess -- run PreProcessing now (Algorithm 1, first line):
  *   undirected: r(v) = size of v's connected component (Section 2.2);
  *   directed:   SCCs, the weighted SCC DAG and alpha(v) <= r(v) <= omega(v)
- *               (Section 2.3), omega held at n;
+ *               (Section 2.3), omega held at n, with the section's
+ *               biggest-SCC refinement (the largest SCC's reach measured,
+ *               smallest member on ties) unless BCM_PLAIN_BOUNDS;
  * and the processing order (degree descending, id ascending; Section 2.1).
  * Idempotent.  Any output pointer may be NULL; when given, each receives n
  * uint32 values (host memory unless out_on_device):

@@ -30,6 +30,7 @@ BCM_CTA_ONLY = 0x8
 BCM_CHECK_SYMMETRIC = 0x10
 BCM_GRID_ONLY = 0x20
 BCM_NO_PULL = 0x40
+BCM_PLAIN_BOUNDS = 0x80
 
 # every symbol include/bcm.h declares
 EXPORTS = ["bcm_graph_create", "bcm_graph_destroy", "bcm_preprocess", "bcm_scc_bounds", "bcm_topk",

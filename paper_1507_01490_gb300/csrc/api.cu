@@ -161,6 +161,7 @@ struct bcm_graph {
     uint32_t n = 0;
     uint64_t m = 0;
     int directed = 0;
+    uint32_t flags = 0;            // bcm_graph_create flags
     cudaStream_t stream = nullptr;
     int dev = 0;
     uint32_t* d_rp = nullptr;
@@ -323,7 +324,8 @@ bcm_status preprocess(bcm_graph* g, double* ms) {
                 break;
             }
             int rc = launch_scc_bounds(g->d_rp, g->d_col, g->d_rrp, g->d_rcol, n, g->m, g->d_comp, g->d_xlo,
-                                       g->d_xhi, &nscc, d_scr, scratch - 1024, d_err, s);
+                                       g->d_xhi, &nscc, !(g->flags & BCM_PLAIN_BOUNDS), d_scr, scratch - 1024,
+                                       d_err, s);
             if (rc == -2) { st = fail(BCM_ERR_UNSUPPORTED, "directed preprocessing is not available"); break; }
             if (rc) { st = fail(BCM_ERR_CUDA, "SCC kernels: %s", cudaGetErrorString(cudaGetLastError())); break; }
             g->n_comp = nscc;
@@ -619,6 +621,7 @@ bcm_status bcm_graph_create(const uint64_t* row_ptr, const uint32_t* col, uint32
     g->n = n;
     g->m = m;
     g->directed = directed ? 1 : 0;
+    g->flags = flags;
     g->stream = (cudaStream_t)stream;
     cudaGetDevice(&g->dev);
     cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->dev);

@@ -106,7 +106,7 @@ int launch_reverse_csr(const uint32_t* rp, const uint32_t* col, uint32_t n, uint
                        uint32_t* rcol, void* scratch, size_t scratch_bytes, cudaStream_t s);
 int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, const uint32_t* rrp, const uint32_t* rcol,
                       uint32_t n, uint64_t m, uint32_t* comp, uint32_t* xlo, uint32_t* xhi, uint32_t* n_scc_host,
-                      void* scratch, size_t scratch_bytes, int* err, cudaStream_t s);
+                      int refine, void* scratch, size_t scratch_bytes, int* err, cudaStream_t s);
 
 // ---- msbfs.cu
 int launch_grid_waves(const WaveParams& p, int W, int blocks, int threads, cudaStream_t s);

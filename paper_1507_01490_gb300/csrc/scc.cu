@@ -234,23 +234,53 @@ __global__ void k_sinks(uint32_t nc, const uint32_t* drp, uint32_t* outcnt, uint
     }
 }
 
+// Section 2.3 for the SCCs of one topological level (all successors done).
+// With the biggest-SCC refinement (big != ~0): big itself gets alpha =
+// omega = R; for an SCC outside big's descendants, Wm is the programme on
+// the DAG without them, and SCCs reaching big keep min(omega, Wm + R).
+struct Refine {
+    uint32_t big;              // largest SCC, or 0xffffffff for the plain programme
+    const uint32_t* R;         // its reach
+    const uint32_t* desc;      // 1: reachable from big (big included)
+    const uint32_t* anc;       // 1: reaches big
+    uint32_t* Wm;
+};
+
 __global__ void k_dp_eval(const uint32_t* front, const uint32_t* fcnt, const uint32_t* drp, const uint32_t* ddst,
-                          const uint32_t* wsz, uint32_t* A, uint32_t* Om, uint32_t n) {
+                          const uint32_t* wsz, uint32_t* A, uint32_t* Om, uint32_t n, Refine rf) {
     const uint32_t cnt = *fcnt;
+    const bool refine = rf.big != 0xffffffffu;
     GRID_STRIDE(i, cnt) {
         uint32_t c = front[i];
         uint32_t amax = 0;
-        unsigned long long osum = 0;
+        unsigned long long osum = 0, msum = 0;
         for (uint32_t e = drp[c]; e < drp[c + 1]; ++e) {
             uint32_t d = ddst[e];
             uint32_t a = vload(&A[d]);
             amax = a > amax ? a : amax;
             osum += vload(&Om[d]);
             if (osum > n) osum = n;
+            if (refine && !rf.desc[d]) {
+                msum += vload(&rf.Wm[d]);
+                if (msum > n) msum = n;
+            }
+        }
+        if (refine && c == rf.big) {
+            A[c] = *rf.R;
+            Om[c] = *rf.R;
+            rf.Wm[c] = 0;
+            continue;
         }
         A[c] = wsz[c] + amax;
         unsigned long long o = wsz[c] + osum;
-        Om[c] = (uint32_t)(o > n ? n : o);
+        o = o > n ? n : o;
+        if (refine) {
+            unsigned long long wm = rf.desc[c] ? 0 : wsz[c] + msum;
+            wm = wm > n ? n : wm;
+            rf.Wm[c] = (uint32_t)wm;
+            if (rf.anc[c] && wm + *rf.R < o) o = wm + *rf.R;
+        }
+        Om[c] = (uint32_t)o;
     }
 }
 
@@ -272,6 +302,55 @@ __global__ void k_dp_release(const uint32_t* front, const uint32_t* fcnt, const 
     }
 }
 
+// Largest SCC: labels follow smallest members, so the smallest label wins ties.
+__global__ void k_argmax_comp(const uint32_t* wsz, uint32_t nc, unsigned long long* best) {
+    unsigned long long b = 0;
+    GRID_STRIDE(c, nc) {
+        unsigned long long key = ((unsigned long long)wsz[c] << 32) | (0xffffffffull - c);
+        b = key > b ? key : b;
+    }
+    for (int o = 16; o; o >>= 1) {
+        unsigned long long t = __shfl_xor_sync(0xffffffffu, b, o);
+        b = t > b ? t : b;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(best, b);
+}
+
+__global__ void k_mark_seed(const unsigned long long* best, uint32_t* mark, uint32_t* list, uint32_t* cnt,
+                            uint32_t* big) {
+    uint32_t c = 0xffffffffu - (uint32_t)(*best & 0xffffffffull);
+    mark[c] = 1;
+    list[0] = c;
+    *cnt = 1;
+    *big = c;
+}
+
+// one BFS level over a DAG given as CSR (successors or predecessors)
+__global__ void k_dag_reach(const uint32_t* ptr, const uint32_t* adj, const uint32_t* front, const uint32_t* fcnt,
+                            uint32_t* next, uint32_t* ncnt, uint32_t* mark) {
+    const uint32_t cnt = *fcnt;
+    WARP_PER_ITEM(i, cnt) {
+        uint32_t c = front[i];
+        for (uint32_t e0 = ptr[c]; e0 < ptr[c + 1]; e0 += 32) {
+            uint32_t e = e0 + lane_;
+            bool app = false;
+            uint32_t d = 0;
+            if (e < ptr[c + 1]) {
+                d = adj[e];
+                app = vload(&mark[d]) == 0 && atomicExch(&mark[d], 1u) == 0;
+            }
+            warp_append(app, d, next, ncnt);
+        }
+    }
+}
+
+__global__ void k_sum_marked(const uint32_t* wsz, const uint32_t* mark, uint32_t nc, unsigned long long* sum) {
+    unsigned long long s = 0;
+    GRID_STRIDE(c, nc) if (mark[c]) s += wsz[c];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(sum, s);
+}
+
 __global__ void k_xbounds(uint32_t n, const uint32_t* comp, const uint32_t* A, const uint32_t* Om, uint32_t* xlo,
                           uint32_t* xhi) {
     GRID_STRIDE(v, n) {
@@ -291,7 +370,7 @@ size_t scc_scratch_bytes(uint32_t n, uint64_t m) {
     s += m8 * 2;                  // keys, keys_tmp
     s += al(scan_scratch_bytes((m > n ? m : n) + 1));
     s += al(radix_scratch_bytes(m ? m : 1));
-    s += 4096;
+    s += nb * 5 + 4096;           // refinement: desc, anc, Wm, two queues
     return s;
 }
 
@@ -342,7 +421,7 @@ int launch_reverse_csr(const uint32_t* rp, const uint32_t* col, uint32_t n, uint
 
 int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, const uint32_t* rrp, const uint32_t* rcol,
                       uint32_t n, uint64_t m, uint32_t* comp, uint32_t* xlo, uint32_t* xhi, uint32_t* n_scc_host,
-                      void* scratch, size_t scratch_bytes, int* err, cudaStream_t s) {
+                      int refine, void* scratch, size_t scratch_bytes, int* err, cudaStream_t s) {
     if (n == 0) { *n_scc_host = 0; return 0; }
     Bump B{(char*)scratch, scratch_bytes};
     uint32_t* cursor = (uint32_t*)B.take(((size_t)n + 1) * 4);
@@ -489,6 +568,49 @@ int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, const uint32_t* r
     LAUNCH(k_set_last<<<1, 1, 0, s>>>(prp, nscc, ndag));
     cudaMemcpyAsync(outcnt, prp, (size_t)nscc * 4, cudaMemcpyDeviceToDevice, s);
     if (ndag) LAUNCH(k_scatter_pred<<<grid_for(ndag), 256, 0, s>>>(dsrc, ddst, ndag, outcnt, pred));
+    // biggest-SCC refinement: the largest SCC, its descendants and ancestors
+    Refine rf{0xffffffffu, nullptr, nullptr, nullptr, nullptr};
+    if (refine && nscc > 1) {
+        uint32_t* desc = (uint32_t*)B.take(((size_t)nscc + 1) * 4);
+        uint32_t* anc = (uint32_t*)B.take(((size_t)nscc + 1) * 4);
+        uint32_t* Wm = (uint32_t*)B.take(((size_t)nscc + 1) * 4);
+        uint32_t* Q0 = (uint32_t*)B.take(((size_t)nscc + 1) * 4);
+        uint32_t* Q1 = (uint32_t*)B.take(((size_t)nscc + 1) * 4);
+        unsigned long long* rsum = (unsigned long long*)B.take(64);
+        uint32_t* dbig = (uint32_t*)B.take(64);
+        uint32_t* R32 = (uint32_t*)B.take(64);
+        if (!desc || !anc || !Wm || !Q0 || !Q1 || !rsum || !dbig || !R32) return -1;
+        cudaMemsetAsync(best, 0, 8, s);
+        LAUNCH(k_argmax_comp<<<grid_for(nscc), 256, 0, s>>>(wsz, nscc, best));
+        for (int dir = 0; dir < 2; ++dir) {     // 0: descendants, 1: ancestors
+            uint32_t* mark = dir ? anc : desc;
+            cudaMemsetAsync(mark, 0, (size_t)nscc * 4, s);
+            cudaMemsetAsync(&cnts[1], 0, 8, s);
+            LAUNCH(k_mark_seed<<<1, 1, 0, s>>>(best, mark, Q0, &cnts[1], dbig));
+            uint32_t *cur = Q0, *nxt = Q1, *cc = &cnts[1], *nc2 = &cnts[2];
+            for (;;) {
+                cudaMemsetAsync(nc2, 0, 4, s);
+                LAUNCH(k_dag_reach<<<grid_for((size_t)nscc * 32), 256, 0, s>>>(dir ? prp : drp, dir ? pred : ddst,
+                                                                               cur, cc, nxt, nc2, mark));
+                if (read_u32(nc2, &h, s)) return -1;
+                if (!h) break;
+                uint32_t* t = cur; cur = nxt; nxt = t;
+                uint32_t* tc = cc; cc = nc2; nc2 = tc;
+            }
+        }
+        cudaMemsetAsync(rsum, 0, 8, s);
+        LAUNCH(k_sum_marked<<<grid_for(nscc), 256, 0, s>>>(wsz, desc, nscc, rsum));
+        uint32_t hbig = 0;
+        unsigned long long hR = 0;
+        cudaMemcpyAsync(&hbig, dbig, 4, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&hR, rsum, 8, cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+        uint32_t R = (uint32_t)hR;
+        cudaMemcpyAsync(R32, &R, 4, cudaMemcpyHostToDevice, s);
+        // anc marks big itself (the BFS seed); the programme treats big apart
+        rf = Refine{hbig, R32, desc, anc, Wm};
+        if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+    }
     // alpha / omega, sinks first
     uint32_t* F0 = L0;
     uint32_t* F1 = color;         // labels were copied out to comp
@@ -500,7 +622,7 @@ int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, const uint32_t* r
     uint32_t done = 0;
     while (fcount) {
         done += fcount;
-        LAUNCH(k_dp_eval<<<grid_for(fcount), 256, 0, s>>>(cur, cc, drp, ddst, wsz, A, Om, n));
+        LAUNCH(k_dp_eval<<<grid_for(fcount), 256, 0, s>>>(cur, cc, drp, ddst, wsz, A, Om, n, rf));
         cudaMemsetAsync(nc, 0, 4, s);
         LAUNCH(k_dp_release<<<grid_for((size_t)fcount * 32), 256, 0, s>>>(cur, cc, prp, pred, outcnt, nxt, nc));
         if (read_u32(nc, &fcount, s)) return -1;

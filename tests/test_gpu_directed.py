@@ -46,10 +46,11 @@ def _partition(labels):
     return sorted(tuple(x) for x in groups.values())
 
 
-def test_scc_alpha_omega(B, gen, orc):
+@pytest.mark.parametrize("refined", [True, False])
+def test_scc_alpha_omega(B, gen, orc, refined):
     for g in directed_graphs(gen):
-        ocomp, oal, oom, onc = orc.alpha_omega(g)
-        with B.BcmGraph.from_graph(g) as h:
+        ocomp, oal, oom, onc = orc.alpha_omega_refined(g) if refined else orc.alpha_omega(g)
+        with B.BcmGraph.from_graph(g, flags=0 if refined else B.BCM_PLAIN_BOUNDS) as h:
             comp, al, om, nc = h.scc_bounds()
             order, lo, hi = h.preprocess()
         assert nc == onc, g.name
@@ -83,12 +84,13 @@ def test_topk_and_farness_directed(B, gen, orc, lanes):
                     assert np.array_equal(tf, f[exp]) and np.array_equal(tr, r[exp]), (g.name, k)
 
 
-def test_plain_equals_oracle_bcm_directed(B, gen, orc):
+@pytest.mark.parametrize("refined", [True, False])
+def test_plain_equals_oracle_bcm_directed(B, gen, orc, refined):
     for g in directed_graphs(gen):
-        with B.BcmGraph.from_graph(g) as h:
+        with B.BcmGraph.from_graph(g, flags=0 if refined else B.BCM_PLAIN_BOUNDS) as h:
             for k in (1, 4):
                 ids, gf, gr, st = h.topk(k, flags=B.BCM_PLAIN)
-                oi, of, orr, ost = orc.bcm(g, k, early_test=True)
+                oi, of, orr, ost = orc.bcm(g, k, early_test=True, refined=refined)
                 assert np.array_equal(ids, oi) and np.array_equal(gf, of), (g.name, k)
                 assert st["m_vis"] == ost["m_vis"] and st["cut"] == ost["cut"], (g.name, k)
 
@@ -96,7 +98,7 @@ def test_plain_equals_oracle_bcm_directed(B, gen, orc):
 def test_rmat_scale14(B, gen, orc):
     g = gen.rmat(14, 16, seed=3)
     f, r = orc.farness_all(g)
-    ocomp, oal, oom, onc = orc.alpha_omega(g)
+    ocomp, oal, oom, onc = orc.alpha_omega_refined(g)
     with B.BcmGraph.from_graph(g) as h:
         comp, al, om, nc = h.scc_bounds()
         assert nc == onc and np.array_equal(al, oal) and np.array_equal(om, oom)

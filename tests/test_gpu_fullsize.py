@@ -89,7 +89,7 @@ def rmat(gen):
 
 def test_rmat20_scc_and_bounds(B, gen, orc, rmat):
     g = rmat
-    ocomp, oal, oom, onc = orc.alpha_omega(g)
+    ocomp, oal, oom, onc = orc.alpha_omega_refined(g)
     with B.BcmGraph.from_graph(g) as h:
         comp, al, om, nc = h.scc_bounds()
     assert nc == onc
