@@ -187,6 +187,95 @@ def run_reference(args, rank, world):
     return 0
 
 
+# ------------------------------------------------------------------ serving
+SERVE_METRIC = "top-k closeness serving: requests/s with p50/p99 latency over a mix of device-resident graphs"
+
+
+def run_serve(args, rank, world):
+    """Serving with continuous batching (paper_1507_01490_gb300.serve): the
+    graph mix is built and made resident, the closed-loop capacity measured,
+    then Poisson streams at fractions of it are served; a sample of results is
+    checked against the same requests run alone."""
+    if rank != 0:
+        return 0
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1507_01490_gb300 import serve
+    t = time.perf_counter()
+    specs = serve.mix_specs(args.serve_graphs)
+    graphs = [serve.build_graph(sp) for sp in specs]
+    t_gen = time.perf_counter() - t
+    t = time.perf_counter()
+    be = serve.GpuBackend(graphs)
+    torch.cuda.synchronize()
+    t_load = time.perf_counter() - t
+    csr_bytes = int(sum(g.row_ptr.nbytes // 2 + g.col.nbytes for g in graphs))
+    budget = int(args.serve_budget_gb * (1 << 30))
+
+    def sched():
+        return serve.Scheduler(be, max_inflight=args.serve_inflight, hbm_budget=budget)
+
+    # warm-up: every graph once (first-use allocations), then a short closed loop
+    sched().run([serve.Request(i, i, 100, 0.0) for i in range(len(graphs))])
+    sched().run(serve.request_stream(min(500, args.serve_requests), len(graphs), float("inf"), seed=77))
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = __import__("paper_1507_01490_gb300.bcm", fromlist=["x"]).bcm_launch_count()
+    t = time.perf_counter()
+    s0 = sched()
+    cap_res = s0.run(serve.request_stream(args.serve_requests, len(graphs), float("inf"), seed=5))
+    cap_span = time.perf_counter() - t
+    capacity = len(cap_res) / cap_span
+    rates = []
+    last = None
+    for frac in [float(x) for x in args.serve_rates.split(",") if x]:
+        reqs = serve.request_stream(args.serve_requests, len(graphs), capacity * frac, seed=5)
+        sc = sched()
+        t = time.perf_counter()
+        res = sc.run(reqs)
+        span = time.perf_counter() - t
+        summ = serve.summarize(res, makespan=span)
+        summ.update({"frac_of_capacity": frac, "offered_rps": capacity * frac,
+                     "peak_inflight": sc.peak_inflight, "peak_workspace_gb": sc.peak_held / 2**30,
+                     "trims": sc.trims})
+        rates.append(summ)
+        last = res
+    launches = __import__("paper_1507_01490_gb300.bcm", fromlist=["x"]).bcm_launch_count() - l0
+    clk = clocks.stop()
+    # the same requests alone
+    rng = np.random.default_rng(3)
+    pick = rng.choice(len(last), size=min(args.serve_check, len(last)), replace=False)
+    same = True
+    for i in pick:
+        r = last[int(i)]
+        ids, far, reach, _ = be.alone(r.graph, r.k)
+        same = same and np.array_equal(ids, r.ids) and np.array_equal(far, r.farness) and \
+            np.array_equal(reach, r.reach)
+    top = rates[-1] if rates else serve.summarize(cap_res, makespan=cap_span)
+    line = {
+        "metric": SERVE_METRIC, "value": top["throughput_rps"], "unit": "requests/s", "n_gpus": 1,
+        "steps": len(rates), "warmup": 2, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "serving mix: %d graphs (first half Barabasi-Albert, second half R-MAT), n "
+                               "log-uniform in [1e3, 2e6], mean degree 8..16, seeds 1000+i; %d requests per rate, "
+                               "graph uniform, k uniform in {1,10,100}, Poisson arrivals (seed 5)"
+                               % (len(graphs), args.serve_requests),
+                   "max_inflight": args.serve_inflight, "hbm_budget_gb": args.serve_budget_gb,
+                   "graphs_resident_bytes": csr_bytes, "vertices": int(sum(g.n for g in graphs)),
+                   "arcs": int(sum(g.m for g in graphs))},
+        "capacity_rps": capacity, "capacity_latency_ms": serve.summarize(cap_res, cap_span)["latency_ms"],
+        "rates": rates,
+        "identical_alone_and_mixed": bool(same), "checked_requests": int(len(pick)),
+        "gpu_launches": launches, "clocks": clk,
+        "setup_s": {"generate": t_gen, "upload_and_preprocess": t_load},
+    }
+    be.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------------- ours
 def main():
     ap = argparse.ArgumentParser()
@@ -206,10 +295,19 @@ def main():
     ap.add_argument("--no-perk", action="store_true", help="skip the per-k timings")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
+    ap.add_argument("--serve", action="store_true", help="the serving benchmark (graph mix, request streams)")
+    ap.add_argument("--serve-graphs", type=int, default=200)
+    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-rates", default="0.5,0.8,1.0", help="fractions of the measured capacity")
+    ap.add_argument("--serve-inflight", type=int, default=16)
+    ap.add_argument("--serve-budget-gb", type=float, default=160.0)
+    ap.add_argument("--serve-check", type=int, default=300, help="results compared with the request alone")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.serve:
+        return run_serve(args, rank, world)
 
     import torch
     torch.cuda.set_device(local)

@@ -29,7 +29,8 @@
  *     memory unless BCM_OUT_DEVICE is set (then they are device memory on the
  *     current device).
  *   - Calls are synchronous: they return after the work on the graph's
- *     stream has finished, unless the name ends in _async.
+ *     stream has finished, except bcm_topk_start, which returns once the
+ *     run is enqueued (bcm_topk_finish completes it).
  *   - Every function returns a bcm_status; on failure bcm_last_error()
  *     returns a message for the calling thread.  No C++ exception crosses
  *     this interface.
@@ -57,7 +58,8 @@ typedef enum {
     BCM_ERR_OOM = 3,            /* device memory exhausted */
     BCM_ERR_CUDA = 4,           /* a CUDA call failed (message has the CUDA error) */
     BCM_ERR_TIMEOUT = 5,        /* a bounded in-kernel wait ran out */
-    BCM_ERR_UNSUPPORTED = 6     /* size or option outside the supported range */
+    BCM_ERR_UNSUPPORTED = 6,    /* size or option outside the supported range */
+    BCM_ERR_PENDING = 7         /* bcm_topk_finish(wait = 0): the run has not finished yet */
 } bcm_status;
 
 /* bcm_options.flags */
@@ -71,13 +73,19 @@ typedef enum {
 #define BCM_NO_PULL       0x40u /* grid-wide waves expand every level by push */
 #define BCM_PLAIN_BOUNDS  0x80u /* bcm_graph_create, digraphs: alpha/omega from the plain programme of
                                    Section 2.3, without its biggest-SCC refinement (results are the same) */
+#define BCM_TRACE         0x100u /* record the run's trace (read it with bcm_trace) */
+#define BCM_NO_DEFER      0x200u /* per-CTA waves never hand their sources to the grid-wide pass */
 
 /* Sources are taken from the degree order in waves.  Waves run first on a
  * grid-wide kernel (all CTAs on one wave) while they are heavy, then on a
  * per-CTA kernel (each CTA its own wave).  A grid wave is narrow when its
  * frontiers averaged fewer than heavy_words (vertex, 64-lane word) entries
- * per level; the first narrow one ends the grid phase.  Exhaustive runs
- * stay on the grid kernel.  Levels of grid waves run by push (each frontier vertex
+ * per level; the first narrow one ends the grid phase (a graph whose
+ * n * grid_lanes/64 is below heavy_words has no heavy wave, and its top-k
+ * runs skip the grid kernel).  A per-CTA wave that turns out wide after all
+ * is stopped and its sources run again on the grid kernel after the
+ * per-CTA phase (see defer_words).  Exhaustive runs stay on the grid
+ * kernel.  Levels of grid waves run by push (each frontier vertex
  * sets its lanes' bits in its out-neighbours) or, when the frontier is a
  * large share of the graph, by pull (each vertex with lanes still to reach
  * gathers them from its in-neighbours' frontier bits, with no atomics). */
@@ -85,13 +93,16 @@ typedef struct {
     uint32_t lanes;           /* sources per per-CTA wave: 64, 128 or 256; 0 = 64 */
     uint32_t grid_lanes;      /* sources per grid-wide wave: 64, 128 or 256; 0 = 128 */
     uint32_t flags;           /* BCM_* flags above */
-    uint32_t blocks;          /* CTAs of the per-CTA kernel; 0 = all that fit on the GPU */
+    uint32_t blocks;          /* CTAs of the per-CTA kernel; 0 = all that fit on the GPU, at most
+                                 one per wave of sources (ceil(n / lanes)) */
     uint32_t threads;         /* threads per CTA of the per-CTA kernel: 256, 512 or 1024; 0 = 512 */
     uint32_t heavy_words;     /* see above; 0 = default (4 per warp of the grid) */
     uint32_t pull_div;        /* a grid-wave level whose frontier holds at least n*W/pull_div words
                                  (W = grid_lanes/64) is expanded by pull; 0 = default
                                  (64 for bcm_topk, 16 for bcm_farness_all) */
-    uint32_t reserved;        /* 0 */
+    uint32_t defer_words;     /* a per-CTA wave whose next frontier reaches this many words stops
+                                 and hands its live sources to a second grid-wide pass, which
+                                 runs them from the start; 0 = default (heavy_words) */
     uint64_t wait_limit_ns;   /* limit of every in-kernel wait; 0 = default (20 s) */
 } bcm_options;
 
@@ -120,6 +131,7 @@ typedef struct {
     uint64_t grid_waves;      /* waves run by the grid-wide kernel */
     uint64_t grid_levels;     /* levels those waves expanded */
     uint64_t grid_bytes;      /* algorithmic bytes of the grid-wide kernel (same unit costs) */
+    uint64_t deferred;        /* sources per-CTA waves handed to the grid-wide pass */
 } bcm_stats;
 
 /*
@@ -183,6 +195,51 @@ bcm_status bcm_topk(bcm_graph_t g, uint32_t k, const bcm_options* opt, uint32_t*
                     uint64_t* farness, uint32_t* reach, bcm_stats* stats);
 
 /*
+ * bcm_topk_start / bcm_topk_finish -- bcm_topk in two halves, for callers
+ * that keep several graphs' runs in flight at once (each graph's work goes
+ * to its own stream, so runs on different graphs overlap on the device).
+ * bcm_topk_start takes bcm_topk's arguments, enqueues the run and the copies
+ * of its results on the graph's stream and returns without waiting.  The
+ * output arrays must stay valid until the run is finished; for the host
+ * copies to be asynchronous they must be pinned host memory (pageable
+ * memory works, but the copy then blocks the calling thread).  If the graph
+ * has not been preprocessed yet, that happens first, synchronously.
+ * bcm_topk_finish(wait = 1) waits for the run and returns its outcome, as
+ * bcm_topk would, filling stats (may be NULL); with wait = 0 it returns
+ * BCM_ERR_PENDING at once while the run is still going.  One run per graph:
+ * starting another run, bcm_farness_all, bcm_trace or bcm_graph_trim before
+ * the finish returns BCM_ERR_INVALID.  bcm_topk is start + finish(wait = 1).
+ */
+bcm_status bcm_topk_start(bcm_graph_t g, uint32_t k, const bcm_options* opt, uint32_t* ids,
+                          uint64_t* farness, uint32_t* reach);
+bcm_status bcm_topk_finish(bcm_graph_t g, int wait, bcm_stats* stats);
+
+/*
+ * bcm_trace -- the trace of the graph's last finished run made with
+ * BCM_TRACE (none otherwise).  Up to cap records of 4 uint64 each are
+ * copied to the host array records; *count receives how many records the
+ * run wrote (the library keeps the first 65,536).  Record words:
+ *   [0] time stamp (ns, the GPU's global timer)
+ *   [1] kind << 60 | id << 32 | level, kind one of
+ *       0  grid-wide level start  (id = wave; [2] frontier entries,
+ *                                  [3] live lanes | 1 << 32 if pulled)
+ *       1  grid-wide wave end     (id = wave; [2] words cleared,
+ *                                  [3] frontier entries over the wave)
+ *       2  per-CTA wave end       (id = CTA;  [2] words cleared,
+ *                                  [3] the wave's start time stamp)
+ * Records of one kind are in time order only per wave or CTA.
+ */
+bcm_status bcm_trace(bcm_graph_t g, uint64_t* records, uint32_t cap, uint32_t* count);
+
+/*
+ * bcm_graph_trim -- give back the graph's run workspace (wave-kernel slots,
+ * exhaustive outputs, plain-run buffers, trace): the slots go to a cache of
+ * clean regions that other graphs' runs reuse, the rest is freed.  The CSR
+ * and the preprocessing results stay.  The next run allocates again.
+ */
+bcm_status bcm_graph_trim(bcm_graph_t g);
+
+/*
  * bcm_farness_all -- f(v) and r(v) of every vertex by a complete BFS from
  * each one (the textbook algorithm of Section 2.1, no cut), n entries each,
  * indexed by vertex id.  opt may be NULL.
@@ -220,7 +277,8 @@ const char* bcm_last_error(void);
 uint64_t bcm_launch_count(void);
 
 /* Device bytes a bcm_topk / bcm_farness_all run on this graph holds with
- * these options (graph copy excluded); 0 on bad arguments. */
+ * these options (graph copy excluded; bcm_graph_trim gives back all but the
+ * preprocessing arrays); 0 on bad arguments. */
 uint64_t bcm_workspace_bytes(bcm_graph_t g, const bcm_options* opt);
 
 #ifdef __cplusplus

@@ -19,9 +19,9 @@ import numpy as np
 from . import _build
 
 BCM_OK, BCM_ERR_INVALID, BCM_ERR_NOT_SYMMETRIC, BCM_ERR_OOM, BCM_ERR_CUDA, BCM_ERR_TIMEOUT, \
-    BCM_ERR_UNSUPPORTED = range(7)
+    BCM_ERR_UNSUPPORTED, BCM_ERR_PENDING = range(8)
 STATUS_NAMES = {0: "BCM_OK", 1: "BCM_ERR_INVALID", 2: "BCM_ERR_NOT_SYMMETRIC", 3: "BCM_ERR_OOM",
-                4: "BCM_ERR_CUDA", 5: "BCM_ERR_TIMEOUT", 6: "BCM_ERR_UNSUPPORTED"}
+                4: "BCM_ERR_CUDA", 5: "BCM_ERR_TIMEOUT", 6: "BCM_ERR_UNSUPPORTED", 7: "BCM_ERR_PENDING"}
 
 BCM_OUT_DEVICE = 0x1
 BCM_NO_FOOTNOTE = 0x2
@@ -31,9 +31,15 @@ BCM_CHECK_SYMMETRIC = 0x10
 BCM_GRID_ONLY = 0x20
 BCM_NO_PULL = 0x40
 BCM_PLAIN_BOUNDS = 0x80
+BCM_TRACE = 0x100
+BCM_NO_DEFER = 0x200
+
+# trace record kinds (bits 60..63 of a record's second word)
+TRACE_GRID_LEVEL, TRACE_GRID_WAVE, TRACE_CTA_WAVE = 0, 1, 2
 
 # every symbol include/bcm.h declares
 EXPORTS = ["bcm_graph_create", "bcm_graph_destroy", "bcm_preprocess", "bcm_scc_bounds", "bcm_topk",
+           "bcm_topk_start", "bcm_topk_finish", "bcm_trace", "bcm_graph_trim",
            "bcm_farness_all", "bcm_farness_all_noalloc", "bcm_last_error", "bcm_launch_count",
            "bcm_workspace_bytes"]
 
@@ -41,7 +47,7 @@ EXPORTS = ["bcm_graph_create", "bcm_graph_destroy", "bcm_preprocess", "bcm_scc_b
 class bcm_options(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_uint32), ("grid_lanes", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("blocks", ctypes.c_uint32), ("threads", ctypes.c_uint32), ("heavy_words", ctypes.c_uint32),
-                ("pull_div", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("wait_limit_ns", ctypes.c_uint64)]
+                ("pull_div", ctypes.c_uint32), ("defer_words", ctypes.c_uint32), ("wait_limit_ns", ctypes.c_uint64)]
 
 
 class bcm_stats(ctypes.Structure):
@@ -53,7 +59,7 @@ class bcm_stats(ctypes.Structure):
                 ("kernel_ms", ctypes.c_double), ("preprocess_ms", ctypes.c_double),
                 ("total_ms", ctypes.c_double), ("seed_ms", ctypes.c_double), ("wave_ms", ctypes.c_double),
                 ("wave_bytes", ctypes.c_uint64), ("grid_waves", ctypes.c_uint64),
-                ("grid_levels", ctypes.c_uint64), ("grid_bytes", ctypes.c_uint64)]
+                ("grid_levels", ctypes.c_uint64), ("grid_bytes", ctypes.c_uint64), ("deferred", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -86,6 +92,10 @@ def load():
         "bcm_preprocess": (i32, [vp, vp, vp, vp, i32]),
         "bcm_scc_bounds": (i32, [vp, vp, vp, vp, vp, i32]),
         "bcm_topk": (i32, [vp, u32, ctypes.POINTER(bcm_options), vp, vp, vp, ctypes.POINTER(bcm_stats)]),
+        "bcm_topk_start": (i32, [vp, u32, ctypes.POINTER(bcm_options), vp, vp, vp]),
+        "bcm_topk_finish": (i32, [vp, i32, ctypes.POINTER(bcm_stats)]),
+        "bcm_trace": (i32, [vp, vp, u32, ctypes.POINTER(u32)]),
+        "bcm_graph_trim": (i32, [vp]),
         "bcm_farness_all": (i32, [vp, ctypes.POINTER(bcm_options), vp, vp, ctypes.POINTER(bcm_stats)]),
         "bcm_farness_all_noalloc": (i32, [vp, vp, u32, u64, vp, vp, vp]),
         "bcm_last_error": (ctypes.c_char_p, []),
@@ -130,8 +140,8 @@ def bcm_launch_count() -> int:
 
 
 def make_options(lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0, grid_lanes=0,
-                 heavy_words=0, pull_div=0) -> bcm_options:
-    return bcm_options(lanes, grid_lanes, flags, blocks, threads, heavy_words, pull_div, 0, wait_limit_ns)
+                 heavy_words=0, pull_div=0, defer_words=0) -> bcm_options:
+    return bcm_options(lanes, grid_lanes, flags, blocks, threads, heavy_words, pull_div, defer_words, wait_limit_ns)
 
 
 def bcm_graph_create(row_ptr, col, n, m, directed, ptr_on_device=False, stream=None, flags=0):
@@ -164,6 +174,34 @@ def bcm_scc_bounds(h, comp=None, alpha=None, omega=None, out_on_device=False):
 def bcm_topk(h, k, options, ids, farness, reach, stats=None):
     _check(load().bcm_topk(h, k, ctypes.byref(options) if options is not None else None, _ptr(ids),
                            _ptr(farness), _ptr(reach), ctypes.byref(stats) if stats is not None else None))
+
+
+def bcm_topk_start(h, k, options, ids, farness, reach):
+    _check(load().bcm_topk_start(h, k, ctypes.byref(options) if options is not None else None, _ptr(ids),
+                                 _ptr(farness), _ptr(reach)))
+
+
+def bcm_topk_finish(h, wait=True, stats=None) -> bool:
+    """True once the run has finished (its errors raise); False while it is
+    still going (only with wait=False)."""
+    st = load().bcm_topk_finish(h, int(bool(wait)), ctypes.byref(stats) if stats is not None else None)
+    if st == BCM_ERR_PENDING:
+        return False
+    _check(st)
+    return True
+
+
+def bcm_trace(h, cap=1 << 16):
+    """The last traced run's records as a (count, 4) uint64 array, and how
+    many records the run wrote."""
+    buf = np.zeros((max(cap, 1), 4), np.uint64)
+    count = ctypes.c_uint32(0)
+    _check(load().bcm_trace(h, _ptr(buf), cap, ctypes.byref(count)))
+    return buf[:min(int(count.value), cap)], int(count.value)
+
+
+def bcm_graph_trim(h):
+    _check(load().bcm_graph_trim(h))
 
 
 def bcm_farness_all(h, options, farness, reach, stats=None):
@@ -233,16 +271,22 @@ class BcmGraph:
         return comp[:self.n], al[:self.n], om[:self.n], nc
 
     def topk(self, k, lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0, grid_lanes=0, heavy_words=0,
-             pull_div=0):
+             pull_div=0, defer_words=0):
         kk = max(min(k, self.n), 1)
         ids = np.zeros(kk, np.uint32)
         far = np.zeros(kk, np.uint64)
         reach = np.zeros(kk, np.uint32)
         st = bcm_stats()
         bcm_topk(self.h, k, make_options(lanes, flags, blocks, threads, wait_limit_ns, grid_lanes, heavy_words,
-                                         pull_div), ids, far, reach, st)
+                                         pull_div, defer_words), ids, far, reach, st)
         kk = min(k, self.n)
         return ids[:kk], far[:kk], reach[:kk], st.as_dict()
+
+    def trace(self):
+        return bcm_trace(self.h)
+
+    def trim(self):
+        bcm_graph_trim(self.h)
 
     def farness_all(self, lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0, grid_lanes=0, pull_div=0):
         far = np.zeros(max(self.n, 1), np.uint64)

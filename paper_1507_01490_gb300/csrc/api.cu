@@ -48,7 +48,7 @@ static bcm_status cuda_fail(cudaError_t e, const char* what) {
     } while (0)
 
 // ---------------------------------------------------------- workspaces
-// The slot region of the wave kernels is large (36 n W bytes per CTA) and
+// The slot region of the wave kernels is large (44 n W bytes per CTA) and
 // must start zeroed; every successful run leaves it zeroed again.  Clean
 // regions are kept here for reuse instead of being freed and re-zeroed.
 // A region is only known to be zero under the slot layout it was last used
@@ -86,7 +86,8 @@ static bcm_status region_acquire(size_t bytes, const Layout& lay, cudaStream_t s
     }
     if (out->ptr) {
         if (!(out->layout == lay)) {
-            CU(cudaMemsetAsync(out->ptr, 0, out->bytes, s), "workspace clear");
+            // only the layout's own bytes must be zero; the rest is unused under it
+            CU(cudaMemsetAsync(out->ptr, 0, bytes, s), "workspace clear");
             out->layout = lay;
         }
         return BCM_OK;
@@ -151,7 +152,23 @@ struct Aux {
     uint32_t glist_n[2];
     uint32_t glog_n;
     uint32_t gchunk[2];
+    uint32_t trace_n;
+    uint32_t defer_n;     // sources handed back by per-CTA waves
+    uint32_t head2;       // queue head of the grid-wide pass over them
 };
+
+// Host side of a run in flight: pinned memory the run's counters are copied
+// into, read once the run's last event has completed.
+struct HostBlock {
+    int err;
+    uint32_t topk_count;
+    uint32_t trace_n;
+    uint32_t pad;
+    unsigned long long stats[ST_COUNT];        // per-CTA wave kernel
+    unsigned long long seed_stats[ST_COUNT];   // grid-wide or plain kernel
+};
+
+constexpr uint32_t kTraceCap = 1u << 16;   // trace records kept per run
 
 }  // namespace bcm
 
@@ -181,6 +198,23 @@ struct bcm_graph {
     uint32_t* d_reach = nullptr;
     Region slots{0, nullptr, 0, Layout{}};
     int sms = 0;
+    // the run started by bcm_topk_start (or a synchronous call) until finished
+    struct Pending {
+        bool active = false;
+        bool exhaustive = false;
+        bool plain = false;
+        uint32_t kk = 0;          // entries the top-k must hold
+        uint32_t flags = 0;
+        uint64_t l0 = 0;          // launch counter at the start
+        double pms = 0;           // preprocessing time of this call
+        std::chrono::steady_clock::time_point t0;
+    } pend;
+    // start, first grid pass done, per-CTA pass done, deferred grid pass done, copies done
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    uint32_t* d_defer = nullptr;   // [n] sources deferred by per-CTA waves
+    HostBlock* h = nullptr;        // pinned
+    unsigned long long* d_trace = nullptr;   // kTraceCap records of 4 words
+    uint32_t trace_n = 0;          // records of the last finished traced run
 };
 
 namespace {
@@ -191,6 +225,7 @@ struct Cfg {
     int W, threads, blocks, grid_W, grid_blocks;
     uint32_t pull_div;
     uint64_t heavy_words;
+    uint64_t defer_words;
     uint64_t limit_ns;
     uint32_t flags;
 };
@@ -211,7 +246,10 @@ bcm_status resolve(bcm_graph* g, const bcm_options* opt, Cfg* c) {
     int per = cta_blocks_per_sm(c->W, c->threads);
     if (per < 1) return fail(BCM_ERR_CUDA, "wave kernel does not fit on an SM");
     int maxb = per * g->sms;
-    c->blocks = o.blocks ? (int)o.blocks : maxb;
+    // default: every CTA that fits, but no more than there are waves of
+    // sources (a small graph then holds a small workspace)
+    uint64_t waves = ((uint64_t)g->n + 64 * c->W - 1) / (64 * c->W);
+    c->blocks = o.blocks ? (int)o.blocks : (waves < (uint64_t)maxb ? (int)(waves ? waves : 1) : maxb);
     if (c->blocks > maxb) c->blocks = maxb;
     c->limit_ns = o.wait_limit_ns ? o.wait_limit_ns : kDefaultLimitNs;
     uint32_t glanes = o.grid_lanes ? o.grid_lanes : 128;
@@ -223,6 +261,7 @@ bcm_status resolve(bcm_graph* g, const bcm_options* opt, Cfg* c) {
     c->grid_blocks = gb;
     c->heavy_words = o.heavy_words ? o.heavy_words : (uint64_t)gb * 16 * 4;   // 4 words per warp and level
     c->pull_div = (c->flags & BCM_NO_PULL) ? 0u : o.pull_div;   // 0: per-mode default below
+    c->defer_words = (c->flags & BCM_NO_DEFER) ? 0 : (o.defer_words ? o.defer_words : c->heavy_words);
     if ((c->flags & BCM_CTA_ONLY) && (c->flags & BCM_GRID_ONLY))
         return fail(BCM_ERR_INVALID, "BCM_CTA_ONLY and BCM_GRID_ONLY exclude each other");
     return BCM_OK;
@@ -250,7 +289,7 @@ bcm_status ensure_slots(bcm_graph* g, const Cfg& c) {
     Layout lay = region_layout(g, c);
     if (g->slots.ptr && g->slots.bytes >= bytes) {
         if (!(g->slots.layout == lay)) {
-            CU(cudaMemsetAsync(g->slots.ptr, 0, g->slots.bytes, g->stream), "workspace clear");
+            CU(cudaMemsetAsync(g->slots.ptr, 0, bytes, g->stream), "workspace clear");
             g->slots.layout = lay;
         }
         return BCM_OK;
@@ -397,6 +436,7 @@ WaveParams base_params(bcm_graph* g, const Cfg& c) {
     p.g.rcol = g->directed ? g->d_rcol : g->d_col;
     p.footnote = (!g->directed && !(c.flags & BCM_NO_FOOTNOTE)) ? 1u : 0u;
     Aux* a = g->d_aux;
+    p.sources = g->d_order;
     p.head = &a->head;
     p.n_end = g->n;
     p.topk.id = a->topk_id;
@@ -445,57 +485,89 @@ void fill_stats(bcm_stats* s, const unsigned long long* st, uint64_t launches, d
     s->arc_words = st[ST_ARCWORDS];
     s->new_words = st[ST_DISCWORDS];
     s->cleared_words = st[ST_CLEARED];
+    s->deferred = st[ST_DEFERRED];
     s->launches = launches;
     s->kernel_ms = kms;
     s->preprocess_ms = pms;
     s->total_ms = tms;
 }
 
-// Runs the wave kernels.  exhaustive: every source, no cut; else top-k.
+// Times and counters of a finished run.
 struct RunTimes {
     double kernel_ms = 0, seed_ms = 0, wave_ms = 0;
     unsigned long long grid[ST_COUNT] = {0};
 };
 
-bcm_status run_waves(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, unsigned long long* stats_out,
-                     unsigned long long* wave_stats_out, RunTimes* times) {
+bcm_status copy_out(void* dst, const void* src, size_t bytes, bool dev, cudaStream_t s);
+
+bcm_status ensure_run_state(bcm_graph* g, bool trace) {
+    for (int i = 0; i < 5; ++i)
+        if (!g->ev[i]) CU(cudaEventCreate(&g->ev[i]), "event");
+    if (!g->h) CU(cudaMallocHost(&g->h, sizeof(HostBlock)), "pinned host allocation");
+    if (trace && !g->d_trace) CU(cudaMalloc(&g->d_trace, (size_t)kTraceCap * 4 * sizeof(u64)), "trace allocation");
+    return BCM_OK;
+}
+
+// Enqueues one run of the wave kernels on the graph's stream and the copies
+// of its results and counters, and returns without waiting.  exhaustive:
+// every source, no cut, outputs o_far/o_reach (n entries); else top-k with
+// outputs o_ids/o_far/o_reach (min(k, n) entries).
+bcm_status start_run(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, void* o_ids, void* o_far,
+                     void* o_reach) {
     cudaStream_t s = g->stream;
+    const bool trace = (c.flags & BCM_TRACE) != 0;
     bcm_status st = ensure_aux(g);
     if (st) return st;
+    if ((st = ensure_run_state(g, trace))) return st;
     const bool plain = !exhaustive && (c.flags & BCM_PLAIN);
-    if (!plain) {
-        st = ensure_slots(g, c);
-        if (st) return st;
-    }
-    CU(cudaMemsetAsync(g->d_aux, 0, sizeof(Aux), s), "aux clear");
+    if (!plain && (st = ensure_slots(g, c))) return st;
     if (exhaustive && !g->d_far) {
         CU(cudaMalloc(&g->d_far, (size_t)g->n * sizeof(uint64_t) + 256), "output allocation");
         CU(cudaMalloc(&g->d_reach, (size_t)g->n * sizeof(uint32_t) + 256), "output allocation");
     }
+    if (plain && !g->d_plain)
+        CU(cudaMalloc(&g->d_plain, (size_t)g->n * 3 * sizeof(uint32_t) + 256), "plain buffers");
+    CU(cudaMemsetAsync(g->d_aux, 0, sizeof(Aux), s), "aux clear");
     WaveParams p = base_params(g, c);
     p.exhaustive = exhaustive ? 1u : 0u;
     p.topk.k = k;
     p.out_far = g->d_far;
     p.out_reach = g->d_reach;
-    cudaEvent_t e0, em, e1;
-    CU(cudaEventCreate(&e0), "event");
-    CU(cudaEventCreate(&em), "event");
-    CU(cudaEventCreate(&e1), "event");
-    CU(cudaEventRecord(e0, s), "event record");
+    if (trace) {
+        p.trace = g->d_trace;
+        p.trace_cap = kTraceCap;
+        p.trace_n = &g->d_aux->trace_n;
+    }
+    CU(cudaEventRecord(g->ev[0], s), "event record");
     int rc = 0;
     p.stats = g->d_aux->seed_stats;
     if (plain) {
-        if (!g->d_plain) CU(cudaMalloc(&g->d_plain, (size_t)g->n * 3 * sizeof(uint32_t) + 256), "plain buffers");
         CU(cudaMemsetAsync(g->d_plain, 0, (size_t)g->n * sizeof(uint32_t), s), "stamp clear");
         int blocks = max_coop_blocks(1, 1, 256);
         int want = g->sms;   // one 256-thread CTA per SM
         if (blocks > want) blocks = want;
         for (uint32_t it = 0; it < g->n && rc == 0; ++it)
             rc = launch_plain_source(p, it, g->d_plain, g->d_plain + g->n, blocks, 256, s);
+        cudaEventRecord(g->ev[1], s);
     } else {
         // grid-wide waves while they are heavy (every wave for exhaustive
-        // runs), then per-CTA waves from wherever the grid kernel left head
-        if (!(c.flags & BCM_CTA_ONLY)) {
+        // runs), then per-CTA waves from wherever the grid kernel left head.
+        // A top-k run on a graph with fewer (vertex, word) pairs than the
+        // heavy threshold cannot have a heavy wave and skips the grid kernel.
+        const bool grid = !(c.flags & BCM_CTA_ONLY) &&
+                          (exhaustive || (c.flags & BCM_GRID_ONLY) || (uint64_t)g->n * c.grid_W >= c.heavy_words);
+        // a per-CTA wave whose frontier grows to defer_words words hands its
+        // sources to a second grid-wide pass (only where one can follow, and
+        // only if a frontier that wide is possible)
+        const bool defer = !exhaustive && !(c.flags & (BCM_CTA_ONLY | BCM_GRID_ONLY)) && c.defer_words &&
+                           (uint64_t)g->n * c.W >= c.defer_words;
+        if (defer) {
+            if (!g->d_defer) CU(cudaMalloc(&g->d_defer, (size_t)g->n * sizeof(uint32_t)), "defer list allocation");
+            p.defer_words = (uint32_t)(c.defer_words < 0xffffffffull ? c.defer_words : 0xffffffffull);
+            p.defer_n = &g->d_aux->defer_n;
+            p.defer_src = g->d_defer;
+        }
+        if (grid) {
             p.max_grid_waves = 0xffffffffu;
             p.heavy_words = (exhaustive || (c.flags & BCM_GRID_ONLY)) ? 0 : c.heavy_words;
             // defaults measured on the Chung-Lu workloads: top-k grid waves
@@ -503,45 +575,108 @@ bcm_status run_waves(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, un
             p.pull_div = (c.flags & BCM_NO_PULL) ? 0u : (c.pull_div ? c.pull_div : (exhaustive ? 16u : 64u));
             rc = launch_grid_waves(p, c.grid_W, c.grid_blocks, 512, s);
         }
-        cudaEventRecord(em, s);
+        cudaEventRecord(g->ev[1], s);
         p.stats = g->d_aux->stats;
         if (rc == 0) rc = launch_cta_waves(p, c.W, c.blocks, c.threads, s);
+        cudaEventRecord(g->ev[2], s);
+        if (defer && rc == 0) {
+            // the deferred sources, on the grid kernel, every wave
+            WaveParams q = p;
+            q.sources = g->d_defer;
+            q.head = &g->d_aux->head2;
+            q.n_end = 0;
+            q.n_end_dev = &g->d_aux->defer_n;
+            q.max_grid_waves = 0xffffffffu;
+            q.heavy_words = 0;
+            q.defer_words = 0;
+            q.pull_div = (c.flags & BCM_NO_PULL) ? 0u : (c.pull_div ? c.pull_div : 64u);
+            q.stats = g->d_aux->seed_stats;
+            rc = launch_grid_waves(q, c.grid_W, c.grid_blocks, 512, s);
+        }
     }
-    if (plain) cudaEventRecord(em, s);
-    cudaEventRecord(e1, s);
+    if (plain) cudaEventRecord(g->ev[2], s);
+    cudaEventRecord(g->ev[3], s);
     if (rc) {
         cudaStreamSynchronize(s);
         return fail(BCM_ERR_CUDA, "wave kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     }
-    int herr = 0;
-    unsigned long long seed_st[ST_COUNT];
-    CU(cudaMemcpyAsync(&herr, &g->d_aux->err, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
-    CU(cudaMemcpyAsync(wave_stats_out, g->d_aux->stats, sizeof(unsigned long long) * ST_COUNT,
-                       cudaMemcpyDeviceToHost, s), "copy");
-    CU(cudaMemcpyAsync(seed_st, g->d_aux->seed_stats, sizeof(unsigned long long) * ST_COUNT,
-                       cudaMemcpyDeviceToHost, s), "copy");
-    cudaError_t se = cudaStreamSynchronize(s);
-    float t = 0, t0m = 0, tm1 = 0;
-    cudaEventElapsedTime(&t, e0, e1);
-    cudaEventElapsedTime(&t0m, e0, em);
-    cudaEventElapsedTime(&tm1, em, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(em);
-    cudaEventDestroy(e1);
+    Aux* a = g->d_aux;
+    HostBlock* h = g->h;
+    CU(cudaMemcpyAsync(&h->err, &a->err, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+    CU(cudaMemcpyAsync(&h->topk_count, &a->topk_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "copy");
+    CU(cudaMemcpyAsync(&h->trace_n, &a->trace_n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "copy");
+    CU(cudaMemcpyAsync(h->stats, a->stats, sizeof(h->stats), cudaMemcpyDeviceToHost, s), "copy");
+    CU(cudaMemcpyAsync(h->seed_stats, a->seed_stats, sizeof(h->seed_stats), cudaMemcpyDeviceToHost, s), "copy");
+    const bool dev = (c.flags & BCM_OUT_DEVICE) != 0;
+    if (exhaustive) {
+        if ((st = copy_out(o_far, g->d_far, (size_t)g->n * sizeof(uint64_t), dev, s))) return st;
+        if ((st = copy_out(o_reach, g->d_reach, (size_t)g->n * sizeof(uint32_t), dev, s))) return st;
+    } else {
+        const uint32_t kk = k < g->n ? k : g->n;
+        if ((st = copy_out(o_ids, a->topk_id, kk * sizeof(uint32_t), dev, s))) return st;
+        if ((st = copy_out(o_far, a->topk_f, kk * sizeof(uint64_t), dev, s))) return st;
+        if ((st = copy_out(o_reach, a->topk_r, kk * sizeof(uint32_t), dev, s))) return st;
+    }
+    CU(cudaEventRecord(g->ev[4], s), "event record");
+    g->pend.active = true;
+    g->pend.exhaustive = exhaustive;
+    g->pend.plain = plain;
+    g->pend.kk = k < g->n ? k : g->n;
+    g->pend.flags = c.flags;
+    return BCM_OK;
+}
+
+// Completes the pending run: BCM_ERR_PENDING if !wait and it has not
+// finished, else its outcome, with its counters in sv (both kernels),
+// wv (per-CTA kernel) and rt.
+bcm_status finish_run(bcm_graph* g, bool wait, unsigned long long* sv, unsigned long long* wv, RunTimes* rt) {
+    if (!g->pend.active) return fail(BCM_ERR_INVALID, "no run is pending on this graph");
+    if (!wait) {
+        cudaError_t q = cudaEventQuery(g->ev[4]);
+        if (q == cudaErrorNotReady) return BCM_ERR_PENDING;
+        if (q != cudaSuccess) { g->pend.active = false; return cuda_fail(q, "wave kernels"); }
+    }
+    cudaError_t se = cudaEventSynchronize(g->ev[4]);
+    g->pend.active = false;
     if (se != cudaSuccess) return cuda_fail(se, "wave kernels");
-    for (int i = 0; i < ST_COUNT; ++i)
-        stats_out[i] = (i == ST_MAXLEVEL) ? (wave_stats_out[i] > seed_st[i] ? wave_stats_out[i] : seed_st[i])
-                                          : wave_stats_out[i] + seed_st[i];
-    times->kernel_ms = t;
-    times->seed_ms = t0m;
-    times->wave_ms = tm1;
-    for (int i = 0; i < ST_COUNT; ++i) times->grid[i] = seed_st[i];
-    if (herr) {
+    const HostBlock* h = g->h;
+    float t = 0, t01 = 0, t12 = 0, t23 = 0;
+    cudaEventElapsedTime(&t, g->ev[0], g->ev[3]);
+    cudaEventElapsedTime(&t01, g->ev[0], g->ev[1]);
+    cudaEventElapsedTime(&t12, g->ev[1], g->ev[2]);
+    cudaEventElapsedTime(&t23, g->ev[2], g->ev[3]);
+    const float t0m = t01 + t23, tm1 = t12;
+    for (int i = 0; i < ST_COUNT; ++i) {
+        wv[i] = h->stats[i];
+        sv[i] = (i == ST_MAXLEVEL) ? (h->stats[i] > h->seed_stats[i] ? h->stats[i] : h->seed_stats[i])
+                                   : h->stats[i] + h->seed_stats[i];
+        rt->grid[i] = h->seed_stats[i];
+    }
+    rt->kernel_ms = t;
+    rt->seed_ms = t0m;
+    rt->wave_ms = tm1;
+    g->trace_n = (g->pend.flags & BCM_TRACE) ? h->trace_n : 0;
+    if (h->err) {
         // a timed-out run may leave words set: do not reuse the region
         region_release(g->slots, false);
-        return check_dev_err(herr);
+        return check_dev_err(h->err);
     }
+    if (!g->pend.exhaustive && h->topk_count != g->pend.kk)
+        return fail(BCM_ERR_CUDA, "top-k holds %u entries, expected %u", h->topk_count, g->pend.kk);
     return BCM_OK;
+}
+
+void fill_run_stats(bcm_stats* stats, bcm_graph* g, const unsigned long long* sv, const unsigned long long* wv,
+                    const RunTimes& rt) {
+    if (!stats) return;
+    fill_stats(stats, sv, g_launches.load() - g->pend.l0, rt.kernel_ms, g->pend.pms, ms_since(g->pend.t0));
+    const bool plain = g->pend.plain;
+    stats->seed_ms = rt.seed_ms;
+    stats->wave_ms = rt.wave_ms;
+    stats->wave_bytes = plain ? 0 : wave_alg_bytes(wv, wv[ST_COMPLETED] + wv[ST_CUT]);
+    stats->grid_waves = rt.grid[ST_WAVES];
+    stats->grid_levels = rt.grid[ST_LEVELS];
+    stats->grid_bytes = plain ? 0 : wave_alg_bytes(rt.grid, rt.grid[ST_COMPLETED] + rt.grid[ST_CUT]);
 }
 
 bcm_status copy_out(void* dst, const void* src, size_t bytes, bool dev, cudaStream_t s) {
@@ -681,7 +816,13 @@ bcm_status bcm_graph_destroy(bcm_graph_t g) {
     cudaFree(g->d_reach);
     cudaFree(g->d_rrp);
     cudaFree(g->d_rcol);
-    region_release(g->slots, true);
+    cudaFree(g->d_trace);
+    cudaFree(g->d_defer);
+    for (int i = 0; i < 5; ++i)
+        if (g->ev[i]) cudaEventDestroy(g->ev[i]);
+    if (g->h) cudaFreeHost(g->h);
+    // a run that was started and never finished may not have left the region clean
+    region_release(g->slots, !g->pend.active);
     delete g;
     return BCM_OK;
 }
@@ -722,45 +863,55 @@ bcm_status bcm_scc_bounds(bcm_graph_t g, uint32_t* comp, uint32_t* alpha, uint32
     return BCM_OK;
 }
 
-bcm_status bcm_topk(bcm_graph_t g, uint32_t k, const bcm_options* opt, uint32_t* ids, uint64_t* farness,
-                    uint32_t* reach, bcm_stats* stats) {
+bcm_status bcm_topk_start(bcm_graph_t g, uint32_t k, const bcm_options* opt, uint32_t* ids, uint64_t* farness,
+                          uint32_t* reach) {
     t_err.clear();
     auto t0 = std::chrono::steady_clock::now();
     uint64_t l0 = g_launches.load();
     if (!g) return fail(BCM_ERR_INVALID, "graph is NULL");
+    if (g->pend.active) return fail(BCM_ERR_INVALID, "a run on this graph has not been finished");
     if (k < 1 || k > 1024) return fail(BCM_ERR_INVALID, "k = %u: must be in 1..1024", k);
     if (!ids || !farness || !reach) return fail(BCM_ERR_INVALID, "output pointer is NULL");
-    double pms = 0, kms = 0;
+    double pms = 0;
     bcm_status st = preprocess(g, &pms);
     if (st) return st;
     Cfg c;
     if ((st = resolve(g, opt, &c))) return st;
+    if (g->n > 0) {
+        if ((st = start_run(g, c, k, false, ids, farness, reach))) return st;
+    } else {
+        // nothing to run: the empty result is complete at once
+        if ((st = ensure_run_state(g, false))) return st;
+        memset(g->h, 0, sizeof(HostBlock));
+        for (int i = 0; i < 5; ++i) CU(cudaEventRecord(g->ev[i], g->stream), "event record");
+        g->pend.active = true;
+        g->pend.exhaustive = false;
+        g->pend.plain = false;
+        g->pend.kk = 0;
+        g->pend.flags = 0;
+    }
+    g->pend.l0 = l0;
+    g->pend.pms = pms;
+    g->pend.t0 = t0;
+    return BCM_OK;
+}
+
+bcm_status bcm_topk_finish(bcm_graph_t g, int wait, bcm_stats* stats) {
+    t_err.clear();
+    if (!g) return fail(BCM_ERR_INVALID, "graph is NULL");
     unsigned long long sv[ST_COUNT] = {0}, wv[ST_COUNT] = {0};
     RunTimes rt;
-    uint32_t kk = k < g->n ? k : g->n;
-    if (g->n > 0) {
-        if ((st = run_waves(g, c, k, false, sv, wv, &rt))) return st;
-        kms = rt.kernel_ms;
-        bool dev = (c.flags & BCM_OUT_DEVICE) != 0;
-        Aux* a = g->d_aux;
-        if ((st = copy_out(ids, a->topk_id, kk * sizeof(uint32_t), dev, g->stream))) return st;
-        if ((st = copy_out(farness, a->topk_f, kk * sizeof(uint64_t), dev, g->stream))) return st;
-        if ((st = copy_out(reach, a->topk_r, kk * sizeof(uint32_t), dev, g->stream))) return st;
-        uint32_t cnt = 0;
-        CU(cudaMemcpyAsync(&cnt, &a->topk_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream), "copy");
-        CU(cudaStreamSynchronize(g->stream), "copy");
-        if (cnt != kk) return fail(BCM_ERR_CUDA, "top-k holds %u entries, expected %u", cnt, kk);
-    }
-    fill_stats(stats, sv, g_launches.load() - l0, kms, pms, ms_since(t0));
-    if (stats) {
-        stats->seed_ms = rt.seed_ms;
-        stats->wave_ms = rt.wave_ms;
-        stats->wave_bytes = (c.flags & BCM_PLAIN) ? 0 : wave_alg_bytes(wv, wv[ST_COMPLETED] + wv[ST_CUT]);
-        stats->grid_waves = rt.grid[ST_WAVES];
-        stats->grid_levels = rt.grid[ST_LEVELS];
-        stats->grid_bytes = (c.flags & BCM_PLAIN) ? 0 : wave_alg_bytes(rt.grid, rt.grid[ST_COMPLETED] + rt.grid[ST_CUT]);
-    }
-    return BCM_OK;
+    bcm_status st = finish_run(g, wait != 0, sv, wv, &rt);
+    if (st == BCM_ERR_PENDING) return st;
+    if (st == BCM_OK) fill_run_stats(stats, g, sv, wv, rt);
+    return st;
+}
+
+bcm_status bcm_topk(bcm_graph_t g, uint32_t k, const bcm_options* opt, uint32_t* ids, uint64_t* farness,
+                    uint32_t* reach, bcm_stats* stats) {
+    bcm_status st = bcm_topk_start(g, k, opt, ids, farness, reach);
+    if (st) return st;
+    return bcm_topk_finish(g, 1, stats);
 }
 
 bcm_status bcm_farness_all(bcm_graph_t g, const bcm_options* opt, uint64_t* farness, uint32_t* reach,
@@ -769,8 +920,9 @@ bcm_status bcm_farness_all(bcm_graph_t g, const bcm_options* opt, uint64_t* farn
     auto t0 = std::chrono::steady_clock::now();
     uint64_t l0 = g_launches.load();
     if (!g) return fail(BCM_ERR_INVALID, "graph is NULL");
+    if (g->pend.active) return fail(BCM_ERR_INVALID, "a run on this graph has not been finished");
     if (!farness || !reach) return fail(BCM_ERR_INVALID, "output pointer is NULL");
-    double pms = 0, kms = 0;
+    double pms = 0;
     bcm_status st = preprocess(g, &pms);
     if (st) return st;
     Cfg c;
@@ -778,22 +930,55 @@ bcm_status bcm_farness_all(bcm_graph_t g, const bcm_options* opt, uint64_t* farn
     unsigned long long sv[ST_COUNT] = {0}, wv[ST_COUNT] = {0};
     RunTimes rt;
     if (g->n > 0) {
-        if ((st = run_waves(g, c, 0, true, sv, wv, &rt))) return st;
-        kms = rt.kernel_ms;
-        bool dev = (c.flags & BCM_OUT_DEVICE) != 0;
-        if ((st = copy_out(farness, g->d_far, (size_t)g->n * sizeof(uint64_t), dev, g->stream))) return st;
-        if ((st = copy_out(reach, g->d_reach, (size_t)g->n * sizeof(uint32_t), dev, g->stream))) return st;
-        CU(cudaStreamSynchronize(g->stream), "copy");
+        if ((st = start_run(g, c, 0, true, nullptr, farness, reach))) return st;
+        g->pend.l0 = l0;
+        g->pend.pms = pms;
+        g->pend.t0 = t0;
+        if ((st = finish_run(g, true, sv, wv, &rt))) return st;
+        fill_run_stats(stats, g, sv, wv, rt);
+    } else if (stats) {
+        g->pend.l0 = l0;
+        g->pend.pms = pms;
+        g->pend.t0 = t0;
+        g->pend.plain = false;
+        fill_run_stats(stats, g, sv, wv, rt);
     }
-    fill_stats(stats, sv, g_launches.load() - l0, kms, pms, ms_since(t0));
-    if (stats) {
-        stats->seed_ms = rt.seed_ms;
-        stats->wave_ms = rt.wave_ms;
-        stats->wave_bytes = wave_alg_bytes(wv, wv[ST_COMPLETED] + wv[ST_CUT]);
-        stats->grid_waves = rt.grid[ST_WAVES];
-        stats->grid_levels = rt.grid[ST_LEVELS];
-        stats->grid_bytes = wave_alg_bytes(rt.grid, rt.grid[ST_COMPLETED] + rt.grid[ST_CUT]);
+    return BCM_OK;
+}
+
+bcm_status bcm_trace(bcm_graph_t g, uint64_t* records, uint32_t cap, uint32_t* count) {
+    t_err.clear();
+    if (!g) return fail(BCM_ERR_INVALID, "graph is NULL");
+    if (g->pend.active) return fail(BCM_ERR_INVALID, "a run on this graph has not been finished");
+    if (!count || (cap && !records)) return fail(BCM_ERR_INVALID, "output pointer is NULL");
+    *count = g->trace_n;
+    uint32_t have = g->trace_n < kTraceCap ? g->trace_n : kTraceCap;
+    uint32_t nrec = have < cap ? have : cap;
+    if (nrec && g->d_trace) {
+        CU(cudaMemcpyAsync(records, g->d_trace, (size_t)nrec * 4 * sizeof(u64), cudaMemcpyDeviceToHost, g->stream),
+           "trace copy");
+        CU(cudaStreamSynchronize(g->stream), "trace copy");
     }
+    return BCM_OK;
+}
+
+bcm_status bcm_graph_trim(bcm_graph_t g) {
+    t_err.clear();
+    if (!g) return fail(BCM_ERR_INVALID, "graph is NULL");
+    if (g->pend.active) return fail(BCM_ERR_INVALID, "a run on this graph has not been finished");
+    CU(g->stream ? cudaStreamSynchronize(g->stream) : cudaDeviceSynchronize(), "synchronize");
+    region_release(g->slots, true);
+    cudaFree(g->d_plain);
+    cudaFree(g->d_far);
+    cudaFree(g->d_reach);
+    cudaFree(g->d_trace);
+    cudaFree(g->d_defer);
+    g->d_defer = nullptr;
+    g->d_plain = nullptr;
+    g->d_far = nullptr;
+    g->d_reach = nullptr;
+    g->d_trace = nullptr;
+    g->trace_n = 0;
     return BCM_OK;
 }
 

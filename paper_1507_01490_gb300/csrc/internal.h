@@ -22,6 +22,7 @@ enum Stat {
     ST_ARCWORDS,        // (arc, frontier word) pairs scanned
     ST_DISCWORDS,       // frontier words created (first discovery in a level)
     ST_CLEARED,         // vertex words cleared at wave ends
+    ST_DEFERRED,        // sources a per-CTA wave handed to the grid-wide pass
     ST_COUNT
 };
 
@@ -52,8 +53,9 @@ struct WaveParams {
     GraphDev g;
     uint32_t footnote;       // undirected: gamma~ uses deg(u)-1 for d >= 1
     uint32_t exhaustive;     // 1: no cut, write farness/reach of every source
-    uint32_t* head;          // next position in `order` (atomic)
-    uint32_t n_end;          // sources are order[*head .. n_end)
+    const uint32_t* sources; // the source queue: the degree order, or the deferred sources
+    uint32_t* head;          // next position in `sources` (atomic)
+    uint32_t n_end;          // sources are sources[*head .. n_end)
     TopK topk;
     unsigned long long* out_far;   // exhaustive outputs, indexed by vertex id
     uint32_t* out_reach;
@@ -73,7 +75,21 @@ struct WaveParams {
     uint32_t max_grid_waves;  // grid kernel: at most this many waves
     uint64_t heavy_words;   // grid kernel: a wave with fewer frontier words in total is light
     uint32_t pull_div;      // grid kernel: pull a level whose frontier holds >= n*W/pull_div words (0: never)
+    // per-CTA kernel: a wave whose next frontier reaches defer_words words is
+    // given up and its live sources appended to defer_src (0: never)
+    uint32_t defer_words;
+    uint32_t* defer_n;
+    uint32_t* defer_src;
+    // grid kernel: when set, the sources end at *n_end_dev (read at launch)
+    const uint32_t* n_end_dev;
+    // optional trace: records of 4 u64 (layout in include/bcm.h, bcm_trace), NULL when off
+    unsigned long long* trace;
+    uint32_t trace_cap;      // records
+    uint32_t* trace_n;       // records written (may exceed trace_cap; the excess is dropped)
 };
+
+// Trace record kinds (bits 60..63 of a record's second word).
+enum TraceKind { TR_GRID_LEVEL = 0, TR_GRID_WAVE = 1, TR_CTA_WAVE = 2 };
 
 // ---- preproc.cu
 int launch_validate(const uint64_t* rp64, const uint32_t* col, uint32_t n, uint64_t m, int* err,

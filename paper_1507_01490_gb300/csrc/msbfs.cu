@@ -94,14 +94,29 @@ __device__ inline void flush_stats(const LocalStats& s, const BlockStats& b, uns
         if ((threadIdx.x & 31) == 0 && x) atomicAdd(&g[idx[i]], x);
     }
     if (threadIdx.x == 0) {
-        const int rare[6] = {ST_COMPLETED, ST_CUT, ST_WAVES, ST_LEVELS, ST_CLEARED, ST_MAXLEVEL};
-        for (int i = 0; i < 6; ++i) {
+        const int rare[7] = {ST_COMPLETED, ST_CUT, ST_WAVES, ST_LEVELS, ST_CLEARED, ST_MAXLEVEL, ST_DEFERRED};
+        for (int i = 0; i < 7; ++i) {
             u64 x = b.v[rare[i]];
             if (!x) continue;
             if (rare[i] == ST_MAXLEVEL) atomicMax(&g[rare[i]], x);
             else atomicAdd(&g[rare[i]], x);
         }
     }
+}
+
+// One trace record (4 words), when tracing is on.  The second word holds
+// the kind in bits 60..63, an identifier (wave or CTA) in bits 32..59 and a
+// level in bits 0..31.
+__device__ __forceinline__ void trace_record(const WaveParams& p, u32 kind, u32 id, u32 level, u64 a, u64 b,
+                                             u64 t) {
+    if (!p.trace) return;
+    const u32 i = atomicAdd(p.trace_n, 1u);
+    if (i >= p.trace_cap) return;
+    unsigned long long* r = p.trace + 4 * (size_t)i;
+    r[0] = t;
+    r[1] = ((u64)kind << 60) | ((u64)(id & 0xfffffffu) << 32) | level;
+    r[2] = a;
+    r[3] = b;
 }
 
 // ------------------------------------------------------- staged appends
@@ -217,42 +232,95 @@ __device__ __forceinline__ void push_finish(const Push& q, u32* cg, u32* cs, War
     lq.push(q.fl & 2u, q.word);
 }
 
-// Level 0: lane j's frontier is its source.  One warp per source, arcs in
-// warp-wide strips.  The source's own bit is set first, by the same warp.
+// Prefix sums of the live sources' degrees (s_pre[0..L]) and their first
+// arcs (s_beg), for expand_sources.  Called by the whole block.
+template <int THREADS>
+__device__ inline void source_prefix(const GraphDev& G, const u32* s_src, const u32* s_alive32, int L, u32* s_pre,
+                                     u32* s_beg, u32* s_wsum) {
+    const u32 tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    u32 incl = 0;
+    if (tid < (u32)L) {
+        // only live lanes hold a source (others may hold a stale or unset id)
+        const bool a = (s_alive32[tid >> 5] >> lane) & 1u;
+        u32 b = 0;
+        if (a) {
+            const u32 v = s_src[tid];
+            b = __ldg(&G.rp[v]);
+            incl = __ldg(&G.rp[v + 1]) - b;
+        }
+        s_beg[tid] = b;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const u32 t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (u32)o) incl += t;
+        }
+        if (lane == 31) s_wsum[wid] = incl;
+    }
+    __syncthreads();
+    if (tid < (u32)L) {
+        u32 off = 0;
+        for (u32 w = 0; w < wid; ++w) off += s_wsum[w];
+        s_pre[tid + 1] = off + incl;
+        if (tid == 0) s_pre[0] = 0;
+    }
+    __syncthreads();
+}
+
+// Level 0: lane j's frontier is its source.  The live sources' arc ranges
+// are laid end to end (s_pre holds the prefix sums of their degrees) and
+// walked 32 arcs at a time by every warp of the caller (the block, or the
+// whole grid), so a wave of hubs spreads over all
+// warps instead of one warp per source.  Each source's own bit is set by one
+// thread; an arc back to the lane's own source (a self-loop) is skipped, so
+// no arc can find the source before its bit is set.
 template <int W>
-__device__ inline void expand_sources(const GraphDev& G, const u32* s_src, const u32* s_alive32, int L,
-                                      u64* vis, u64* Fnext, u32* cg, u32* cs, u32 foot,
-                                      WarpQueue& nq, WarpQueue& lq, u32 wid, u32 nw, LocalStats& st) {
+__device__ inline void expand_sources(const GraphDev& G, const u32* s_src, const u32* s_alive32, const u32* s_pre,
+                                      const u32* s_beg, int L, u64* vis, u64* Fnext, u32* cg, u32* cs, u32 foot,
+                                      WarpQueue& nq, WarpQueue& lq, u32 wid, u32 nw, u32 tid, u32 nthreads,
+                                      LocalStats& st) {
     const u32 lane = threadIdx.x & 31;
-    for (u32 j = wid; j < (u32)L; j += nw) {
-        if (!((s_alive32[j >> 5] >> (j & 31)) & 1u)) continue;
-        u32 u = s_src[j], g = j >> 6;
-        u64 F = 1ull << (j & 63);
-        u32 beg = __ldg(&G.rp[u]), end = __ldg(&G.rp[u + 1]);
+    lq.reserve(32);
+    for (u32 j0 = tid - lane; j0 < (u32)L; j0 += nthreads) {
+        const u32 j = j0 + lane;
         bool first = false;
-        if (lane == 0) {
-            first = atomicOr(&vis[ri(u * W + g)], F) == 0;
-            st.mvis += end - beg;
-            st.arcwords += end - beg;
+        u32 word = 0;
+        if (j < (u32)L && ((s_alive32[j >> 5] >> (j & 31)) & 1u)) {
+            const u32 deg = s_pre[j + 1] - s_pre[j];
+            word = s_src[j] * W + (j >> 6);
+            first = atomicOr(&vis[ri(word)], 1ull << (j & 63)) == 0;
+            st.mvis += deg;
+            st.arcwords += deg;
         }
         lq.reserve(32);
-        lq.push(first, u * W + g);
-        __syncwarp();
-        for (u32 e0 = beg; e0 < end; e0 += 32) {
-            nq.reserve(32);
-            lq.reserve(32);
-            u32 e = e0 + lane;
-            Push q;
-            q.nb = 0; q.fl = 0; q.degp = 0; q.g = g; q.word = 0;
-            if (e < end) {
-                push_load<W>(G.col, e, F, g, q);
-                push_check<W>(G.rp, vis, q);
-                u64 old;
-                push_vis(vis, q, old);
-                push_next(Fnext, q, old, foot, st);
+        lq.push(first, word);
+    }
+    const u32 total = s_pre[L];
+    for (u32 t0 = wid * 32; t0 < total; t0 += nw * 32) {
+        const u32 idx = t0 + lane;
+        bool v = idx < total;
+        Push q;
+        q.nb = 0; q.fl = 0; q.degp = 0; q.g = 0; q.word = 0;
+        if (v) {
+            // the lane owning arc idx: the last j with s_pre[j] <= idx
+            u32 lo = 0, hi = (u32)L;
+            while (hi - lo > 1) {
+                const u32 mid = (lo + hi) >> 1;
+                if (s_pre[mid] <= idx) lo = mid; else hi = mid;
             }
-            push_finish(q, cg, cs, nq, lq);
+            push_load<W>(G.col, s_beg[lo] + idx - s_pre[lo], 1ull << (lo & 63), lo >> 6, q);
+            if (q.x == s_src[lo]) v = false;   // self-loop
         }
+        nq.reserve(32);
+        lq.reserve(32);
+        if (v) {
+            push_check<W>(G.rp, vis, q);
+            u64 old;
+            push_vis(vis, q, old);
+            push_next(Fnext, q, old, foot, st);
+        } else {
+            q.nb = 0;
+        }
+        push_finish(q, cg, cs, nq, lq);
     }
 }
 
@@ -345,26 +413,37 @@ __device__ inline void expand_entries(const GraphDev& G, const u32* list, u32 cn
 // Level >= 1 by pull, for a frontier that covers much of the graph: each
 // vertex x whose vis words miss live lanes ("pending") ORs in the frontier
 // words of its in-neighbours, stopping once every pending lane is found.
-// A vertex is owned by one thread, so vis/F-next are written without
-// atomics.  The frontier words themselves are cleared afterwards
-// (pull_retire), once no thread can still be reading them.
+// Warps take 32 vertices at a time, in the degree order.
+// A vertex with at most kPullSerial in-arcs is scanned by its own thread;
+// a larger one by the whole warp, 32 in-arcs per step with an OR-reduction
+// and the same early stop, so a hub's in-list does not hold one thread for
+// thousands of dependent loads.  vis/F-next of x are written by x's own
+// thread, without atomics.  The frontier words themselves are cleared
+// afterwards (pull_retire), once no thread can still be reading them.
+constexpr u32 kPullSerial = 32;
+
 template <int W>
 __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32* s_alive32, u64* vis, u64* Fnext,
-                                  u32* cg, u32* cs, u32 foot, WarpQueue& nq, WarpQueue& lq, u32 gw, u32 gnw,
+                                  u32* cg, u32* cs, u32 foot, WarpQueue& nq, WarpQueue& lq, u32* chunk_ctr,
                                   LocalStats& st) {
     const u32 lane = threadIdx.x & 31;
     u64 alive[W];
 #pragma unroll
     for (int g = 0; g < W; ++g) alive[g] = ((u64)s_alive32[2 * g + 1] << 32) | s_alive32[2 * g];
-    for (u32 x0 = gw * 32; x0 < G.n; x0 += gnw * 32) {
-        const u32 x = x0 + lane;
-        u64 nb[W], v0[W];
+    // vertices in degree order, 32 at a time from a shared counter: the
+    // large in-lists start first and the rest fill in around them
+    for (;;) {
+        u32 x0 = 0;
+        if (lane == 0) x0 = atomicAdd(chunk_ctr, 32u);
+        x0 = __shfl_sync(0xffffffffu, x0, 0);
+        if (x0 >= G.n) break;
+        const u32 x = x0 + lane < G.n ? __ldg(&G.order[x0 + lane]) : G.n;
+        u64 pend[W], acc[W], v0[W];
+        bool any = false;
+        u32 b = 0, e = 0;
 #pragma unroll
-        for (int g = 0; g < W; ++g) { nb[g] = 0; v0[g] = 0; }
-        u32 degp = 0;
+        for (int g = 0; g < W; ++g) { pend[g] = 0; acc[g] = 0; v0[g] = 0; }
         if (x < G.n) {
-            u64 pend[W];
-            bool any = false;
 #pragma unroll
             for (int g = 0; g < W; ++g) {
                 v0[g] = __ldcg(&vis[ri(x * W + g)]);
@@ -372,32 +451,81 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
                 any = any || pend[g] != 0;
             }
             if (any) {
-                const u32 b = __ldg(&G.rrp[x]), e = __ldg(&G.rrp[x + 1]);
-                u64 acc[W];
-#pragma unroll
-                for (int g = 0; g < W; ++g) acc[g] = 0;
-                u32 i = b;
-                for (; i < e; ++i) {
-                    const u32 u = __ldg(&G.rcol[i]);
-                    bool done = true;
-#pragma unroll
-                    for (int g = 0; g < W; ++g) {
-                        if (pend[g] & ~acc[g]) acc[g] |= __ldcg(&Fcur[ri(u * W + g)]);
-                        done = done && !(pend[g] & ~acc[g]);
-                    }
-                    if (done) { ++i; break; }
-                }
-                st.arcwords += i - b;
-                degp = __ldg(&G.rp[x + 1]) - __ldg(&G.rp[x]) - foot;
+                b = __ldg(&G.rrp[x]);
+                e = __ldg(&G.rrp[x + 1]);
+            }
+        }
+        const bool coop = any && e - b > kPullSerial;
+        if (any && !coop) {
+            u32 i = b;
+            for (; i < e; ++i) {
+                const u32 u = __ldg(&G.rcol[i]);
+                bool done = true;
 #pragma unroll
                 for (int g = 0; g < W; ++g) {
-                    nb[g] = acc[g] & pend[g];
-                    if (nb[g]) {
-                        vis[ri(x * W + g)] = v0[g] | nb[g];
-                        Fnext[ri(x * W + g)] = nb[g];
-                        st.disc += __popcll(nb[g]);
-                        st.discwords++;
-                    }
+                    if (pend[g] & ~acc[g]) acc[g] |= __ldcg(&Fcur[ri(u * W + g)]);
+                    done = done && !(pend[g] & ~acc[g]);
+                }
+                if (done) { ++i; break; }
+            }
+            st.arcwords += i - b;
+        }
+        // the large in-lists, one at a time by the whole warp
+        u32 todo = __ballot_sync(0xffffffffu, coop);
+        while (todo) {
+            const int l0 = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const u32 cb = __shfl_sync(0xffffffffu, b, l0), ce = __shfl_sync(0xffffffffu, e, l0);
+            u64 cp[W], ca[W];
+#pragma unroll
+            for (int g = 0; g < W; ++g) {
+                const u32 lo = __shfl_sync(0xffffffffu, (u32)pend[g], l0);
+                const u32 hi = __shfl_sync(0xffffffffu, (u32)(pend[g] >> 32), l0);
+                cp[g] = ((u64)hi << 32) | lo;
+                ca[g] = 0;
+            }
+            u32 i = cb;
+            for (; i < ce; i += 32) {
+                u64 f[W];
+#pragma unroll
+                for (int g = 0; g < W; ++g) f[g] = 0;
+                if (i + lane < ce) {
+                    const u32 u = __ldg(&G.rcol[i + lane]);
+#pragma unroll
+                    for (int g = 0; g < W; ++g)
+                        if (cp[g] & ~ca[g]) f[g] = __ldcg(&Fcur[ri(u * W + g)]) & cp[g];
+                }
+                bool done = true;
+#pragma unroll
+                for (int g = 0; g < W; ++g) {
+                    const u32 lo = __reduce_or_sync(0xffffffffu, (u32)f[g]);
+                    const u32 hi = __reduce_or_sync(0xffffffffu, (u32)(f[g] >> 32));
+                    ca[g] |= ((u64)hi << 32) | lo;
+                    done = done && !(cp[g] & ~ca[g]);
+                }
+                if (done) { i = (i + 32 < ce) ? i + 32 : ce; break; }
+            }
+            if (i > ce) i = ce;
+            if (lane == (u32)l0) {
+                st.arcwords += i - cb;
+#pragma unroll
+                for (int g = 0; g < W; ++g) acc[g] = ca[g];
+            }
+        }
+        u64 nb[W];
+        u32 degp = 0;
+#pragma unroll
+        for (int g = 0; g < W; ++g) nb[g] = 0;
+        if (any) {
+            degp = __ldg(&G.rp[x + 1]) - __ldg(&G.rp[x]) - foot;
+#pragma unroll
+            for (int g = 0; g < W; ++g) {
+                nb[g] = acc[g] & pend[g];
+                if (nb[g]) {
+                    vis[ri(x * W + g)] = v0[g] | nb[g];
+                    Fnext[ri(x * W + g)] = nb[g];
+                    st.disc += __popcll(nb[g]);
+                    st.discwords++;
                 }
             }
         }
@@ -430,30 +558,105 @@ __device__ inline void pull_retire(const GraphDev& G, const u32* list, u32 cnt, 
 }
 
 // Completed lanes: exhaustive runs write (f, r) by vertex id; top-k runs
-// insert, under the lock, the entries that beat the cached k-th key.
-__device__ inline void flush_completions(const WaveParams& p, const u32* cid, const u64* cf, const u32* cr,
-                                         u32 nc, const ThrCache& thr, u32 nthreads) {
+// merge the ones that beat the cached k-th key into the shared top-k, under
+// the lock, with the whole block: the held entries (best first) are copied
+// to shared memory, the new ones ranked among themselves, every entry's
+// final place found by binary search in the other list, and the first k
+// written back in rank order.  Call with every thread of the block; nc is
+// the same in all of them.  scratch: 4608 u32 of shared memory not otherwise
+// in use during the call.
+__device__ __noinline__ void flush_completions(const WaveParams& p, const u32* cid, const u64* cf, const u32* cr,
+                                         u32 nc, const ThrCache& thr, u32 nthreads, u32* scratch, int* s_go) {
     if (nc == 0) return;
+    const u32 tid = threadIdx.x;
     if (p.exhaustive) {
-        for (u32 i = threadIdx.x; i < nc; i += nthreads) {
+        for (u32 i = tid; i < nc; i += nthreads) {
             p.out_far[cid[i]] = cf[i];
             p.out_reach[cid[i]] = cr[i];
         }
         return;
     }
-    if (threadIdx.x != 0) return;
-    bool any = false;
-    for (u32 i = 0; i < nc && !any; ++i) {
-        if (!thr.valid) { any = true; break; }
-        u64 N, F;
-        score_key(cf[i], cr[i], N, F);
-        any = ranks_before(N, F, cid[i], thr.N, thr.F, thr.id);
+    const TopK& T = p.topk;
+    if (tid == 0) {
+        bool any = !thr.valid;
+        for (u32 i = 0; i < nc && !any; ++i) {
+            u64 N, F;
+            score_key(cf[i], cr[i], N, F);
+            any = ranks_before(N, F, cid[i], thr.N, thr.F, thr.id);
+        }
+        *s_go = any && lock_acquire(T.lock, p.lock_limit_ns, p.err);
     }
-    if (!any) return;
-    if (!lock_acquire(p.topk.lock, p.lock_limit_ns, p.err)) return;
-    for (u32 i = 0; i < nc; ++i) topk_insert_locked(p.topk, cid[i], cf[i], cr[i]);
-    topk_publish_locked(p.topk);
-    lock_release(p.topk.lock);
+    __syncthreads();
+    if (!*s_go) return;
+    u32* hid = scratch;                      // held entries [cnt]
+    u64* hf = (u64*)(scratch + 1024);
+    u32* hr = scratch + 3072;
+    u32* nrank = scratch + 4096;             // rank of new entry j among the new ones
+    u32* order = scratch + 4352;             // new entries by that rank
+    const u32 cnt = vload(T.count);
+    for (u32 i = tid; i < cnt; i += nthreads) {
+        hid[i] = vload(&T.id[i]);
+        hf[i] = vload(&T.f[i]);
+        hr[i] = vload(&T.r[i]);
+    }
+    for (u32 j = tid; j < nc; j += nthreads) {
+        u64 N, F;
+        score_key(cf[j], cr[j], N, F);
+        u32 rk = 0;
+        for (u32 q = 0; q < nc; ++q) {
+            u64 Nq, Fq;
+            score_key(cf[q], cr[q], Nq, Fq);
+            rk += ranks_before(Nq, Fq, cid[q], N, F, cid[j]) ? 1u : 0u;
+        }
+        nrank[j] = rk;
+        order[rk] = j;
+    }
+    __syncthreads();
+    // new entry j lands at nrank[j] + (held entries before it)
+    for (u32 j = tid; j < nc; j += nthreads) {
+        u64 N, F;
+        score_key(cf[j], cr[j], N, F);
+        u32 lo = 0, hi = cnt;               // first held entry that j ranks before
+        while (lo < hi) {
+            const u32 mid = (lo + hi) >> 1;
+            u64 Nh, Fh;
+            score_key(hf[mid], hr[mid], Nh, Fh);
+            if (ranks_before(N, F, cid[j], Nh, Fh, hid[mid])) hi = mid; else lo = mid + 1;
+        }
+        const u32 pos = nrank[j] + lo;
+        if (pos < T.k) {
+            vstore(&T.id[pos], cid[j]);
+            vstore(&T.f[pos], cf[j]);
+            vstore(&T.r[pos], cr[j]);
+        }
+    }
+    // held entry i lands at i + (new entries before it)
+    for (u32 i = tid; i < cnt; i += nthreads) {
+        u64 Nh, Fh;
+        score_key(hf[i], hr[i], Nh, Fh);
+        u32 lo = 0, hi = nc;                // first new entry (in rank order) that i ranks before
+        while (lo < hi) {
+            const u32 mid = (lo + hi) >> 1;
+            const u32 q = order[mid];
+            u64 Nq, Fq;
+            score_key(cf[q], cr[q], Nq, Fq);
+            if (ranks_before(Nh, Fh, hid[i], Nq, Fq, cid[q])) hi = mid; else lo = mid + 1;
+        }
+        const u32 pos = i + lo;
+        if (pos < T.k) {
+            vstore(&T.id[pos], hid[i]);
+            vstore(&T.f[pos], hf[i]);
+            vstore(&T.r[pos], hr[i]);
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        vstore(T.count, cnt + nc < T.k ? cnt + nc : T.k);
+        topk_publish_locked(T);
+        lock_release(T.lock);
+    }
+    __syncthreads();
 }
 
 // --------------------------------------------------------- per-CTA waves
@@ -467,12 +670,16 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
     __shared__ u32 s_cg[L], s_cs[L];
     __shared__ u32 s_alive32[2 * W];
     __shared__ u32 s_ln[2], s_logn, s_base, s_nc, s_stop, s_chunk;
+    __shared__ u64 s_twave;
     __shared__ ThrCache s_thr;
     __shared__ BlockStats s_bst;
     constexpr u32 QCAP = 4096 / NWARP;
-    __shared__ u32 s_stage[NWARP * 2 * QCAP];
+    __shared__ __align__(16) u32 s_stage[NWARP * 2 * QCAP];
+    static_assert(NWARP * 2 * QCAP >= 4608, "flush_completions scratch");
     __shared__ u32 s_cid[L], s_cr[L];
     __shared__ u64 s_cf[L];
+    __shared__ u32 s_pre[L + 1], s_beg[L], s_wsum[L / 32];
+    __shared__ int s_go;
 
     const u32 tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const GraphDev& G = p.g;
@@ -493,13 +700,14 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
         __syncthreads();
         if (s_stop) break;
         const u32 base = s_base;
+        if (p.trace && tid == 0) s_twave = global_ns();   // kept in shared memory, not a register
         if (tid == 0) bstat_add(s_bst, ST_WAVES, 1);
         if (tid < L) {
             bool alive = false;
             s_cg[tid] = 0;
             s_cs[tid] = 0;
             if (base + tid < p.n_end) {
-                u32 v = __ldg(&G.order[base + tid]);
+                u32 v = __ldg(&p.sources[base + tid]);
                 u32 deg = __ldg(&G.rp[v + 1]) - __ldg(&G.rp[v]);
                 s_src[tid] = v; s_nd[tid] = 1; s_f[tid] = 0; s_gt[tid] = deg;
                 s_xlo[tid] = __ldg(&G.xlo[v]); s_xhi[tid] = __ldg(&G.xhi[v]);
@@ -515,7 +723,7 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
             if (lane == 0) s_alive32[tid >> 5] = m;
         }
         __syncthreads();
-        flush_completions(p, s_cid, s_cf, s_cr, s_nc, s_thr, THREADS);
+        flush_completions(p, s_cid, s_cf, s_cr, s_nc, s_thr, THREADS, s_stage, &s_go);
         __syncthreads();
         if (tid == 0) s_nc = 0;
 
@@ -542,13 +750,32 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
             for (int i = 0; i < 2 * W; ++i) any |= s_alive32[i];
             if (!any) break;
 
+            if (d > 0 && p.defer_words && s_ln[cur] >= p.defer_words) {
+                // a level too wide for one CTA is next: the live sources go
+                // to the grid-wide pass, which runs them again from the
+                // start; the wave ends here and its clear log resets every
+                // word it touched
+                if (tid < L) {
+                    const bool a = (s_alive32[tid >> 5] >> lane) & 1u;
+                    const u32 m = __ballot_sync(0xffffffffu, a);
+                    u32 at = 0;
+                    if (lane == 0 && m) {
+                        at = atomicAdd(p.defer_n, (u32)__popc(m));
+                        bstat_add(s_bst, ST_DEFERRED, __popc(m));
+                    }
+                    at = __shfl_sync(0xffffffffu, at, 0);
+                    if (a) p.defer_src[at + __popc(m & lanemask_lt())] = s_src[tid];
+                }
+                break;
+            }
+            if (d == 0) source_prefix<THREADS>(G, s_src, s_alive32, L, s_pre, s_beg, s_wsum);
             u64* Fnext = S.F[cur ^ 1];
             {
                 WarpQueue nq{&s_stage[(2 * wid) * QCAP], S.list[cur ^ 1], &s_ln[cur ^ 1], QCAP, 0};
                 WarpQueue lq{&s_stage[(2 * wid + 1) * QCAP], S.clog, &s_logn, QCAP, 0};
                 if (d == 0)
-                    expand_sources<W>(G, s_src, s_alive32, L, S.vis, Fnext, s_cg, s_cs, p.footnote, nq, lq, wid,
-                                      NWARP, st);
+                    expand_sources<W>(G, s_src, s_alive32, s_pre, s_beg, L, S.vis, Fnext, s_cg, s_cs, p.footnote,
+                                      nq, lq, wid, NWARP, tid, THREADS, st);
                 else
                     expand_entries<W>(G, S.list[cur], s_ln[cur], S.F[cur], s_alive32, S.vis, Fnext, s_cg, s_cs,
                                       p.footnote, nq, lq, &s_chunk, NWARP, st);
@@ -578,7 +805,7 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
             }
             if (tid == 0) s_ln[cur] = 0;
             __syncthreads();
-            flush_completions(p, s_cid, s_cf, s_cr, s_nc, s_thr, THREADS);
+            flush_completions(p, s_cid, s_cf, s_cr, s_nc, s_thr, THREADS, s_stage, &s_go);
             __syncthreads();
             if (tid == 0) s_nc = 0;
             cur ^= 1;
@@ -594,7 +821,10 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
             u32 w = S.clog[i];
             clear_record(S.vis, w);
         }
-        if (tid == 0) bstat_add(s_bst, ST_CLEARED, nlog);
+        if (tid == 0) {
+            bstat_add(s_bst, ST_CLEARED, nlog);
+            trace_record(p, TR_CTA_WAVE, blockIdx.x, d, nlog, s_twave, global_ns());
+        }
         __syncthreads();
         if (tid == 0) { s_logn = 0; s_ln[0] = 0; s_ln[1] = 0; }
     }
@@ -626,9 +856,12 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
     __shared__ ThrCache s_thr;
     __shared__ BlockStats s_bst;
     constexpr u32 QCAP = 4096 / NWARP;
-    __shared__ u32 s_stage[NWARP * 2 * QCAP];
+    __shared__ __align__(16) u32 s_stage[NWARP * 2 * QCAP];
+    static_assert(NWARP * 2 * QCAP >= 4608, "flush_completions scratch");
     __shared__ u32 s_cid[L], s_cr[L];
     __shared__ u64 s_cf[L];
+    __shared__ u32 s_pre[L + 1], s_beg[L], s_wsum[L / 32];
+    __shared__ int s_go;
 
     const u32 tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const bool leader = blockIdx.x == 0;
@@ -638,6 +871,7 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
     SlotPtrs S = slot_ptrs(p.seed_base, G.n, 4);
     LocalStats st;
     const u32 gw = blockIdx.x * NWARP + wid, gnw = gridDim.x * NWARP;
+    const u32 n_end = p.n_end_dev ? vload(p.n_end_dev) : p.n_end;
     if (tid == 0) { s_nc = 0; s_thr.valid = 0; s_thr.N = 0; s_thr.F = 1; s_thr.id = 0; }
     bstat_init(s_bst);
     bool ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err);
@@ -646,13 +880,13 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
         if (tid == 0) s_base = vload(p.head);
         __syncthreads();
         const u32 base = s_base;
-        if (base >= p.n_end) break;
+        if (base >= n_end) break;
         if (tid < L) {
             bool alive = false;
             s_cg[tid] = 0;
             s_cs[tid] = 0;
-            if (base + tid < p.n_end) {
-                u32 v = __ldg(&G.order[base + tid]);
+            if (base + tid < n_end) {
+                u32 v = __ldg(&p.sources[base + tid]);
                 u32 deg = __ldg(&G.rp[v + 1]) - __ldg(&G.rp[v]);
                 s_src[tid] = v; s_nd[tid] = 1; s_f[tid] = 0; s_gt[tid] = deg;
                 s_xlo[tid] = __ldg(&G.xlo[v]); s_xhi[tid] = __ldg(&G.xhi[v]);
@@ -670,7 +904,7 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
             if (lane == 0) s_alive32[tid >> 5] = m;
         }
         __syncthreads();
-        if (leader) flush_completions(p, s_cid, s_cf, s_cr, s_nc, s_thr, THREADS);
+        if (leader) flush_completions(p, s_cid, s_cf, s_cr, s_nc, s_thr, THREADS, s_stage, &s_go);
         __syncthreads();
         if (tid == 0) s_nc = 0;
         if (!(ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err))) break;
@@ -697,6 +931,14 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
             for (int i = 0; i < 2 * W; ++i) any |= s_alive32[i];
             if (!any) break;
 
+            if (p.trace && leader && tid == 0) {
+                u32 alive = 0;
+                for (int i = 0; i < 2 * W; ++i) alive += __popc(s_alive32[i]);
+                const u32 cnt = d ? vload(&p.glist_n[cur]) : 0u;
+                const bool pull = d && p.pull_div && (u64)cnt * p.pull_div >= (u64)G.n * W;
+                trace_record(p, TR_GRID_LEVEL, wave, d, cnt, alive | ((u64)pull << 32), global_ns());
+            }
+            if (d == 0) source_prefix<THREADS>(G, s_src, s_alive32, L, s_pre, s_beg, s_wsum);
             const u32 par = d & 1;
             u32* gcg = p.gcnt + par * 512;
             u32* gcs = gcg + 256;
@@ -704,15 +946,16 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
                 WarpQueue nq{&s_stage[(2 * wid) * QCAP], S.list[cur ^ 1], &p.glist_n[cur ^ 1], QCAP, 0};
                 WarpQueue lq{&s_stage[(2 * wid + 1) * QCAP], S.clog, p.glog_n, QCAP, 0};
                 if (d == 0) {
-                    expand_sources<W>(G, s_src, s_alive32, L, S.vis, S.F[cur ^ 1], s_cg, s_cs, p.footnote, nq, lq,
-                                      gw, gnw, st);
+                    expand_sources<W>(G, s_src, s_alive32, s_pre, s_beg, L, S.vis, S.F[cur ^ 1], s_cg, s_cs,
+                                      p.footnote, nq, lq, gw, gnw, blockIdx.x * THREADS + tid, gridDim.x * THREADS,
+                                      st);
                 } else {
                     const u32 cnt = vload(&p.glist_n[cur]);
                     wave_entries += cnt;
                     pulled = p.pull_div && (u64)cnt * p.pull_div >= (u64)G.n * W;
                     if (pulled)
                         pull_level<W>(G, S.F[cur], s_alive32, S.vis, S.F[cur ^ 1], s_cg, s_cs, p.footnote, nq, lq,
-                                      gw, gnw, st);
+                                      &p.gchunk[cur], st);
                     else
                         expand_entries<W>(G, S.list[cur], cnt, S.F[cur], s_alive32, S.vis, S.F[cur ^ 1], s_cg,
                                           s_cs, p.footnote, nq, lq, &p.gchunk[cur], gnw, st);
@@ -762,7 +1005,7 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
                 }
             }
             __syncthreads();
-            if (leader) flush_completions(p, s_cid, s_cf, s_cr, s_nc, s_thr, THREADS);
+            if (leader) flush_completions(p, s_cid, s_cf, s_cr, s_nc, s_thr, THREADS, s_stage, &s_go);
             __syncthreads();
             if (tid == 0) s_nc = 0;
             if (!(ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err))) break;
@@ -785,6 +1028,7 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
         }
         if (leader && tid == 0) bstat_add(s_bst, ST_CLEARED, nlog);
         if (!(ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err))) break;
+        if (leader && tid == 0) trace_record(p, TR_GRID_WAVE, wave, d, nlog, wave_entries, global_ns());
         if (leader) {   // reset per-wave counters and advance the queue
             for (u32 i = tid; i < 1024; i += THREADS) p.gcnt[i] = 0;
             if (tid == 0) {

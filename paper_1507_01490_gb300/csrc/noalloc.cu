@@ -132,6 +132,7 @@ extern "C" bcm_status bcm_farness_all_noalloc(const uint64_t* row_ptr, const uin
     w.g.rp = rp32;
     w.g.col = col;
     w.g.order = order;
+    w.sources = order;
     w.g.xlo = order;          // bounds are not read when nothing is cut
     w.g.xhi = order;
     w.g.rrp = rp32;

@@ -11,8 +11,9 @@
  * arithmetic or IEEE-754 +,-,*,/ with contraction disabled, so the same seed
  * gives the same graph on x86-64 and AArch64.
  *
- * Outputs are edge lists (src, dst) in caller-provided buffers; the Python
- * side turns them into CSR (duplicate and self-loop removal happen there).
+ * Outputs are edge lists (src, dst) in caller-provided buffers; gen_csr at
+ * the end turns an edge list into CSR (mirroring, self-loop and duplicate
+ * removal, sorted rows).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -292,4 +293,63 @@ void gen_uniform_u32(uint64_t seed, uint64_t count, uint32_t bound, uint32_t *ou
 void gen_exponential(uint64_t seed, uint64_t count, double mean, double *out) {
     rng_t r; rng_seed(&r, seed);
     for (uint64_t i = 0; i < count; ++i) out[i] = -gen_log(rng_open01(&r)) * mean;
+}
+
+/* ------------------------------------------------------------ CSR build */
+static int cmp_u32(const void *a, const void *b) {
+    uint32_t x = *(const uint32_t *)a, y = *(const uint32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* CSR from k arcs (src[i], dst[i]): undirected lists are mirrored first,
+ * self-loops dropped if drop_loops, rows sorted ascending, repeats removed if
+ * dedup.  row_ptr has n+1 entries; col must hold k arcs (2k if undirected).
+ * Returns the arc count written, or -1 if a working array cannot be
+ * allocated or an endpoint is >= n. */
+int64_t gen_csr(uint32_t n, const uint32_t *src, const uint32_t *dst, uint64_t k, int undirected,
+                int drop_loops, int dedup, uint64_t *row_ptr, uint32_t *col) {
+    memset(row_ptr, 0, ((size_t)n + 1) * sizeof(uint64_t));
+    for (uint64_t i = 0; i < k; ++i) {
+        uint32_t s = src[i], d = dst[i];
+        if (s >= n || d >= n) return -1;
+        if (drop_loops && s == d) continue;
+        row_ptr[s + 1]++;
+        if (undirected) row_ptr[d + 1]++;
+    }
+    for (uint32_t v = 0; v < n; ++v) row_ptr[v + 1] += row_ptr[v];
+    uint64_t *pos = (uint64_t *)malloc(((size_t)n + 1) * sizeof(uint64_t));
+    if (!pos) return -1;
+    memcpy(pos, row_ptr, ((size_t)n + 1) * sizeof(uint64_t));
+    for (uint64_t i = 0; i < k; ++i) {
+        uint32_t s = src[i], d = dst[i];
+        if (drop_loops && s == d) continue;
+        col[pos[s]++] = d;
+        if (undirected) col[pos[d]++] = s;
+    }
+    free(pos);
+    /* sort each row, drop repeats, compact in place (the write cursor never
+     * passes the row being read) */
+    uint64_t w = 0;
+    for (uint32_t v = 0; v < n; ++v) {
+        uint64_t b = row_ptr[v], e = row_ptr[v + 1];
+        uint64_t len = e - b;
+        uint32_t *r = col + b;
+        if (len > 32) {
+            qsort(r, len, sizeof(uint32_t), cmp_u32);
+        } else {
+            for (uint64_t i = 1; i < len; ++i) {
+                uint32_t x = r[i];
+                uint64_t j = i;
+                while (j > 0 && r[j - 1] > x) { r[j] = r[j - 1]; --j; }
+                r[j] = x;
+            }
+        }
+        row_ptr[v] = w;
+        for (uint64_t i = 0; i < len; ++i) {
+            if (dedup && i > 0 && r[i] == r[i - 1]) continue;
+            col[w++] = r[i];
+        }
+    }
+    row_ptr[n] = w;
+    return (int64_t)w;
 }

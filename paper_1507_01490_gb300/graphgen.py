@@ -47,6 +47,9 @@ def _lib():
                                 ctypes.c_uint64, _u32p, _u32p]
         lib.gen_uniform_u32.restype = None
         lib.gen_uniform_u32.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _u32p]
+        lib.gen_csr.restype = ctypes.c_int64
+        lib.gen_csr.argtypes = [ctypes.c_uint32, _u32p, _u32p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), _u32p]
         lib.gen_exponential.restype = None
         lib.gen_exponential.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double,
                                         ctypes.POINTER(ctypes.c_double)]
@@ -93,21 +96,16 @@ def csr_from_arcs(n: int, src, dst, directed: bool, name: str = "", dedup: bool 
                   drop_self_loops: bool = True) -> Graph:
     """CSR from an arc list.  Undirected: each pair is stored in both directions.
     Rows come out sorted; duplicates and self-loops are dropped unless asked not to."""
-    src = np.asarray(src, dtype=np.uint64)
-    dst = np.asarray(dst, dtype=np.uint64)
-    if not directed:
-        src, dst = np.concatenate([src, dst]), np.concatenate([dst, src])
-    if drop_self_loops:
-        keep = src != dst
-        src, dst = src[keep], dst[keep]
-    key = (src << np.uint64(32)) | dst
-    key = np.unique(key) if dedup else np.sort(key, kind="stable")
-    s = (key >> np.uint64(32)).astype(np.int64)
-    col = (key & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    src = np.ascontiguousarray(src, dtype=np.uint32)
+    dst = np.ascontiguousarray(dst, dtype=np.uint32)
+    k = int(src.shape[0])
     row_ptr = np.zeros(n + 1, dtype=np.uint64)
-    if n:
-        np.cumsum(np.bincount(s, minlength=n), out=row_ptr[1:])
-    return Graph(n=n, row_ptr=row_ptr, col=col, directed=directed, name=name)
+    col = np.empty(max(k * (1 if directed else 2), 1), dtype=np.uint32)
+    m = _lib().gen_csr(n, _p32(src), _p32(dst), k, int(not directed), int(drop_self_loops), int(dedup),
+                       row_ptr.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), _p32(col))
+    if m < 0:
+        raise ValueError("gen_csr failed: an endpoint is >= n or memory ran out")
+    return Graph(n=n, row_ptr=row_ptr, col=col[:m].copy(), directed=directed, name=name)
 
 
 # --------------------------------------------------------------- large recipes

@@ -114,6 +114,26 @@ def test_topk_kernel_choices_and_footnote(B, gen, orc):
                         assert np.array_equal(ids, exp) and np.array_equal(gf, f[exp]), (g.name, k, gl, pd)
 
 
+def test_deferred_waves_rerun_exactly(B, gen, orc):
+    """Per-CTA waves that hand their sources to the second grid-wide pass
+    (forced with tiny defer_words) give the exact top-k: a deferred source is
+    run again from the start under the threshold of the moment."""
+    graphs = undirected_graphs(gen)[1::2] + [gen.gnp(300, 0.01, seed=7, directed=True), gen.rmat(10, 8, seed=9)]
+    for g in graphs:
+        f, r = orc.farness_all(g)
+        with B.BcmGraph.from_graph(g) as h:
+            for k in (1, 10, 50):
+                exp = orc.topk(f, r, k)
+                for hw, dw, lanes in ((1 << 30, 1, 64), (1 << 30, 3, 256), (1, 2, 64), (50, 1, 128)):
+                    ids, gf, gr, st = h.topk(k, heavy_words=hw, defer_words=dw, lanes=lanes)
+                    assert np.array_equal(ids, exp) and np.array_equal(gf, f[exp]) and np.array_equal(gr, r[exp]), \
+                        (g.name, k, hw, dw, lanes)
+                    if hw == 1 << 30 and dw == 1 and g.m > 0 and g.n > 1:
+                        assert st["deferred"] > 0, g.name
+                ids, gf, gr, st = h.topk(k, heavy_words=1 << 30, defer_words=1, flags=B.BCM_NO_DEFER)
+                assert np.array_equal(ids, exp) and st["deferred"] == 0
+
+
 def test_plain_equals_oracle_bcm(B, gen, orc):
     """One source per launch follows the oracle's Algorithm 1 step for step:
     same top-k and the same arcs scanned, completions and cuts."""
