@@ -276,6 +276,72 @@ def run_serve(args, rank, world):
     return 0
 
 
+# ------------------------------------------------------------------- sweeps
+def run_sweep(args, rank, world):
+    """ratio: the performance ratio m_vis / (m n) of Section 3.1 against n on
+    Barabasi-Albert graphs (the synthetic counterpart of the paper's growing
+    actor graphs, whose inverse ratio grew about linearly with n), batched
+    kernels and, where it finishes in seconds, the plain one-source kernel.
+    race: the positive race of Section 3.3 -- how many more arcs the batched
+    kernels scan than the sequential order (the plain kernel), by lane width."""
+    if rank != 0:
+        return 0
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1507_01490_gb300 import bcm as B, graphgen
+    rows = []
+    if args.sweep == "ratio":
+        for lg in range(args.sweep_lo, args.sweep_hi + 1):
+            n = 1 << lg
+            g = graphgen.ba(n, 4, seed=100 + lg)
+            mn = float(g.m) * g.n
+            with B.BcmGraph.from_graph(g) as h:
+                h.topk(10)
+                row = {"graph": "BA n=2^%d m=4 (seed %d)" % (lg, 100 + lg), "n": n, "m_arcs": g.m}
+                for k in (1, 10, 100):
+                    ids, far, reach, st = h.topk(k)
+                    row["k%d" % k] = {"m_vis": st["m_vis"], "ratio": st["m_vis"] / mn,
+                                      "inverse_ratio": mn / st["m_vis"], "kernel_ms": st["kernel_ms"]}
+                    if n <= args.plain_max_n and k <= 10:
+                        _, _, _, sp = h.topk(k, flags=B.BCM_PLAIN)
+                        row["k%d" % k]["plain_m_vis"] = sp["m_vis"]
+                        row["k%d" % k]["plain_ratio"] = sp["m_vis"] / mn
+                        row["k%d" % k]["plain_ms"] = sp["kernel_ms"]
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+        # least-squares slope of the inverse ratio against n (k = 10)
+        xs = np.array([r["n"] for r in rows], dtype=float)
+        ys = np.array([r["k10"]["inverse_ratio"] for r in rows])
+        slope, icpt = np.polyfit(xs, ys, 1)
+        fit = {"inverse_ratio_vs_n_k10": {"slope_per_vertex": slope, "intercept": icpt,
+                                          "r2": float(1 - np.sum((ys - (slope * xs + icpt)) ** 2) /
+                                                      np.sum((ys - ys.mean()) ** 2))}}
+        print(json.dumps({"sweep": "performance ratio vs n", "rows": rows, "fit": fit}), flush=True)
+    else:
+        for name in args.sweep_graphs.split(","):
+            g = graphgen.workload(name)
+            with B.BcmGraph.from_graph(g) as h:
+                h.topk(10)
+                row = {"graph": name, "n": g.n, "m_arcs": g.m}
+                for k in (1, 10):
+                    _, _, _, sp = h.topk(k, flags=B.BCM_PLAIN)
+                    base = sp["m_vis"]
+                    ent = {"plain_m_vis": base}
+                    for lanes in (64, 128, 256):
+                        for gl in (64, 128, 256):
+                            _, _, _, st = h.topk(k, lanes=lanes, grid_lanes=gl)
+                            ent["cta%d_grid%d" % (lanes, gl)] = {"m_vis": st["m_vis"],
+                                                                 "increase": st["m_vis"] / base - 1.0}
+                    row["k%d" % k] = ent
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+        print(json.dumps({"sweep": "positive race: m_vis of the batched kernels over the sequential order",
+                          "rows": rows}), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------------- ours
 def main():
     ap = argparse.ArgumentParser()
@@ -302,12 +368,19 @@ def main():
     ap.add_argument("--serve-inflight", type=int, default=16)
     ap.add_argument("--serve-budget-gb", type=float, default=160.0)
     ap.add_argument("--serve-check", type=int, default=300, help="results compared with the request alone")
+    ap.add_argument("--sweep", choices=["ratio", "race"], help="a sweep instead of the benchmark")
+    ap.add_argument("--sweep-lo", type=int, default=14, help="ratio sweep: smallest n = 2^lo")
+    ap.add_argument("--sweep-hi", type=int, default=21)
+    ap.add_argument("--plain-max-n", type=int, default=1 << 18)
+    ap.add_argument("--sweep-graphs", default="ba2000,chunglu256k,chunglu1m,rmat20")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if args.serve:
         return run_serve(args, rank, world)
+    if args.sweep:
+        return run_sweep(args, rank, world)
 
     import torch
     torch.cuda.set_device(local)

@@ -86,9 +86,10 @@ typedef enum {
  * is stopped and its sources run again on the grid kernel after the
  * per-CTA phase (see defer_words).  Exhaustive runs stay on the grid
  * kernel.  Levels of grid waves run by push (each frontier vertex
- * sets its lanes' bits in its out-neighbours) or, when the frontier is a
- * large share of the graph, by pull (each vertex with lanes still to reach
- * gathers them from its in-neighbours' frontier bits, with no atomics). */
+ * sets its lanes' bits in its out-neighbours) or, when the frontier's arcs
+ * are a large share of the graph's, by pull (each vertex with lanes still
+ * to reach gathers them from its in-neighbours' frontier bits, with no
+ * atomics). */
 typedef struct {
     uint32_t lanes;           /* sources per per-CTA wave: 64, 128 or 256; 0 = 64 */
     uint32_t grid_lanes;      /* sources per grid-wide wave: 64, 128 or 256; 0 = 128 */
@@ -97,9 +98,9 @@ typedef struct {
                                  one per wave of sources (ceil(n / lanes)) */
     uint32_t threads;         /* threads per CTA of the per-CTA kernel: 256, 512 or 1024; 0 = 512 */
     uint32_t heavy_words;     /* see above; 0 = default (4 per warp of the grid) */
-    uint32_t pull_div;        /* a grid-wave level whose frontier holds at least n*W/pull_div words
-                                 (W = grid_lanes/64) is expanded by pull; 0 = default
-                                 (64 for bcm_topk, 16 for bcm_farness_all) */
+    uint32_t pull_div;        /* a grid-wave level is expanded by pull when the out-arcs of its
+                                 frontier's (vertex, word) entries number at least n*W/pull_div
+                                 (W = grid_lanes/64); 0 = default (32) */
     uint32_t defer_words;     /* a per-CTA wave whose next frontier reaches this many words stops
                                  and hands its live sources to a second grid-wide pass, which
                                  runs them from the start; 0 = default (heavy_words) */
@@ -222,7 +223,8 @@ bcm_status bcm_topk_finish(bcm_graph_t g, int wait, bcm_stats* stats);
  *   [0] time stamp (ns, the GPU's global timer)
  *   [1] kind << 60 | id << 32 | level, kind one of
  *       0  grid-wide level start  (id = wave; [2] frontier entries,
- *                                  [3] live lanes | 1 << 32 if pulled)
+ *                                  [3] live lanes | 1 << 16 if pulled |
+ *                                  out-arcs of the frontier's words << 20)
  *       1  grid-wide wave end     (id = wave; [2] words cleared,
  *                                  [3] frontier entries over the wave)
  *       2  per-CTA wave end       (id = CTA;  [2] words cleared,

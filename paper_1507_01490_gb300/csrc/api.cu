@@ -152,6 +152,9 @@ struct Aux {
     uint32_t glist_n[2];
     uint32_t glog_n;
     uint32_t gchunk[2];
+    unsigned long long garc[2];
+    HeavyEntry gheavy[2048];
+    uint32_t gheavy_n;
     uint32_t trace_n;
     uint32_t defer_n;     // sources handed back by per-CTA waves
     uint32_t head2;       // queue head of the grid-wide pass over them
@@ -457,6 +460,10 @@ WaveParams base_params(bcm_graph* g, const Cfg& c) {
     p.glist_n = a->glist_n;
     p.glog_n = &a->glog_n;
     p.gchunk = a->gchunk;
+    p.garc = a->garc;
+    p.gheavy = a->gheavy;
+    p.gheavy_n = &a->gheavy_n;
+    p.gheavy_cap = 2048;
     return p;
 }
 
@@ -570,9 +577,9 @@ bcm_status start_run(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, vo
         if (grid) {
             p.max_grid_waves = 0xffffffffu;
             p.heavy_words = (exhaustive || (c.flags & BCM_GRID_ONLY)) ? 0 : c.heavy_words;
-            // defaults measured on the Chung-Lu workloads: top-k grid waves
-            // pull nearly every level, exhaustive ones only the dense ones
-            p.pull_div = (c.flags & BCM_NO_PULL) ? 0u : (c.pull_div ? c.pull_div : (exhaustive ? 16u : 64u));
+            // default measured per level on the Chung-Lu and R-MAT workloads:
+            // pull wins once the frontier's out-arcs reach about n*W/32
+            p.pull_div = (c.flags & BCM_NO_PULL) ? 0u : (c.pull_div ? c.pull_div : 32u);
             rc = launch_grid_waves(p, c.grid_W, c.grid_blocks, 512, s);
         }
         cudaEventRecord(g->ev[1], s);
@@ -589,7 +596,7 @@ bcm_status start_run(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, vo
             q.max_grid_waves = 0xffffffffu;
             q.heavy_words = 0;
             q.defer_words = 0;
-            q.pull_div = (c.flags & BCM_NO_PULL) ? 0u : (c.pull_div ? c.pull_div : 64u);
+            q.pull_div = (c.flags & BCM_NO_PULL) ? 0u : (c.pull_div ? c.pull_div : 32u);
             q.stats = g->d_aux->seed_stats;
             rc = launch_grid_waves(q, c.grid_W, c.grid_blocks, 512, s);
         }

@@ -49,6 +49,14 @@ inline size_t slot_bytes(uint32_t n, int W) {
     return (b + 255) & ~(size_t)255;
 }
 
+// A frontier word whose vertex has many out-arcs, queued so that every warp
+// can take a share of its arcs.
+struct HeavyEntry {
+    unsigned long long F;   // live frontier lanes of the word
+    uint32_t beg, deg;      // the vertex's arcs
+    uint32_t g, pad;        // word group
+};
+
 struct WaveParams {
     GraphDev g;
     uint32_t footnote;       // undirected: gamma~ uses deg(u)-1 for d >= 1
@@ -72,9 +80,13 @@ struct WaveParams {
     uint32_t* glist_n;       // [2] frontier list sizes
     uint32_t* glog_n;        // [1] cleared-word log size
     uint32_t* gchunk;        // [2] chunk counters of the frontier lists
+    unsigned long long* garc; // [2] out-arcs of the frontier lists' words
+    HeavyEntry* gheavy;      // heavy entries of the level being pushed
+    uint32_t* gheavy_n;
+    uint32_t gheavy_cap;
     uint32_t max_grid_waves;  // grid kernel: at most this many waves
     uint64_t heavy_words;   // grid kernel: a wave with fewer frontier words in total is light
-    uint32_t pull_div;      // grid kernel: pull a level whose frontier holds >= n*W/pull_div words (0: never)
+    uint32_t pull_div;      // grid kernel: pull a level whose frontier words have >= n*W/pull_div out-arcs (0: never)
     // per-CTA kernel: a wave whose next frontier reaches defer_words words is
     // given up and its live sources appended to defer_src (0: never)
     uint32_t defer_words;

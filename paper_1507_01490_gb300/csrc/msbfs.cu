@@ -69,8 +69,17 @@ __device__ __forceinline__ void clear_record(u64* vis, u32 word) {
 // levels, cleared words) go to a per-block shared array instead.
 struct LocalStats {
     u64 mvis = 0;
+    u64 fwarcs = 0;      // out-arcs of the words this thread put in the next frontier (this level)
     u32 disc = 0, entries = 0, arcwords = 0, discwords = 0;
 };
+
+// Adds the warp's next-frontier arc words to *dst and clears the counters.
+__device__ __forceinline__ void flush_fwarcs(LocalStats& st, unsigned long long* dst) {
+    u64 x = st.fwarcs;
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(dst, (unsigned long long)x);
+    st.fwarcs = 0;
+}
 
 // per-block counters of rare events, indexed by Stat
 struct BlockStats { unsigned long long v[ST_COUNT]; };
@@ -192,37 +201,37 @@ __device__ __forceinline__ void push_next(u64* Fnext, Push& q, u64 old, u32 foot
     q.nb &= ~old;
     if (!q.nb) return;
     u64 oldF = atomicOr(&Fnext[ri(q.word)], q.nb);
-    if (oldF == 0) { q.fl |= 1u; st.discwords++; }
+    if (oldF == 0) { q.fl |= 1u; st.discwords++; st.fwarcs += q.r1 - q.r0; }
     q.degp = q.r1 - q.r0 - foot;
     st.disc += __popcll(q.nb);
 }
 
-// Per-lane counts of this step's discoveries, summed across the warp with
-// ballots and reductions (one shared-memory update per lane bit present in
-// the warp, not one per discovery): cg[lane] += how many vertices the lane
-// discovered, cs[lane] += the sum of their degrees (minus the footnote).
+// Per-lane counts of this step's discoveries, summed across the warp:
+// cg[lane] += how many vertices the lane discovered, cs[lane] += the sum of
+// their degrees (minus the footnote).  Transposed: the warp walks the
+// threads holding discoveries (at most 32) and thread t keeps the counts of
+// bit lanes t and t+32 of the word group being walked, so the shared-memory
+// updates are one per thread and bit lane, with no two threads on one
+// counter.
 __device__ __forceinline__ void warp_count(u64 nb, u32 degp, u32 g, u32* cg, u32* cs) {
     const u32 lane = threadIdx.x & 31;
     u32 active = __ballot_sync(0xffffffffu, nb != 0);
     while (active) {
-        const int l0 = __ffs(active) - 1;
-        const u32 g0 = __shfl_sync(0xffffffffu, g, l0);
-        const bool mine = nb != 0 && g == g0;
-        active &= ~__ballot_sync(0xffffffffu, mine);
-        const u64 m = mine ? nb : 0ull;
-        u64 bits = ((u64)__reduce_or_sync(0xffffffffu, (u32)(m >> 32)) << 32) |
-                   (u64)__reduce_or_sync(0xffffffffu, (u32)m);
-        while (bits) {
-            const int j = __ffsll((long long)bits) - 1;
-            bits &= bits - 1;
-            const bool has = (m >> j) & 1ull;
-            const u32 c = __popc(__ballot_sync(0xffffffffu, has));
-            const u32 sd = __reduce_add_sync(0xffffffffu, has ? degp : 0u);
-            if (lane == 0) {
-                atomicAdd(&cg[g0 * 64 + j], c);
-                atomicAdd(&cs[g0 * 64 + j], sd);
-            }
+        const u32 g0 = __shfl_sync(0xffffffffu, g, __ffs(active) - 1);
+        u32 grp = __ballot_sync(0xffffffffu, nb != 0 && g == g0);
+        active &= ~grp;
+        u32 c_lo = 0, c_hi = 0, s_lo = 0, s_hi = 0;
+        while (grp) {
+            const int i = __ffs(grp) - 1;
+            grp &= grp - 1;
+            const u32 lo = __shfl_sync(0xffffffffu, (u32)nb, i);
+            const u32 hi = __shfl_sync(0xffffffffu, (u32)(nb >> 32), i);
+            const u32 dg = __shfl_sync(0xffffffffu, degp, i);
+            if ((lo >> lane) & 1u) { ++c_lo; s_lo += dg; }
+            if ((hi >> lane) & 1u) { ++c_hi; s_hi += dg; }
         }
+        if (c_lo) { atomicAdd(&cg[g0 * 64 + lane], c_lo); atomicAdd(&cs[g0 * 64 + lane], s_lo); }
+        if (c_hi) { atomicAdd(&cg[g0 * 64 + 32 + lane], c_hi); atomicAdd(&cs[g0 * 64 + 32 + lane], s_hi); }
     }
 }
 
@@ -324,6 +333,18 @@ __device__ inline void expand_sources(const GraphDev& G, const u32* s_src, const
     }
 }
 
+// Frontier entries with more than kHeavyArcs out-arcs are not expanded by
+// the warp that reads them: they go to a heavy list, and once every warp is
+// past the main pass, all warps share their arcs (expand_heavy).  A list
+// that is full leaves the entry with its warp.
+constexpr u32 kHeavyArcs = 1024;
+constexpr u32 kHeavyCapCta = 64;
+struct HeavyList {
+    HeavyEntry* e;
+    u32* n;       // entries claimed (may pass cap; only the first cap are stored)
+    u32 cap;
+};
+
 // Level >= 1: frontier words from `list`.  Warps take chunks of 32 entries
 // from a shared counter (so a chunk holding a high-degree vertex does not
 // hold back the others), form the exclusive scan of the chunk's degrees and
@@ -332,7 +353,7 @@ template <int W>
 __device__ inline void expand_entries(const GraphDev& G, const u32* list, u32 cnt, u64* Fcur,
                                       const u32* s_alive32, u64* vis, u64* Fnext, u32* cg, u32* cs,
                                       u32 foot, WarpQueue& nq, WarpQueue& lq, u32* chunk_ctr, u32 nw,
-                                      LocalStats& st) {
+                                      const HeavyList& H, LocalStats& st) {
     const u32 lane = threadIdx.x & 31;
     // entries taken per counter reservation: 32 when the frontier is small,
     // up to 256 when it is large enough to keep every warp busy anyway
@@ -364,6 +385,16 @@ __device__ inline void expand_entries(const GraphDev& G, const u32* list, u32 cn
                 deg = __ldg(&G.rp[u + 1]) - beg;
                 st.mvis += (u64)__popcll(F) * deg;
                 st.arcwords += deg;
+                if (deg > kHeavyArcs) {
+                    const u32 slot = atomicAdd(H.n, 1u);
+                    if (slot < H.cap) {
+                        H.e[slot].F = F;
+                        H.e[slot].beg = beg;
+                        H.e[slot].deg = deg;
+                        H.e[slot].g = g;
+                        deg = 0;          // expanded by expand_heavy
+                    }
+                }
             }
         }
         u32 incl = deg;
@@ -410,10 +441,78 @@ __device__ inline void expand_entries(const GraphDev& G, const u32* list, u32 cn
     }
 }
 
+// The heavy list's arcs, 64 at a time, piece c to warp c mod nw (warp wid
+// of nw); run by every warp after all of them have left expand_entries.
+template <int W>
+__device__ __noinline__ void expand_heavy(const GraphDev& G, const HeavyEntry* H, u32 hn, u64* vis, u64* Fnext,
+                                    u32* cg, u32* cs, u32 foot, WarpQueue& nq, WarpQueue& lq, u32 wid, u32 nw,
+                                    LocalStats& st) {
+    const u32 lane = threadIdx.x & 31;
+    u32 base = 0;   // pieces in the batches before this one
+    for (u32 h0 = 0; h0 < hn; h0 += 32) {
+        const u32 h = h0 + lane;
+        u32 pc = 0, beg = 0, deg = 0, g = 0;
+        u64 F = 0;
+        if (h < hn) {
+            F = H[h].F;
+            beg = H[h].beg;
+            deg = H[h].deg;
+            g = H[h].g;
+            pc = (deg + 63) / 64;
+        }
+        u32 incl = pc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const u32 t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (u32)o) incl += t;
+        }
+        const u32 total = __shfl_sync(0xffffffffu, incl, 31);
+        const u32 excl = incl - pc;
+        // this warp's pieces: base + idx with (base + idx) % nw == wid
+        for (u32 idx = (wid + nw - base % nw) % nw; idx < total; idx += nw) {
+            int owner = 0;
+#pragma unroll
+            for (int step = 16; step; step >>= 1) {
+                const u32 ex = __shfl_sync(0xffffffffu, excl, owner + step);
+                if (ex <= idx) owner += step;
+            }
+            const u32 o_beg = __shfl_sync(0xffffffffu, beg, owner);
+            const u32 o_deg = __shfl_sync(0xffffffffu, deg, owner);
+            const u32 o_excl = __shfl_sync(0xffffffffu, excl, owner);
+            const u32 o_g = __shfl_sync(0xffffffffu, g, owner);
+            const u64 o_F = ((u64)__shfl_sync(0xffffffffu, (u32)(F >> 32), owner) << 32) |
+                            __shfl_sync(0xffffffffu, (u32)F, owner);
+            const u32 off = (idx - o_excl) * 64;
+            Push q[2];
+            bool v[2];
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const u32 a = off + 32 * hh + lane;
+                v[hh] = a < o_deg;
+                q[hh].nb = 0; q[hh].fl = 0; q[hh].degp = 0; q[hh].g = o_g; q[hh].word = 0;
+                if (v[hh]) push_load<W>(G.col, o_beg + a, o_F, o_g, q[hh]);
+            }
+            nq.reserve(64);
+            lq.reserve(64);
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh)
+                if (v[hh]) push_check<W>(G.rp, vis, q[hh]);
+            u64 old[2];
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) push_vis(vis, q[hh], old[hh]);
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) push_next(Fnext, q[hh], old[hh], foot, st);
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) push_finish(q[hh], cg, cs, nq, lq);
+        }
+        base += total;
+    }
+}
+
 // Level >= 1 by pull, for a frontier that covers much of the graph: each
 // vertex x whose vis words miss live lanes ("pending") ORs in the frontier
 // words of its in-neighbours, stopping once every pending lane is found.
-// Warps take 32 vertices at a time, in the degree order.
+// Warps take 32 consecutive vertices at a time from a shared counter.
 // A vertex with at most kPullSerial in-arcs is scanned by its own thread;
 // a larger one by the whole warp, 32 in-arcs per step with an OR-reduction
 // and the same early stop, so a hub's in-list does not hold one thread for
@@ -430,14 +529,14 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
     u64 alive[W];
 #pragma unroll
     for (int g = 0; g < W; ++g) alive[g] = ((u64)s_alive32[2 * g + 1] << 32) | s_alive32[2 * g];
-    // vertices in degree order, 32 at a time from a shared counter: the
-    // large in-lists start first and the rest fill in around them
+    // 32 consecutive vertices at a time from a shared counter (a warp held
+    // up by a large in-list takes fewer chunks)
     for (;;) {
         u32 x0 = 0;
         if (lane == 0) x0 = atomicAdd(chunk_ctr, 32u);
         x0 = __shfl_sync(0xffffffffu, x0, 0);
         if (x0 >= G.n) break;
-        const u32 x = x0 + lane < G.n ? __ldg(&G.order[x0 + lane]) : G.n;
+        const u32 x = x0 + lane;
         u64 pend[W], acc[W], v0[W];
         bool any = false;
         u32 b = 0, e = 0;
@@ -526,6 +625,7 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
                     Fnext[ri(x * W + g)] = nb[g];
                     st.disc += __popcll(nb[g]);
                     st.discwords++;
+                    st.fwarcs += degp + foot;
                 }
             }
         }
@@ -671,6 +771,9 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
     __shared__ u32 s_alive32[2 * W];
     __shared__ u32 s_ln[2], s_logn, s_base, s_nc, s_stop, s_chunk;
     __shared__ u64 s_twave;
+    __shared__ unsigned long long s_arcs[2];   // out-arcs of each frontier list's words
+    __shared__ HeavyEntry s_heavy[kHeavyCapCta];
+    __shared__ u32 s_hn;
     __shared__ ThrCache s_thr;
     __shared__ BlockStats s_bst;
     constexpr u32 QCAP = 4096 / NWARP;
@@ -687,8 +790,9 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
     LocalStats st;
     if (tid == 0) {
         s_thr.valid = 0; s_thr.N = 0; s_thr.F = 1; s_thr.id = 0;
-        s_nc = 0; s_logn = 0; s_ln[0] = 0; s_ln[1] = 0;
+        s_nc = 0; s_logn = 0; s_ln[0] = 0; s_ln[1] = 0; s_arcs[0] = 0; s_arcs[1] = 0; s_hn = 0;
     }
+    const HeavyList Hc{s_heavy, &s_hn, kHeavyCapCta};
     bstat_init(s_bst);
     __syncthreads();
 
@@ -778,9 +882,17 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
                                       nq, lq, wid, NWARP, tid, THREADS, st);
                 else
                     expand_entries<W>(G, S.list[cur], s_ln[cur], S.F[cur], s_alive32, S.vis, Fnext, s_cg, s_cs,
-                                      p.footnote, nq, lq, &s_chunk, NWARP, st);
+                                      p.footnote, nq, lq, &s_chunk, NWARP, Hc, st);
+                if (d > 0) {
+                    __syncthreads();   // the heavy list is complete
+                    const u32 hn = s_hn < kHeavyCapCta ? s_hn : kHeavyCapCta;
+                    if (hn)
+                        expand_heavy<W>(G, s_heavy, hn, S.vis, Fnext, s_cg, s_cs, p.footnote, nq, lq, wid, NWARP,
+                                        st);
+                }
                 nq.flush();
                 lq.flush();
+                flush_fwarcs(st, &s_arcs[cur ^ 1]);
             }
             __syncthreads();
             if (tid < L) {   // level d+1 is known: gamma_{d+1} and its degree sum
@@ -803,7 +915,7 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
                 u32 m = __ballot_sync(0xffffffffu, a);
                 if (lane == 0) s_alive32[tid >> 5] = m;
             }
-            if (tid == 0) s_ln[cur] = 0;
+            if (tid == 0) { s_ln[cur] = 0; s_arcs[cur] = 0; s_hn = 0; }
             __syncthreads();
             flush_completions(p, s_cid, s_cf, s_cr, s_nc, s_thr, THREADS, s_stage, &s_go);
             __syncthreads();
@@ -826,7 +938,7 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
             trace_record(p, TR_CTA_WAVE, blockIdx.x, d, nlog, s_twave, global_ns());
         }
         __syncthreads();
-        if (tid == 0) { s_logn = 0; s_ln[0] = 0; s_ln[1] = 0; }
+        if (tid == 0) { s_logn = 0; s_ln[0] = 0; s_ln[1] = 0; s_arcs[0] = 0; s_arcs[1] = 0; }
     }
     __syncthreads();
     flush_stats(st, s_bst, p.stats);
@@ -843,8 +955,14 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
 // high-diameter graph) is better left to one CTA.  On the first narrow wave
 // the kernel returns and leaves *head where the per-CTA kernel continues;
 // exhaustive runs stay until the queue is empty.
+// CTAs per SM the grid kernel is compiled for (its register budget is
+// 65536 / (this * THREADS) per thread)
+#ifndef BCM_GRID_MIN_BLOCKS
+#define BCM_GRID_MIN_BLOCKS 2
+#endif
+
 template <int W, int THREADS>
-__global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREADS) : 1) k_wave_grid(WaveParams p) {
+__global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(WaveParams p) {
     constexpr int L = 64 * W;
     constexpr int NWARP = THREADS / 32;
     static_assert(THREADS >= L, "one thread per lane");
@@ -872,6 +990,7 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
     LocalStats st;
     const u32 gw = blockIdx.x * NWARP + wid, gnw = gridDim.x * NWARP;
     const u32 n_end = p.n_end_dev ? vload(p.n_end_dev) : p.n_end;
+    const HeavyList Hg{p.gheavy, p.gheavy_n, p.gheavy_cap};
     if (tid == 0) { s_nc = 0; s_thr.valid = 0; s_thr.N = 0; s_thr.F = 1; s_thr.id = 0; }
     bstat_init(s_bst);
     bool ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err);
@@ -935,8 +1054,9 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
                 u32 alive = 0;
                 for (int i = 0; i < 2 * W; ++i) alive += __popc(s_alive32[i]);
                 const u32 cnt = d ? vload(&p.glist_n[cur]) : 0u;
-                const bool pull = d && p.pull_div && (u64)cnt * p.pull_div >= (u64)G.n * W;
-                trace_record(p, TR_GRID_LEVEL, wave, d, cnt, alive | ((u64)pull << 32), global_ns());
+                const u64 arcs = d ? vload(&p.garc[cur]) : 0ull;
+                const bool pull = d && p.pull_div && arcs >= ((u64)G.n * W + p.pull_div - 1) / p.pull_div;
+                trace_record(p, TR_GRID_LEVEL, wave, d, cnt, alive | ((u64)pull << 16) | (arcs << 20), global_ns());
             }
             if (d == 0) source_prefix<THREADS>(G, s_src, s_alive32, L, s_pre, s_beg, s_wsum);
             const u32 par = d & 1;
@@ -952,16 +1072,20 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
                 } else {
                     const u32 cnt = vload(&p.glist_n[cur]);
                     wave_entries += cnt;
-                    pulled = p.pull_div && (u64)cnt * p.pull_div >= (u64)G.n * W;
+                    // by pull once the frontier's out-arcs reach n*W/pull_div:
+                    // push pays per arc (and a hub's arcs fall to one warp),
+                    // pull pays a fixed scan of every vertex's vis words
+                    pulled = p.pull_div && vload(&p.garc[cur]) >= ((u64)G.n * W + p.pull_div - 1) / p.pull_div;
                     if (pulled)
                         pull_level<W>(G, S.F[cur], s_alive32, S.vis, S.F[cur ^ 1], s_cg, s_cs, p.footnote, nq, lq,
                                       &p.gchunk[cur], st);
                     else
                         expand_entries<W>(G, S.list[cur], cnt, S.F[cur], s_alive32, S.vis, S.F[cur ^ 1], s_cg,
-                                          s_cs, p.footnote, nq, lq, &p.gchunk[cur], gnw, st);
+                                          s_cs, p.footnote, nq, lq, &p.gchunk[cur], gnw, Hg, st);
                 }
                 nq.flush();
                 lq.flush();
+                flush_fwarcs(st, &p.garc[cur ^ 1]);
             }
             __syncthreads();
             if (tid < L) {
@@ -970,6 +1094,30 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
                 s_cs[tid] = 0;
             }
             if (!(ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err))) break;
+            {
+                // the heavy entries of a push level, shared by every warp of
+                // the grid (one more barrier, only when there are any)
+                u32 hn = vload(p.gheavy_n);
+                hn = hn < p.gheavy_cap ? hn : p.gheavy_cap;
+                if (hn) {
+                    {
+                        WarpQueue nq{&s_stage[(2 * wid) * QCAP], S.list[cur ^ 1], &p.glist_n[cur ^ 1], QCAP, 0};
+                        WarpQueue lq{&s_stage[(2 * wid + 1) * QCAP], S.clog, p.glog_n, QCAP, 0};
+                        expand_heavy<W>(G, p.gheavy, hn, S.vis, S.F[cur ^ 1], s_cg, s_cs, p.footnote, nq, lq, gw,
+                                        gnw, st);
+                        nq.flush();
+                        lq.flush();
+                        flush_fwarcs(st, &p.garc[cur ^ 1]);
+                    }
+                    __syncthreads();
+                    if (tid < L) {
+                        if (s_cg[tid]) { atomicAdd(&gcg[tid], s_cg[tid]); atomicAdd(&gcs[tid], s_cs[tid]); }
+                        s_cg[tid] = 0;
+                        s_cs[tid] = 0;
+                    }
+                    if (!(ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err))) break;
+                }
+            }
             if (pulled) {   // every block is past the pull: retire the frontier words
                 pull_retire<W>(G, S.list[cur], vload(&p.glist_n[cur]), S.F[cur], s_alive32,
                                blockIdx.x * THREADS + tid, gridDim.x * THREADS, st);
@@ -1001,7 +1149,9 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
                 for (u32 i = tid; i < 512; i += THREADS) nx[i] = 0;
                 if (tid == 0) {
                     p.glist_n[cur] = 0;
+                    p.garc[cur] = 0;
                     p.gchunk[cur ^ 1] = 0;
+                    *p.gheavy_n = 0;
                 }
             }
             __syncthreads();
@@ -1034,6 +1184,8 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
             if (tid == 0) {
                 p.glist_n[0] = 0;
                 p.glist_n[1] = 0;
+                p.garc[0] = 0;
+                p.garc[1] = 0;
                 p.gchunk[0] = 0;
                 p.gchunk[1] = 0;
                 *p.glog_n = 0;

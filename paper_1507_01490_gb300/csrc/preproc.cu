@@ -313,7 +313,7 @@ __global__ void k_radix_scatter(const K* kin, const uint32_t* vin, K* kout, uint
                                 int shift, const uint32_t* offs, uint32_t ntiles) {
     __shared__ uint32_t s_run[256];
     __shared__ uint32_t s_w[RADIX_THREADS / 32][256];
-    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t wid = threadIdx.x >> 5;
     s_run[threadIdx.x] = offs[(size_t)threadIdx.x * ntiles + blockIdx.x];
     size_t base = (size_t)blockIdx.x * RADIX_TILE;
     for (int r = 0; r < RADIX_ITEMS; ++r) {

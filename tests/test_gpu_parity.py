@@ -236,6 +236,29 @@ def test_errors(B, gen):
         assert h.topk(1)[0].tolist() == [4]
 
 
+def test_bounded_waits_time_out_cleanly(B, gen, orc):
+    """Failure detection without a fault: a wait limit far below any real
+    grid-barrier wait makes the waiting blocks give up.  The kernel records
+    the error and every block leaves; the call returns BCM_ERR_TIMEOUT, and
+    the next calls on the same handle and context are exact."""
+    g = gen.chung_lu(1 << 15, 10.0, 2.3, seed=3)
+    f, r = orc.farness_all(g)
+    exp = orc.topk(f, r, 10)
+    with B.BcmGraph.from_graph(g) as h:
+        for _ in range(2):
+            with pytest.raises(B.BcmError) as ei:
+                h.topk(10, wait_limit_ns=1, flags=B.BCM_GRID_ONLY)
+            assert ei.value.status == B.BCM_ERR_TIMEOUT
+            assert "limit" in str(ei.value)
+            ids, gf, gr, st = h.topk(10)
+            assert np.array_equal(ids, exp) and np.array_equal(gf, f[exp]) and np.array_equal(gr, r[exp])
+        with pytest.raises(B.BcmError) as ei:
+            h.farness_all(wait_limit_ns=1)
+        assert ei.value.status == B.BCM_ERR_TIMEOUT
+        gf, gr, _ = h.farness_all()
+        assert np.array_equal(gf, f) and np.array_equal(gr, r)
+
+
 def test_repeated_runs_reuse_clean_workspace(B, gen, orc):
     g = gen.ba(500, 3, seed=21)
     f, r = orc.farness_all(g)
