@@ -14,9 +14,14 @@ C-ABI from pinned host buffers, the dominant kernel's roofline, the CPU
 oracle timed on a bounded sample, and a bit-exactness check of the result
 against the oracle on sampled outputs.
 
---gpus N (under torchrun) runs N independent replicas, one per GPU: the
-method's sources could be sharded, but no cross-GPU exchange is built, so
-per-GPU work is fixed and scaling is weak.
+--gpus N (under torchrun, one rank per GPU) shares each step's graph among
+the N GPUs: rank r runs the top-k over its shard of the sources (every N-th
+chunk of 64 positions of the degree order), one all-gather brings the
+k-entry lists to every rank and rank 0 merges them (bcm_topk_merge) into the
+graph's top-k.  Preprocessing is repeated on every rank.  Total work per
+step is fixed, so scaling is strong.
+--serve runs the serving benchmark (a graph mix and request streams) and
+--sweep ratio|race the performance-ratio and positive-race sweeps instead.
 --impl reference times the CPU oracle (one BFS per source, all host cores)
 on a bounded sample of the same workload.
 """
@@ -346,7 +351,7 @@ def run_sweep(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)   # ~1.2 s timed: several clock samples
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="chunglu1m", choices=sorted(WORKLOADS))
@@ -359,6 +364,7 @@ def main():
     ap.add_argument("--no-verify", action="store_true", help="skip the oracle check of the result")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer timing")
     ap.add_argument("--no-perk", action="store_true", help="skip the per-k timings")
+    ap.add_argument("--no-autotune", action="store_true", help="library defaults instead of the autotuner")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     ap.add_argument("--serve", action="store_true", help="the serving benchmark (graph mix, request streams)")
@@ -404,8 +410,30 @@ def main():
     far_d = torch.zeros(kbuf, dtype=torch.int64, device=dev)
     reach_d = torch.zeros(kbuf, dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB of L2
-    opts = B.make_options(lanes=args.lanes, threads=args.threads, blocks=args.blocks, flags=B.BCM_OUT_DEVICE)
     torch.cuda.synchronize()
+
+    # launch parameters: the autotuner's choice for this graph (rank 0 tunes,
+    # the others take its choice), unless fixed on the command line
+    tuned, tuning_s = None, 0.0
+    if not args.no_autotune and not (args.lanes or args.threads):
+        from paper_1507_01490_gb300 import autotune
+        if rank == 0:
+            with B.BcmGraph(rp_d, col_d, g.n, g.directed, on_device=True, stream=stream.cuda_stream) as th:
+                tuned, tuning_s, _ = autotune.tuned_options(th, g, k, cache_path=None, rounds=2, reps=2)
+        if dist:
+            box = [tuned]
+            dist.broadcast_object_list(box, src=0)
+            tuned = box[0]
+    par = dict(lanes=args.lanes, threads=args.threads, grid_lanes=0, pull_div=0)
+    if tuned:
+        par.update(lanes=tuned["lanes"], threads=tuned["threads"], grid_lanes=tuned["grid_lanes"],
+                   pull_div=tuned["pull_div"])
+
+    def mkopt(flags, **extra):
+        return B.make_options(lanes=par["lanes"], threads=par["threads"], blocks=args.blocks, flags=flags,
+                              grid_lanes=par["grid_lanes"], pull_div=par["pull_div"], **extra)
+
+    opts = mkopt(B.BCM_OUT_DEVICE)
 
     def step(kq=k, o=opts, stats=None):
         h = B.bcm_graph_create(rp_d, col_d, g.n, g.m, g.directed, ptr_on_device=True,
@@ -415,6 +443,35 @@ def main():
             B.bcm_topk(h, kq, o, ids_d, far_d, reach_d, stats)
         finally:
             B.bcm_graph_destroy(h)
+
+    # N > 1: the ranks share one graph per step.  Rank r takes shard r of the
+    # degree order, then one all-gather brings every shard's list to every
+    # rank and rank 0 merges them (bcm_topk_merge) into the graph's top-k.
+    merged = {}
+    if world > 1:
+        sopts = mkopt(B.BCM_OUT_DEVICE, shard_index=rank, shard_count=world)
+        kloc = min(k, B.shard_size(g.n, rank, world))
+        gath = [torch.zeros((world, k), dtype=t, device=dev) for t in (torch.int32, torch.int64, torch.int32)]
+        cnts = torch.zeros(world, dtype=torch.int64, device=dev)
+
+        def shard_step(stats=None):
+            h = B.bcm_graph_create(rp_d, col_d, g.n, g.m, g.directed, ptr_on_device=True,
+                                   stream=stream.cuda_stream)
+            try:
+                B.bcm_topk(h, k, sopts, ids_d, far_d, reach_d, stats)
+            finally:
+                B.bcm_graph_destroy(h)
+            with torch.cuda.stream(stream):
+                mine = torch.tensor([kloc], dtype=torch.int64, device=dev)
+                dist.all_gather_into_tensor(cnts, mine)
+                for buf, src in zip(gath, (ids_d, far_d, reach_d)):
+                    dist.all_gather_into_tensor(buf.view(-1), src[:k].contiguous())
+            if rank == 0:
+                c = cnts.cpu().numpy()
+                parts = [x.cpu().numpy() for x in gath]
+                sel = [np.concatenate([parts[j][i, :c[i]] for i in range(world)]) for j in range(3)]
+                merged["ids"], merged["far"], merged["reach"] = B.bcm_topk_merge(
+                    sel[0].view(np.uint32), sel[1].view(np.uint64), sel[2].view(np.uint32), k)
 
     def timed(fn, reps):
         """per-step device time (CUDA events on the library's stream), L2 flushed before each"""
@@ -431,8 +488,9 @@ def main():
             ts.append(e0.elapsed_time(e1) / 1e3)
         return ts
 
+    run_step = shard_step if world > 1 else step
     for _ in range(args.warmup):
-        step()
+        run_step()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -441,7 +499,7 @@ def main():
     l0 = B.bcm_launch_count()
     torch.cuda.synchronize()
     t_wall = time.perf_counter()
-    step_times = timed(step, args.steps)
+    step_times = timed(run_step, args.steps)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
     launches = B.bcm_launch_count() - l0
@@ -451,27 +509,35 @@ def main():
         t = torch.tensor([total], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total = float(t.item())
-    s_per_graph = total / (args.steps * world)
+    # N ranks finish one graph per step together
+    s_per_graph = total / args.steps
 
     # one more step with stats (outside the timed region)
     st = B.bcm_stats()
-    step(stats=st)
+    run_step(stats=st)
     st = st.as_dict()
-    got_ids = ids_d[:kk].cpu().numpy().view(np.uint32).copy()
-    got_far = far_d[:kk].cpu().numpy().view(np.uint64).copy()
-    got_reach = reach_d[:kk].cpu().numpy().view(np.uint32).copy()
-
-    if rank != 0:
-        if dist:
-            dist.barrier()
+    if world > 1:
+        shard_stats = st
+        if rank == 0:
+            got_ids, got_far, got_reach = merged["ids"], merged["far"], merged["reach"]
+        dist.barrier()
+        if rank != 0:
             dist.destroy_process_group()
-        return 0
+            return 0
+        st = B.bcm_stats()           # rank 0 alone: the whole graph, for the counters below
+        step(stats=st)
+        st = st.as_dict()
+        same_as_single = bool(np.array_equal(got_ids, ids_d[:kk].cpu().numpy().view(np.uint32)))
+    else:
+        shard_stats = None
+        got_ids = ids_d[:kk].cpu().numpy().view(np.uint32).copy()
+        got_far = far_d[:kk].cpu().numpy().view(np.uint64).copy()
+        got_reach = reach_d[:kk].cpu().numpy().view(np.uint32).copy()
 
     # per-k times and the plain baseline
     per_k = {}
     for kq in ([] if args.no_perk else sorted({1, 10, 100} | {k})):
-        kq_opts = B.make_options(lanes=args.lanes, threads=args.threads, blocks=args.blocks,
-                                 flags=B.BCM_OUT_DEVICE)
+        kq_opts = mkopt(B.BCM_OUT_DEVICE)
         ts = timed(lambda: step(kq, kq_opts), 3)
         s2 = B.bcm_stats()
         step(kq, kq_opts, s2)
@@ -495,7 +561,7 @@ def main():
     ids_h = torch.zeros(kk, dtype=torch.int32).pin_memory()
     far_h = torch.zeros(kk, dtype=torch.int64).pin_memory()
     reach_h = torch.zeros(kk, dtype=torch.int32).pin_memory()
-    hopts = B.make_options(lanes=args.lanes, threads=args.threads, blocks=args.blocks)
+    hopts = mkopt(0)
 
     def e2e_step():
         h = B.bcm_graph_create(rp_h.data_ptr(), col_h.data_ptr(), g.n, g.m, g.directed, ptr_on_device=False,
@@ -508,7 +574,7 @@ def main():
     e2e_t = []
     if not args.no_e2e:
         e2e_step()
-    for _ in range(0 if args.no_e2e else max(3, min(args.steps, 10))):
+    for _ in range(0 if args.no_e2e else max(3, min(args.steps, 20))):
         with torch.cuda.stream(stream):
             flush.zero_()
         torch.cuda.synchronize()
@@ -584,11 +650,18 @@ def main():
     line = {
         "metric": METRIC, "value": s_per_graph, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": "%s: %s" % (args.workload, WORKLOADS[args.workload]), "n": g.n, "m_arcs": g.m,
-                   "k": k, "lanes": args.lanes or 64, "l2": "256 MiB buffer written before every timed step",
-                   "step": "graph handle from device CSR + preprocessing + top-k + release",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "k": k, "lanes": par["lanes"] or 64, "grid_lanes": par["grid_lanes"] or 128,
+                   "pull_div": par["pull_div"] or 32, "threads": par["threads"] or 512,
+                   "launch_parameters": ("autotuned for this graph (%.2f s, outside the timed region)" % tuning_s)
+                   if tuned else "library defaults" if not (args.lanes or args.threads) else "command line",
+                   "l2": "256 MiB buffer written before every timed step",
+                   "step": "graph handle from device CSR + preprocessing + top-k + release" +
+                           (" (each rank its shard of the sources), all-gather of the k-entry lists, "
+                            "merge on rank 0" if world > 1 else ""),
+                   "parallelism": ("source shards over %d GPUs (chunks of 64 of the degree order)" % world)
+                   if world > 1 else "single GPU"},
         "gteps": st["m_vis"] / s_per_graph / 1e9 * world if s_per_graph else None,
         "m_vis": st["m_vis"], "m_tot": m_tot,
         "m_vis_over_m_tot": (st["m_vis"] / m_tot) if m_tot else None,
@@ -604,11 +677,13 @@ def main():
         "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,
+        "shards": None if world == 1 else {"rank0_shard_stats": {kk_: shard_stats[kk_] for kk_ in
+                                                                  ("m_vis", "kernel_ms", "seed_ms", "wave_ms")},
+                                           "merged_equals_single_gpu": same_as_single},
         "wall_s_timed_region": t_wall,
     }
     print(json.dumps(line), flush=True)
     if dist:
-        dist.barrier()
         dist.destroy_process_group()
     return 0
 

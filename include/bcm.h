@@ -105,6 +105,11 @@ typedef struct {
                                  and hands its live sources to a second grid-wide pass, which
                                  runs them from the start; 0 = default (heavy_words) */
     uint64_t wait_limit_ns;   /* limit of every in-kernel wait; 0 = default (20 s) */
+    uint32_t shard_index;     /* bcm_topk over one shard of the sources (several GPUs, one graph):  */
+    uint32_t shard_count;     /* the positions p of the degree order with (p / 64) % shard_count ==
+                                 shard_index; the result is that shard's own top-k, min(k, shard
+                                 size) entries, and bcm_topk_merge of every shard's lists is the
+                                 graph's top-k.  shard_count 0 or 1 = every source */
 } bcm_options;
 
 typedef struct {
@@ -271,6 +276,19 @@ bcm_status bcm_farness_all(bcm_graph_t g, const bcm_options* opt, uint64_t* farn
  */
 bcm_status bcm_farness_all_noalloc(const uint64_t* row_ptr, const uint32_t* col, uint32_t n, uint64_t m,
                                    void* stream, uint64_t* farness, uint32_t* reach);
+
+/*
+ * bcm_topk_merge -- the best min(k, count) of `count` (id, farness, reach)
+ * entries under the ranking above (exact 128-bit comparisons, equal scores
+ * by id), written best first to out_ids / out_far / out_reach.  Host memory
+ * only; runs on the CPU (it merges the k-entry lists of several shards,
+ * whose union holds the graph's top-k).  Ids must be distinct.  Returns the
+ * number of entries written in *written.  Errors: BCM_ERR_INVALID (NULL
+ * pointer, k = 0), BCM_ERR_OOM.
+ */
+bcm_status bcm_topk_merge(const uint32_t* ids, const uint64_t* farness, const uint32_t* reach, uint32_t count,
+                          uint32_t k, uint32_t* out_ids, uint64_t* out_far, uint32_t* out_reach,
+                          uint32_t* written);
 
 /* Thread-local message for the last failing call ("" if none). */
 const char* bcm_last_error(void);

@@ -40,14 +40,15 @@ TRACE_GRID_LEVEL, TRACE_GRID_WAVE, TRACE_CTA_WAVE = 0, 1, 2
 # every symbol include/bcm.h declares
 EXPORTS = ["bcm_graph_create", "bcm_graph_destroy", "bcm_preprocess", "bcm_scc_bounds", "bcm_topk",
            "bcm_topk_start", "bcm_topk_finish", "bcm_trace", "bcm_graph_trim",
-           "bcm_farness_all", "bcm_farness_all_noalloc", "bcm_last_error", "bcm_launch_count",
+           "bcm_farness_all", "bcm_farness_all_noalloc", "bcm_topk_merge", "bcm_last_error", "bcm_launch_count",
            "bcm_workspace_bytes"]
 
 
 class bcm_options(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_uint32), ("grid_lanes", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("blocks", ctypes.c_uint32), ("threads", ctypes.c_uint32), ("heavy_words", ctypes.c_uint32),
-                ("pull_div", ctypes.c_uint32), ("defer_words", ctypes.c_uint32), ("wait_limit_ns", ctypes.c_uint64)]
+                ("pull_div", ctypes.c_uint32), ("defer_words", ctypes.c_uint32), ("wait_limit_ns", ctypes.c_uint64),
+                ("shard_index", ctypes.c_uint32), ("shard_count", ctypes.c_uint32)]
 
 
 class bcm_stats(ctypes.Structure):
@@ -98,6 +99,7 @@ def load():
         "bcm_graph_trim": (i32, [vp]),
         "bcm_farness_all": (i32, [vp, ctypes.POINTER(bcm_options), vp, vp, ctypes.POINTER(bcm_stats)]),
         "bcm_farness_all_noalloc": (i32, [vp, vp, u32, u64, vp, vp, vp]),
+        "bcm_topk_merge": (i32, [vp, vp, vp, u32, u32, vp, vp, vp, ctypes.POINTER(u32)]),
         "bcm_last_error": (ctypes.c_char_p, []),
         "bcm_launch_count": (u64, []),
         "bcm_workspace_bytes": (u64, [vp, ctypes.POINTER(bcm_options)]),
@@ -131,6 +133,26 @@ def _check(st):
         raise BcmError(st, bcm_last_error())
 
 
+SHARD_CHUNK = 64
+
+
+def shard_size(n, index, count):
+    """Sources of shard `index` of `count`: the degree order's positions p
+    with (p // 64) % count == index (the rule of bcm_options.shard_*)."""
+    if count <= 1:
+        return n
+    rnd = SHARD_CHUNK * count
+    rem = n % rnd
+    lo = index * SHARD_CHUNK
+    return (n // rnd) * SHARD_CHUNK + (min(rem - lo, SHARD_CHUNK) if rem > lo else 0)
+
+
+def shard_positions(n, index, count):
+    """The degree-order positions shard `index` of `count` takes, in order."""
+    p = np.arange(n, dtype=np.int64)
+    return p if count <= 1 else p[(p // SHARD_CHUNK) % count == index]
+
+
 def bcm_last_error() -> str:
     return load().bcm_last_error().decode()
 
@@ -140,8 +162,9 @@ def bcm_launch_count() -> int:
 
 
 def make_options(lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0, grid_lanes=0,
-                 heavy_words=0, pull_div=0, defer_words=0) -> bcm_options:
-    return bcm_options(lanes, grid_lanes, flags, blocks, threads, heavy_words, pull_div, defer_words, wait_limit_ns)
+                 heavy_words=0, pull_div=0, defer_words=0, shard_index=0, shard_count=0) -> bcm_options:
+    return bcm_options(lanes, grid_lanes, flags, blocks, threads, heavy_words, pull_div, defer_words, wait_limit_ns,
+                       shard_index, shard_count)
 
 
 def bcm_graph_create(row_ptr, col, n, m, directed, ptr_on_device=False, stream=None, flags=0):
@@ -217,6 +240,23 @@ def bcm_farness_all_noalloc(row_ptr, col, n, m, stream, farness, reach):
                                           _ptr(reach)))
 
 
+def bcm_topk_merge(ids, farness, reach, k):
+    """The best min(k, len(ids)) entries of the given lists (host arrays), best first."""
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    far = np.ascontiguousarray(farness, dtype=np.uint64)
+    rch = np.ascontiguousarray(reach, dtype=np.uint32)
+    if not (len(ids) == len(far) == len(rch)):
+        raise ValueError("ids, farness and reach must have the same length")
+    w = max(min(k, len(ids)), 1)
+    oi, of, orr = np.zeros(w, np.uint32), np.zeros(w, np.uint64), np.zeros(w, np.uint32)
+    written = ctypes.c_uint32(0)
+    _check(load().bcm_topk_merge(_ptr(ids) if len(ids) else None, _ptr(far) if len(ids) else None,
+                                 _ptr(rch) if len(ids) else None, len(ids), k, _ptr(oi), _ptr(of), _ptr(orr),
+                                 ctypes.byref(written)))
+    n = int(written.value)
+    return oi[:n], of[:n], orr[:n]
+
+
 def bcm_workspace_bytes(h, options=None) -> int:
     return int(load().bcm_workspace_bytes(h, ctypes.byref(options) if options is not None else None))
 
@@ -271,15 +311,16 @@ class BcmGraph:
         return comp[:self.n], al[:self.n], om[:self.n], nc
 
     def topk(self, k, lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0, grid_lanes=0, heavy_words=0,
-             pull_div=0, defer_words=0):
+             pull_div=0, defer_words=0, shard_index=0, shard_count=0):
         kk = max(min(k, self.n), 1)
         ids = np.zeros(kk, np.uint32)
         far = np.zeros(kk, np.uint64)
         reach = np.zeros(kk, np.uint32)
         st = bcm_stats()
         bcm_topk(self.h, k, make_options(lanes, flags, blocks, threads, wait_limit_ns, grid_lanes, heavy_words,
-                                         pull_div, defer_words), ids, far, reach, st)
-        kk = min(k, self.n)
+                                         pull_div, defer_words, shard_index, shard_count), ids, far, reach, st)
+        n_src = shard_size(self.n, shard_index, shard_count) if shard_count > 1 else self.n
+        kk = min(k, n_src)
         return ids[:kk], far[:kk], reach[:kk], st.as_dict()
 
     def trace(self):

@@ -1,5 +1,6 @@
 // The C-ABI of include/bcm.h: graph handles, preprocessing, the wave
 // kernels' workspace and launch sequence, and error reporting.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cstdarg>
@@ -215,6 +216,7 @@ struct bcm_graph {
     // start, first grid pass done, per-CTA pass done, deferred grid pass done, copies done
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     uint32_t* d_defer = nullptr;   // [n] sources deferred by per-CTA waves
+    uint32_t* d_shard = nullptr;   // [n] this shard's sources, in degree order
     HostBlock* h = nullptr;        // pinned
     unsigned long long* d_trace = nullptr;   // kTraceCap records of 4 words
     uint32_t trace_n = 0;          // records of the last finished traced run
@@ -229,6 +231,7 @@ struct Cfg {
     uint32_t pull_div;
     uint64_t heavy_words;
     uint64_t defer_words;
+    uint32_t shard_index, shard_count;
     uint64_t limit_ns;
     uint32_t flags;
 };
@@ -265,6 +268,10 @@ bcm_status resolve(bcm_graph* g, const bcm_options* opt, Cfg* c) {
     c->heavy_words = o.heavy_words ? o.heavy_words : (uint64_t)gb * 16 * 4;   // 4 words per warp and level
     c->pull_div = (c->flags & BCM_NO_PULL) ? 0u : o.pull_div;   // 0: per-mode default below
     c->defer_words = (c->flags & BCM_NO_DEFER) ? 0 : (o.defer_words ? o.defer_words : c->heavy_words);
+    c->shard_count = o.shard_count > 1 ? o.shard_count : 1;
+    c->shard_index = o.shard_count > 1 ? o.shard_index : 0;
+    if (c->shard_index >= c->shard_count)
+        return fail(BCM_ERR_INVALID, "shard_index %u is not below shard_count %u", o.shard_index, o.shard_count);
     if ((c->flags & BCM_CTA_ONLY) && (c->flags & BCM_GRID_ONLY))
         return fail(BCM_ERR_INVALID, "BCM_CTA_ONLY and BCM_GRID_ONLY exclude each other");
     return BCM_OK;
@@ -507,6 +514,28 @@ struct RunTimes {
 
 bcm_status copy_out(void* dst, const void* src, size_t bytes, bool dev, cudaStream_t s);
 
+// Sources of one shard: the degree order's positions in every
+// count-th chunk of kShardChunk, starting with chunk `index`.
+constexpr uint32_t kShardChunk = 64;
+
+__global__ void k_shard_sources(const uint32_t* order, uint32_t n_local, uint32_t index, uint32_t count,
+                                uint32_t* out) {
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n_local; i += stride) {
+        const size_t pos = ((i / kShardChunk) * count + index) * kShardChunk + i % kShardChunk;
+        out[i] = order[pos];
+    }
+}
+
+// Positions of the degree order that fall to shard `index` of `count`.
+uint32_t shard_size(uint32_t n, uint32_t index, uint32_t count) {
+    const uint64_t C = kShardChunk, round = C * count;
+    const uint64_t rem = n % round, lo = (uint64_t)index * C;
+    uint64_t r = (n / round) * C;
+    if (rem > lo) r += (rem - lo < C ? rem - lo : C);
+    return (uint32_t)r;
+}
+
 bcm_status ensure_run_state(bcm_graph* g, bool trace) {
     for (int i = 0; i < 5; ++i)
         if (!g->ev[i]) CU(cudaEventCreate(&g->ev[i]), "event");
@@ -538,6 +567,19 @@ bcm_status start_run(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, vo
     WaveParams p = base_params(g, c);
     p.exhaustive = exhaustive ? 1u : 0u;
     p.topk.k = k;
+    uint32_t n_src = g->n;   // sources this run takes
+    if (!exhaustive && c.shard_count > 1) {
+        n_src = shard_size(g->n, c.shard_index, c.shard_count);
+        if (!g->d_shard) CU(cudaMalloc(&g->d_shard, (size_t)g->n * sizeof(uint32_t)), "shard list allocation");
+        if (n_src) {
+            unsigned blocks = (n_src + 255) / 256 < 4864 ? (n_src + 255) / 256 : 4864;
+            k_shard_sources<<<blocks, 256, 0, s>>>(g->d_order, n_src, c.shard_index, c.shard_count, g->d_shard);
+            note_launch();
+            CU(cudaGetLastError(), "shard list kernel");
+        }
+        p.sources = g->d_shard;
+        p.n_end = n_src;
+    }
     p.out_far = g->d_far;
     p.out_reach = g->d_reach;
     if (trace) {
@@ -619,7 +661,7 @@ bcm_status start_run(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, vo
         if ((st = copy_out(o_far, g->d_far, (size_t)g->n * sizeof(uint64_t), dev, s))) return st;
         if ((st = copy_out(o_reach, g->d_reach, (size_t)g->n * sizeof(uint32_t), dev, s))) return st;
     } else {
-        const uint32_t kk = k < g->n ? k : g->n;
+        const uint32_t kk = k < n_src ? k : n_src;
         if ((st = copy_out(o_ids, a->topk_id, kk * sizeof(uint32_t), dev, s))) return st;
         if ((st = copy_out(o_far, a->topk_f, kk * sizeof(uint64_t), dev, s))) return st;
         if ((st = copy_out(o_reach, a->topk_r, kk * sizeof(uint32_t), dev, s))) return st;
@@ -628,7 +670,7 @@ bcm_status start_run(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, vo
     g->pend.active = true;
     g->pend.exhaustive = exhaustive;
     g->pend.plain = plain;
-    g->pend.kk = k < g->n ? k : g->n;
+    g->pend.kk = k < n_src ? k : n_src;
     g->pend.flags = c.flags;
     return BCM_OK;
 }
@@ -825,6 +867,7 @@ bcm_status bcm_graph_destroy(bcm_graph_t g) {
     cudaFree(g->d_rcol);
     cudaFree(g->d_trace);
     cudaFree(g->d_defer);
+    cudaFree(g->d_shard);
     for (int i = 0; i < 5; ++i)
         if (g->ev[i]) cudaEventDestroy(g->ev[i]);
     if (g->h) cudaFreeHost(g->h);
@@ -980,12 +1023,56 @@ bcm_status bcm_graph_trim(bcm_graph_t g) {
     cudaFree(g->d_reach);
     cudaFree(g->d_trace);
     cudaFree(g->d_defer);
+    cudaFree(g->d_shard);
     g->d_defer = nullptr;
+    g->d_shard = nullptr;
     g->d_plain = nullptr;
     g->d_far = nullptr;
     g->d_reach = nullptr;
     g->d_trace = nullptr;
     g->trace_n = 0;
+    return BCM_OK;
+}
+
+bcm_status bcm_topk_merge(const uint32_t* ids, const uint64_t* farness, const uint32_t* reach, uint32_t count,
+                          uint32_t k, uint32_t* out_ids, uint64_t* out_far, uint32_t* out_reach,
+                          uint32_t* written) {
+    t_err.clear();
+    if (k == 0) return fail(BCM_ERR_INVALID, "k must be at least 1");
+    if (!written || (count && (!ids || !farness || !reach)) || !out_ids || !out_far || !out_reach)
+        return fail(BCM_ERR_INVALID, "a pointer argument is NULL");
+    std::vector<uint32_t> idx;
+    try {
+        idx.resize(count);
+    } catch (...) {
+        return fail(BCM_ERR_OOM, "host allocation");
+    }
+    for (uint32_t i = 0; i < count; ++i) idx[i] = i;
+    // (N, F) = ((r-1)^2, f), or (0, 1) when r <= 1; a before b iff
+    // N_a F_b > N_b F_a, or equal and id_a < id_b
+    auto key = [&](uint32_t i, unsigned __int128& N, unsigned __int128& F) {
+        if (reach[i] <= 1) { N = 0; F = 1; return; }
+        const uint64_t r1 = reach[i] - 1;
+        N = (unsigned __int128)r1 * r1;
+        F = farness[i];
+    };
+    auto before = [&](uint32_t a, uint32_t b) {
+        unsigned __int128 Na, Fa, Nb, Fb;
+        key(a, Na, Fa);
+        key(b, Nb, Fb);
+        // N < 2^60 and F < 2^62, so the products fit in 128 bits
+        const unsigned __int128 l = Na * Fb, r = Nb * Fa;
+        if (l != r) return l > r;
+        return ids[a] < ids[b];
+    };
+    const uint32_t w = k < count ? k : count;
+    std::partial_sort(idx.begin(), idx.begin() + w, idx.end(), before);
+    for (uint32_t i = 0; i < w; ++i) {
+        out_ids[i] = ids[idx[i]];
+        out_far[i] = farness[idx[i]];
+        out_reach[i] = reach[idx[i]];
+    }
+    *written = w;
     return BCM_OK;
 }
 
