@@ -249,7 +249,8 @@ def run_serve(args, rank, world):
         last = res
     launches = __import__("paper_1507_01490_gb300.bcm", fromlist=["x"]).bcm_launch_count() - l0
     clk = clocks.stop()
-    # the same requests alone
+    # the same requests alone (each graph's workspace given back first)
+    be.trim_all()
     rng = np.random.default_rng(3)
     pick = rng.choice(len(last), size=min(args.serve_check, len(last)), replace=False)
     same = True
@@ -372,7 +373,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rates", default="0.5,0.8,1.0", help="fractions of the measured capacity")
     ap.add_argument("--serve-inflight", type=int, default=16)
-    ap.add_argument("--serve-budget-gb", type=float, default=160.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--serve-check", type=int, default=300, help="results compared with the request alone")
     ap.add_argument("--sweep", choices=["ratio", "race"], help="a sweep instead of the benchmark")
     ap.add_argument("--sweep-lo", type=int, default=14, help="ratio sweep: smallest n = 2^lo")

@@ -75,6 +75,9 @@ typedef enum {
                                    Section 2.3, without its biggest-SCC refinement (results are the same) */
 #define BCM_TRACE         0x100u /* record the run's trace (read it with bcm_trace) */
 #define BCM_NO_DEFER      0x200u /* per-CTA waves never hand their sources to the grid-wide pass */
+#define BCM_NO_PREFILTER  0x400u /* no level-0/1 prefilter before the per-CTA waves (it runs on simple
+                                    graphs -- sorted rows, no repeated arc, no self-loop -- after the
+                                    grid-wide waves; results are the same) */
 
 /* Sources are taken from the degree order in waves.  Waves run first on a
  * grid-wide kernel (all CTAs on one wave) while they are heavy, then on a
@@ -101,9 +104,10 @@ typedef struct {
     uint32_t pull_div;        /* a grid-wave level is expanded by pull when the out-arcs of its
                                  frontier's (vertex, word) entries number at least n*W/pull_div
                                  (W = grid_lanes/64); 0 = default (32) */
-    uint32_t defer_words;     /* a per-CTA wave whose next frontier reaches this many words stops
-                                 and hands its live sources to a second grid-wide pass, which
-                                 runs them from the start; 0 = default (heavy_words) */
+    uint32_t defer_words;     /* a per-CTA wave about to expand a level of this many words (or of 8x
+                                 as many out-arcs) stops and hands its live sources to a second
+                                 grid-wide pass, which runs them from the start; 0 = default
+                                 (heavy_words) */
     uint64_t wait_limit_ns;   /* limit of every in-kernel wait; 0 = default (20 s) */
     uint32_t shard_index;     /* bcm_topk over one shard of the sources (several GPUs, one graph):  */
     uint32_t shard_count;     /* the positions p of the degree order with (p / 64) % shard_count ==

@@ -33,6 +33,7 @@ BCM_NO_PULL = 0x40
 BCM_PLAIN_BOUNDS = 0x80
 BCM_TRACE = 0x100
 BCM_NO_DEFER = 0x200
+BCM_NO_PREFILTER = 0x400
 
 # trace record kinds (bits 60..63 of a record's second word)
 TRACE_GRID_LEVEL, TRACE_GRID_WAVE, TRACE_CTA_WAVE = 0, 1, 2

@@ -74,6 +74,10 @@ static bcm_status region_acquire(size_t bytes, const Layout& lay, cudaStream_t s
         for (size_t i = 0; i < g_regions.size(); ++i) {
             const Region& r = g_regions[i];
             if (r.dev != dev || r.bytes < bytes) continue;
+            // a much larger region stays for a run that needs it: a small run
+            // holding it would hide that memory from the caller's accounting
+            // (bcm_workspace_bytes)
+            if (r.bytes > 2 * bytes + (64ull << 20)) continue;
             // prefer a region already zero under this layout, then the smallest
             if (best < 0 || (r.layout == lay && !(g_regions[best].layout == lay)) ||
                 ((r.layout == lay) == (g_regions[best].layout == lay) && r.bytes < g_regions[best].bytes))
@@ -159,6 +163,8 @@ struct Aux {
     uint32_t trace_n;
     uint32_t defer_n;     // sources handed back by per-CTA waves
     uint32_t head2;       // queue head of the grid-wide pass over them
+    uint32_t surv_n;      // sources the prefilter could not stop
+    uint32_t head3;       // queue head of the per-CTA waves over them
 };
 
 // Host side of a run in flight: pinned memory the run's counters are copied
@@ -195,6 +201,7 @@ struct bcm_graph {
     uint32_t* d_rcol = nullptr;
     uint32_t n_comp = 0;
     bool labels_ready = false;     // d_comp holds labels (else component roots)
+    bool simple = false;           // rows strictly increasing, no self-loops
     bool preprocessed = false;
     Aux* d_aux = nullptr;
     uint32_t* d_plain = nullptr;   // stamps [n], two vertex queues [2n]
@@ -217,6 +224,7 @@ struct bcm_graph {
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     uint32_t* d_defer = nullptr;   // [n] sources deferred by per-CTA waves
     uint32_t* d_shard = nullptr;   // [n] this shard's sources, in degree order
+    uint32_t* d_surv = nullptr;    // [n] sources left for the per-CTA waves by the prefilter
     HostBlock* h = nullptr;        // pinned
     unsigned long long* d_trace = nullptr;   // kTraceCap records of 4 words
     uint32_t trace_n = 0;          // records of the last finished traced run
@@ -277,9 +285,11 @@ bcm_status resolve(bcm_graph* g, const bcm_options* opt, Cfg* c) {
     return BCM_OK;
 }
 
-// CTA slots first, then one slot (4 words per vertex) for the seed wave.
+// CTA slots first, then one slot (4 words per vertex) for the grid-wide waves and their bitmaps.
 size_t cta_region_bytes(bcm_graph* g, const Cfg& c) { return (size_t)c.blocks * slot_bytes(g->n, c.W); }
-size_t region_bytes(bcm_graph* g, const Cfg& c) { return cta_region_bytes(g, c) + slot_bytes(g->n, 4); }
+size_t region_bytes(bcm_graph* g, const Cfg& c) {
+    return cta_region_bytes(g, c) + slot_bytes(g->n, 4) + bitmap_bytes(g->n);
+}
 Layout region_layout(bcm_graph* g, const Cfg& c) {
     Layout l;
     l.n = g->n;
@@ -458,6 +468,8 @@ WaveParams base_params(bcm_graph* g, const Cfg& c) {
     p.slot_base = (char*)g->slots.ptr;
     p.slot_stride = slot_bytes(g->n, c.W);
     p.seed_base = (char*)g->slots.ptr + cta_region_bytes(g, c);
+    p.gbm = (uint32_t*)(p.seed_base + slot_bytes(g->n, 4));
+    p.nbw = (g->n + 31) / 32;
     p.stats = a->stats;
     p.err = &a->err;
     p.lock_limit_ns = c.limit_ns;
@@ -624,9 +636,36 @@ bcm_status start_run(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, vo
             p.pull_div = (c.flags & BCM_NO_PULL) ? 0u : (c.pull_div ? c.pull_div : 32u);
             rc = launch_grid_waves(p, c.grid_W, c.grid_blocks, 512, s);
         }
-        cudaEventRecord(g->ev[1], s);
         p.stats = g->d_aux->stats;
-        if (rc == 0) rc = launch_cta_waves(p, c.W, c.blocks, c.threads, s);
+        // a graph too small for grid-wide waves: one CTA first runs the
+        // first wave alone (the highest-degree sources), so the threshold
+        // exists before the other waves start (otherwise they all start at
+        // once, and none of them can be stopped)
+        const bool seed = !grid && rc == 0 && !exhaustive && !(c.flags & (BCM_CTA_ONLY | BCM_NO_PREFILTER));
+        if (seed) {
+            WaveParams ps = p;
+            ps.max_cta_waves = 1;
+            rc = launch_cta_waves(ps, c.W, 1, c.threads, s);
+        }
+        cudaEventRecord(g->ev[1], s);
+        WaveParams pc = p;
+        // on a simple graph, the sources the grid (or the seed wave) left are
+        // first tested at levels 0 and 1 from degrees alone; the waves take
+        // the rest
+        const bool prefilter = (grid || seed) && rc == 0 && g->simple &&
+                               !(c.flags & (BCM_NO_PREFILTER | BCM_GRID_ONLY));
+        if (prefilter) {
+            if (!g->d_surv) {
+                cudaError_t e = cudaMalloc(&g->d_surv, (size_t)g->n * sizeof(uint32_t));
+                if (e != cudaSuccess) { cudaStreamSynchronize(s); return cuda_fail(e, "prefilter list allocation"); }
+            }
+            rc = launch_prefilter(p, g->d_surv, &g->d_aux->surv_n, s);
+            pc.sources = g->d_surv;
+            pc.head = &g->d_aux->head3;
+            pc.n_end = 0;
+            pc.n_end_dev = &g->d_aux->surv_n;
+        }
+        if (rc == 0) rc = launch_cta_waves(pc, c.W, c.blocks, c.threads, s);
         cudaEventRecord(g->ev[2], s);
         if (defer && rc == 0) {
             // the deferred sources, on the grid kernel, every wave
@@ -817,20 +856,26 @@ bcm_status bcm_graph_create(const uint64_t* row_ptr, const uint32_t* col, uint32
         cudaError_t e;
         if ((e = cudaMalloc(&g->d_rp, ((size_t)n + 1) * sizeof(uint32_t))) != cudaSuccess) { st = cuda_fail(e, "graph allocation"); break; }
         if ((e = cudaMalloc(&g->d_col, (m ? m : 1) * sizeof(uint32_t))) != cudaSuccess) { st = cuda_fail(e, "graph allocation"); break; }
-        if ((e = cudaMalloc(&d_rp64, ((size_t)n + 1) * sizeof(uint64_t) + sizeof(int) * 2)) != cudaSuccess) { st = cuda_fail(e, "graph allocation"); break; }
+        if ((e = cudaMalloc(&d_rp64, ((size_t)n + 1) * sizeof(uint64_t) + sizeof(int) * 4)) != cudaSuccess) { st = cuda_fail(e, "graph allocation"); break; }
         d_err = (int*)(d_rp64 + n + 1);
         cudaMemcpyKind kind = ptr_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         if ((e = cudaMemcpyAsync(d_rp64, row_ptr, ((size_t)n + 1) * sizeof(uint64_t), kind, s)) != cudaSuccess) { st = cuda_fail(e, "row_ptr copy"); break; }
         if (m && (e = cudaMemcpyAsync(g->d_col, col, m * sizeof(uint32_t), kind, s)) != cudaSuccess) { st = cuda_fail(e, "col copy"); break; }
-        if ((e = cudaMemsetAsync(d_err, 0, 2 * sizeof(int), s)) != cudaSuccess) { st = cuda_fail(e, "memset"); break; }
+        if ((e = cudaMemsetAsync(d_err, 0, 4 * sizeof(int), s)) != cudaSuccess) { st = cuda_fail(e, "memset"); break; }
         if (launch_validate(d_rp64, g->d_col, n, m, d_err, s) || launch_narrow_offsets(d_rp64, g->d_rp, n, s)) {
             st = fail(BCM_ERR_CUDA, "validation kernels: %s", cudaGetErrorString(cudaGetLastError()));
             break;
         }
-        int herr[2] = {0, 0};
+        int herr[4] = {0, 0, 0, 0};
         if ((e = cudaMemcpyAsync(herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) { st = cuda_fail(e, "copy"); break; }
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { st = cuda_fail(e, "graph upload"); break; }
         if (herr[0]) { st = fail(BCM_ERR_INVALID, "malformed CSR: row_ptr must rise from 0 to m and every col < n"); break; }
+        // simple (sorted rows, no repeated arc, no self-loop): level 1 of every
+        // BFS is then known from degrees alone (see the prefilter)
+        if (launch_simple_check(g->d_rp, g->d_col, n, d_err + 2, s)) { st = fail(BCM_ERR_CUDA, "simple-graph check"); break; }
+        if ((e = cudaMemcpyAsync(&herr[2], d_err + 2, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) { st = cuda_fail(e, "copy"); break; }
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { st = cuda_fail(e, "graph upload"); break; }
+        g->simple = herr[2] == 0;
         if (!directed && (flags & BCM_CHECK_SYMMETRIC) && n > 0) {
             if ((e = cudaMemsetAsync(d_err + 1, 0, sizeof(int), s)) != cudaSuccess) { st = cuda_fail(e, "memset"); break; }
             unsigned blocks = (unsigned)(((size_t)n * 32 + 255) / 256);
@@ -868,6 +913,7 @@ bcm_status bcm_graph_destroy(bcm_graph_t g) {
     cudaFree(g->d_trace);
     cudaFree(g->d_defer);
     cudaFree(g->d_shard);
+    cudaFree(g->d_surv);
     for (int i = 0; i < 5; ++i)
         if (g->ev[i]) cudaEventDestroy(g->ev[i]);
     if (g->h) cudaFreeHost(g->h);
@@ -1024,6 +1070,8 @@ bcm_status bcm_graph_trim(bcm_graph_t g) {
     cudaFree(g->d_trace);
     cudaFree(g->d_defer);
     cudaFree(g->d_shard);
+    cudaFree(g->d_surv);
+    g->d_surv = nullptr;
     g->d_defer = nullptr;
     g->d_shard = nullptr;
     g->d_plain = nullptr;

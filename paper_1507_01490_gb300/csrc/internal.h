@@ -43,6 +43,8 @@ struct GraphDev {
 // vertex.  Word index of (vertex v, word g) is v*W + g; each word has a
 // 32-byte record (vis, F[0], F[1], padding), then two frontier lists and a
 // clear log of 4-byte word indices.
+inline size_t bitmap_bytes(uint32_t n) { return ((((size_t)n + 31) / 32) * 2 * sizeof(uint32_t) + 255) & ~(size_t)255; }
+
 inline size_t slot_bytes(uint32_t n, int W) {
     size_t nw = (size_t)n * W;
     size_t b = nw * (4 * sizeof(uint64_t) + 3 * sizeof(uint32_t));
@@ -70,6 +72,8 @@ struct WaveParams {
     char* slot_base;         // CTA i: slot_base + i * slot_stride
     size_t slot_stride;
     char* seed_base;         // the grid kernel's own slot (4 words per vertex)
+    uint32_t* gbm;           // grid kernel: two frontier bitmaps of nbw words (one bit per vertex), zero between runs
+    uint32_t nbw;
     unsigned long long* stats;   // [ST_COUNT]
     int* err;
     unsigned long long lock_limit_ns;
@@ -87,12 +91,15 @@ struct WaveParams {
     uint32_t max_grid_waves;  // grid kernel: at most this many waves
     uint64_t heavy_words;   // grid kernel: a wave with fewer frontier words in total is light
     uint32_t pull_div;      // grid kernel: pull a level whose frontier words have >= n*W/pull_div out-arcs (0: never)
-    // per-CTA kernel: a wave whose next frontier reaches defer_words words is
-    // given up and its live sources appended to defer_src (0: never)
+    // per-CTA kernel: a wave about to expand a level of at least defer_words
+    // words, or of at least 8 * defer_words out-arcs, is given up and its
+    // live sources appended to defer_src (0: never)
     uint32_t defer_words;
     uint32_t* defer_n;
     uint32_t* defer_src;
-    // grid kernel: when set, the sources end at *n_end_dev (read at launch)
+    // per-CTA kernel: each CTA stops after this many waves (0: when the queue is empty)
+    uint32_t max_cta_waves;
+    // when set, the sources end at *n_end_dev (read at launch)
     const uint32_t* n_end_dev;
     // optional trace: records of 4 u64 (layout in include/bcm.h, bcm_trace), NULL when off
     unsigned long long* trace;
@@ -107,6 +114,8 @@ enum TraceKind { TR_GRID_LEVEL = 0, TR_GRID_WAVE = 1, TR_CTA_WAVE = 2 };
 int launch_validate(const uint64_t* rp64, const uint32_t* col, uint32_t n, uint64_t m, int* err,
                     cudaStream_t s);
 int launch_narrow_offsets(const uint64_t* rp64, uint32_t* rp32, uint32_t n, cudaStream_t s);
+// *not_simple |= 1 unless every row is strictly increasing and free of its own vertex
+int launch_simple_check(const uint32_t* rp32, const uint32_t* col, uint32_t n, int* not_simple, cudaStream_t s);
 int launch_cc_reach(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t* parent,
                     uint32_t* size, uint32_t* xlo, uint32_t* xhi, int* err, cudaStream_t s);
 int launch_degree_order(const uint32_t* rp, uint32_t n, uint32_t* order, void* scratch,
@@ -139,6 +148,9 @@ int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, const uint32_t* r
 // ---- msbfs.cu
 int launch_grid_waves(const WaveParams& p, int W, int blocks, int threads, cudaStream_t s);
 int launch_cta_waves(const WaveParams& p, int W, int blocks, int threads, cudaStream_t s);
+// level-0/1 stopping rule for sources p.sources[*p.head .. p.n_end) of a simple graph;
+// the sources it cannot stop are appended to out (count in *out_n)
+int launch_prefilter(const WaveParams& p, uint32_t* out, uint32_t* out_n, cudaStream_t s);
 int launch_plain_source(const WaveParams& p, uint32_t it, uint32_t* stamp, uint32_t* lists,
                         int blocks, int threads, cudaStream_t s);
 int max_coop_blocks(int kind, int W, int threads);   // kind 0 grid waves, 1 plain

@@ -195,13 +195,18 @@ __device__ __forceinline__ void push_vis(u64* vis, Push& q, u64& old) {
     old = q.nb ? atomicOr(&vis[ri(q.word)], q.nb) : ~0ull;
 }
 
-__device__ __forceinline__ void push_next(u64* Fnext, Push& q, u64 old, u32 foot, LocalStats& st) {
+__device__ __forceinline__ void push_next(u64* Fnext, Push& q, u64 old, u32 foot, LocalStats& st, u32* bmn) {
     if (!q.nb) return;
     q.fl = (old == 0) ? 2u : 0u;
     q.nb &= ~old;
     if (!q.nb) return;
     u64 oldF = atomicOr(&Fnext[ri(q.word)], q.nb);
-    if (oldF == 0) { q.fl |= 1u; st.discwords++; st.fwarcs += q.r1 - q.r0; }
+    if (oldF == 0) {
+        q.fl |= 1u;
+        st.discwords++;
+        st.fwarcs += q.r1 - q.r0;
+        if (bmn) atomicOr(&bmn[q.x >> 5], 1u << (q.x & 31));   // x is in the next frontier
+    }
     q.degp = q.r1 - q.r0 - foot;
     st.disc += __popcll(q.nb);
 }
@@ -286,7 +291,7 @@ template <int W>
 __device__ inline void expand_sources(const GraphDev& G, const u32* s_src, const u32* s_alive32, const u32* s_pre,
                                       const u32* s_beg, int L, u64* vis, u64* Fnext, u32* cg, u32* cs, u32 foot,
                                       WarpQueue& nq, WarpQueue& lq, u32 wid, u32 nw, u32 tid, u32 nthreads,
-                                      LocalStats& st) {
+                                      LocalStats& st, u32* bmn) {
     const u32 lane = threadIdx.x & 31;
     lq.reserve(32);
     for (u32 j0 = tid - lane; j0 < (u32)L; j0 += nthreads) {
@@ -325,7 +330,7 @@ __device__ inline void expand_sources(const GraphDev& G, const u32* s_src, const
             push_check<W>(G.rp, vis, q);
             u64 old;
             push_vis(vis, q, old);
-            push_next(Fnext, q, old, foot, st);
+            push_next(Fnext, q, old, foot, st, bmn);
         } else {
             q.nb = 0;
         }
@@ -353,7 +358,7 @@ template <int W>
 __device__ inline void expand_entries(const GraphDev& G, const u32* list, u32 cnt, u64* Fcur,
                                       const u32* s_alive32, u64* vis, u64* Fnext, u32* cg, u32* cs,
                                       u32 foot, WarpQueue& nq, WarpQueue& lq, u32* chunk_ctr, u32 nw,
-                                      const HeavyList& H, LocalStats& st) {
+                                      const HeavyList& H, LocalStats& st, u32* bmn) {
     const u32 lane = threadIdx.x & 31;
     // entries taken per counter reservation: 32 when the frontier is small,
     // up to 256 when it is large enough to keep every warp busy anyway
@@ -434,7 +439,7 @@ __device__ inline void expand_entries(const GraphDev& G, const u32* list, u32 cn
 #pragma unroll
             for (int h = 0; h < 2; ++h) push_vis(vis, q[h], old[h]);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) push_next(Fnext, q[h], old[h], foot, st);
+            for (int h = 0; h < 2; ++h) push_next(Fnext, q[h], old[h], foot, st, bmn);
 #pragma unroll
             for (int h = 0; h < 2; ++h) push_finish(q[h], cg, cs, nq, lq);
         }
@@ -446,7 +451,7 @@ __device__ inline void expand_entries(const GraphDev& G, const u32* list, u32 cn
 template <int W>
 __device__ __noinline__ void expand_heavy(const GraphDev& G, const HeavyEntry* H, u32 hn, u64* vis, u64* Fnext,
                                     u32* cg, u32* cs, u32 foot, WarpQueue& nq, WarpQueue& lq, u32 wid, u32 nw,
-                                    LocalStats& st) {
+                                    LocalStats& st, u32* bmn) {
     const u32 lane = threadIdx.x & 31;
     u32 base = 0;   // pieces in the batches before this one
     for (u32 h0 = 0; h0 < hn; h0 += 32) {
@@ -501,7 +506,7 @@ __device__ __noinline__ void expand_heavy(const GraphDev& G, const HeavyEntry* H
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh) push_vis(vis, q[hh], old[hh]);
 #pragma unroll
-            for (int hh = 0; hh < 2; ++hh) push_next(Fnext, q[hh], old[hh], foot, st);
+            for (int hh = 0; hh < 2; ++hh) push_next(Fnext, q[hh], old[hh], foot, st, bmn);
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh) push_finish(q[hh], cg, cs, nq, lq);
         }
@@ -520,11 +525,15 @@ __device__ __noinline__ void expand_heavy(const GraphDev& G, const HeavyEntry* H
 // thread, without atomics.  The frontier words themselves are cleared
 // afterwards (pull_retire), once no thread can still be reading them.
 constexpr u32 kPullSerial = 32;
+#ifndef BCM_PULL_UNROLL
+#define BCM_PULL_UNROLL 2
+#endif
+constexpr int kPullUnroll = BCM_PULL_UNROLL;   // in-neighbours per step of a thread's scan
 
 template <int W>
 __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32* s_alive32, u64* vis, u64* Fnext,
                                   u32* cg, u32* cs, u32 foot, WarpQueue& nq, WarpQueue& lq, u32* chunk_ctr,
-                                  LocalStats& st) {
+                                  LocalStats& st, const u32* bmc, u32* bmn) {
     const u32 lane = threadIdx.x & 31;
     u64 alive[W];
 #pragma unroll
@@ -556,16 +565,32 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
         }
         const bool coop = any && e - b > kPullSerial;
         if (any && !coop) {
+            // kPullUnroll in-neighbours per step: their col entries, then
+            // their frontier words, are loaded together (independent loads
+            // in flight), and the early stop is checked once per step
             u32 i = b;
-            for (; i < e; ++i) {
-                const u32 u = __ldg(&G.rcol[i]);
+            while (i < e) {
+                u32 u[kPullUnroll];
+#pragma unroll
+                for (int j = 0; j < kPullUnroll; ++j) u[j] = i + j < e ? __ldg(&G.rcol[i + j]) : 0xffffffffu;
+                // in-neighbours outside the current frontier have no frontier words
+#pragma unroll
+                for (int j = 0; j < kPullUnroll; ++j)
+                    if (u[j] != 0xffffffffu && !((__ldcg(&bmc[u[j] >> 5]) >> (u[j] & 31)) & 1u)) u[j] = 0xffffffffu;
                 bool done = true;
 #pragma unroll
                 for (int g = 0; g < W; ++g) {
-                    if (pend[g] & ~acc[g]) acc[g] |= __ldcg(&Fcur[ri(u * W + g)]);
+                    if (pend[g] & ~acc[g]) {
+                        u64 f = 0;
+#pragma unroll
+                        for (int j = 0; j < kPullUnroll; ++j)
+                            if (u[j] != 0xffffffffu) f |= __ldcg(&Fcur[ri(u[j] * W + g)]);
+                        acc[g] |= f;
+                    }
                     done = done && !(pend[g] & ~acc[g]);
                 }
-                if (done) { ++i; break; }
+                i = i + kPullUnroll < e ? i + kPullUnroll : e;
+                if (done) break;
             }
             st.arcwords += i - b;
         }
@@ -590,9 +615,11 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
                 for (int g = 0; g < W; ++g) f[g] = 0;
                 if (i + lane < ce) {
                     const u32 u = __ldg(&G.rcol[i + lane]);
+                    if ((__ldcg(&bmc[u >> 5]) >> (u & 31)) & 1u) {
 #pragma unroll
-                    for (int g = 0; g < W; ++g)
-                        if (cp[g] & ~ca[g]) f[g] = __ldcg(&Fcur[ri(u * W + g)]) & cp[g];
+                        for (int g = 0; g < W; ++g)
+                            if (cp[g] & ~ca[g]) f[g] = __ldcg(&Fcur[ri(u * W + g)]) & cp[g];
+                    }
                 }
                 bool done = true;
 #pragma unroll
@@ -628,6 +655,13 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
                     st.fwarcs += degp + foot;
                 }
             }
+        }
+        {   // the warp's 32 vertices share one bitmap word (x0 is a multiple of 32)
+            bool found = false;
+#pragma unroll
+            for (int g = 0; g < W; ++g) found = found || nb[g] != 0;
+            const u32 word = __ballot_sync(0xffffffffu, found);
+            if (lane == 0 && word) bmn[x0 >> 5] = word;
         }
 #pragma unroll
         for (int g = 0; g < W; ++g) {
@@ -759,6 +793,72 @@ __device__ __noinline__ void flush_completions(const WaveParams& p, const u32* c
     __syncthreads();
 }
 
+// ------------------------------------------------------------ prefilter
+// On a simple graph (sorted rows, no repeated arc, no self-loop) level 1 of
+// v's BFS is known without expanding it: Gamma_1 = N(v), so gamma_1 = deg(v),
+// n_1 = 1 + deg(v), f_1 = deg(v), and gamma~_2 (Table 1, with the footnote's
+// deg(u) - 1 on undirected graphs) = sum over u in N(v) of deg(u) - footnote.
+// One warp per source applies the stopping rule at levels 0 and 1, exactly as
+// a wave would, against the threshold the grid-wide waves left (no higher
+// than the one a later wave would read); the sources it cannot stop go to
+// `out` for the per-CTA waves.  Sources p.sources[*p.head .. p.n_end).
+__global__ void __launch_bounds__(256) k_prefilter(WaveParams p, u32* out, u32* out_n) {
+    __shared__ ThrCache s_thr;
+    __shared__ BlockStats s_bst;
+    __shared__ u32 s_begin;
+    const GraphDev& G = p.g;
+    if (threadIdx.x == 0) {
+        s_thr.valid = 0; s_thr.N = 0; s_thr.F = 1; s_thr.id = 0;
+        read_threshold(p.topk.thr, s_thr);
+        s_begin = vload(p.head);
+    }
+    bstat_init(s_bst);
+    __syncthreads();
+    LocalStats st;
+    const u32 lane = threadIdx.x & 31;
+    const size_t gw = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5;
+    const size_t gnw = ((size_t)gridDim.x * blockDim.x) >> 5;
+    for (size_t pos = s_begin + gw; pos < p.n_end; pos += gnw) {
+        const u32 v = __ldg(&p.sources[pos]);
+        const u32 b = __ldg(&G.rp[v]), deg = __ldg(&G.rp[v + 1]) - b;
+        bool cut = false;
+        if (s_thr.valid && deg == 0) {
+            // R(v) = {v}: complete with key (0, 1); it only goes on (to be
+            // merged by a wave) if it ranks before the k-th
+            if (!ranks_before(0, 1, v, s_thr.N, s_thr.F, s_thr.id)) {
+                cut = true;   // done: not a stop by the bound, a completion that cannot enter
+                if (lane == 0) bstat_add(s_bst, ST_COMPLETED, 1);
+            }
+        } else if (s_thr.valid) {
+            const u32 xlo = __ldg(&G.xlo[v]), xhi = __ldg(&G.xhi[v]);
+            cut = bfscut_stops(0, deg, 0, 1, xlo, xhi, v, s_thr);
+            if (!cut) {
+                u64 g2 = 0;
+                for (u32 i = lane; i < deg; i += 32) {
+                    const u32 u = __ldg(&G.col[b + i]);
+                    g2 += __ldg(&G.rp[u + 1]) - __ldg(&G.rp[u]) - p.footnote;
+                }
+                for (int o = 16; o; o >>= 1) g2 += __shfl_xor_sync(0xffffffffu, g2, o);
+                cut = bfscut_stops(deg, g2, 1, 1 + deg, xlo, xhi, v, s_thr);
+                if (cut && lane == 0) {   // level 0 was expanded
+                    st.mvis += deg;
+                    st.arcwords += deg;
+                }
+            }
+            if (cut && lane == 0) bstat_add(s_bst, ST_CUT, 1);
+        }
+        if (!cut && lane == 0) out[atomicAdd(out_n, 1u)] = v;
+    }
+    __syncthreads();
+    flush_stats(st, s_bst, p.stats);
+}
+
+int launch_prefilter(const WaveParams& p, uint32_t* out, uint32_t* out_n, cudaStream_t s) {
+    k_prefilter<<<152 * 8, 256, 0, s>>>(p, out, out_n);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 // --------------------------------------------------------- per-CTA waves
 template <int W, int THREADS>
 __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREADS) : 1) k_wave_cta(WaveParams p) {
@@ -786,6 +886,7 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
 
     const u32 tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const GraphDev& G = p.g;
+    const u32 n_end = p.n_end_dev ? vload(p.n_end_dev) : p.n_end;
     SlotPtrs S = slot_ptrs(p.slot_base + (size_t)blockIdx.x * p.slot_stride, G.n, W);
     LocalStats st;
     if (tid == 0) {
@@ -796,10 +897,14 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
     bstat_init(s_bst);
     __syncthreads();
 
-    for (;;) {
+    for (u32 waves_done = 0;; ++waves_done) {
         if (tid == 0) {
-            s_base = atomicAdd(p.head, (u32)L);
-            s_stop = (s_base >= p.n_end) || (vload(p.err) != 0);
+            if (p.max_cta_waves && waves_done >= p.max_cta_waves) {
+                s_stop = 1;
+            } else {
+                s_base = atomicAdd(p.head, (u32)L);
+                s_stop = (s_base >= n_end) || (vload(p.err) != 0);
+            }
         }
         __syncthreads();
         if (s_stop) break;
@@ -810,7 +915,7 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
             bool alive = false;
             s_cg[tid] = 0;
             s_cs[tid] = 0;
-            if (base + tid < p.n_end) {
+            if (base + tid < n_end) {
                 u32 v = __ldg(&p.sources[base + tid]);
                 u32 deg = __ldg(&G.rp[v + 1]) - __ldg(&G.rp[v]);
                 s_src[tid] = v; s_nd[tid] = 1; s_f[tid] = 0; s_gt[tid] = deg;
@@ -826,6 +931,10 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
             u32 m = __ballot_sync(0xffffffffu, alive);
             if (lane == 0) s_alive32[tid >> 5] = m;
         }
+        // the current k-th key before the wave's first completions are
+        // merged: sources of degree 0 rarely beat it, and a stale (empty)
+        // key would send every CTA through the top-k lock
+        if (tid == 0 && !p.exhaustive) read_threshold(p.topk.thr, s_thr);
         __syncthreads();
         flush_completions(p, s_cid, s_cf, s_cr, s_nc, s_thr, THREADS, s_stage, &s_go);
         __syncthreads();
@@ -854,11 +963,12 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
             for (int i = 0; i < 2 * W; ++i) any |= s_alive32[i];
             if (!any) break;
 
-            if (d > 0 && p.defer_words && s_ln[cur] >= p.defer_words) {
-                // a level too wide for one CTA is next: the live sources go
-                // to the grid-wide pass, which runs them again from the
-                // start; the wave ends here and its clear log resets every
-                // word it touched
+            if (d > 0 && p.defer_words && (s_ln[cur] >= p.defer_words || s_arcs[cur] >= 8ull * p.defer_words)) {
+                // a level too wide for one CTA is next (many frontier words,
+                // or few with very many out-arcs): the live sources go to the
+                // grid-wide pass, which runs them again from the start; the
+                // wave ends here and its clear log resets every word it
+                // touched
                 if (tid < L) {
                     const bool a = (s_alive32[tid >> 5] >> lane) & 1u;
                     const u32 m = __ballot_sync(0xffffffffu, a);
@@ -879,16 +989,16 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
                 WarpQueue lq{&s_stage[(2 * wid + 1) * QCAP], S.clog, &s_logn, QCAP, 0};
                 if (d == 0)
                     expand_sources<W>(G, s_src, s_alive32, s_pre, s_beg, L, S.vis, Fnext, s_cg, s_cs, p.footnote,
-                                      nq, lq, wid, NWARP, tid, THREADS, st);
+                                      nq, lq, wid, NWARP, tid, THREADS, st, nullptr);
                 else
                     expand_entries<W>(G, S.list[cur], s_ln[cur], S.F[cur], s_alive32, S.vis, Fnext, s_cg, s_cs,
-                                      p.footnote, nq, lq, &s_chunk, NWARP, Hc, st);
+                                      p.footnote, nq, lq, &s_chunk, NWARP, Hc, st, nullptr);
                 if (d > 0) {
                     __syncthreads();   // the heavy list is complete
                     const u32 hn = s_hn < kHeavyCapCta ? s_hn : kHeavyCapCta;
                     if (hn)
                         expand_heavy<W>(G, s_heavy, hn, S.vis, Fnext, s_cg, s_cs, p.footnote, nq, lq, wid, NWARP,
-                                        st);
+                                        st, nullptr);
                 }
                 nq.flush();
                 lq.flush();
@@ -991,6 +1101,8 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
     const u32 gw = blockIdx.x * NWARP + wid, gnw = gridDim.x * NWARP;
     const u32 n_end = p.n_end_dev ? vload(p.n_end_dev) : p.n_end;
     const HeavyList Hg{p.gheavy, p.gheavy_n, p.gheavy_cap};
+    // frontier bitmaps, one bit per vertex, by level parity
+    u32* const bm[2] = {p.gbm, p.gbm + p.nbw};
     if (tid == 0) { s_nc = 0; s_thr.valid = 0; s_thr.N = 0; s_thr.F = 1; s_thr.id = 0; }
     bstat_init(s_bst);
     bool ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err);
@@ -1068,7 +1180,7 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
                 if (d == 0) {
                     expand_sources<W>(G, s_src, s_alive32, s_pre, s_beg, L, S.vis, S.F[cur ^ 1], s_cg, s_cs,
                                       p.footnote, nq, lq, gw, gnw, blockIdx.x * THREADS + tid, gridDim.x * THREADS,
-                                      st);
+                                      st, bm[cur ^ 1]);
                 } else {
                     const u32 cnt = vload(&p.glist_n[cur]);
                     wave_entries += cnt;
@@ -1078,10 +1190,10 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
                     pulled = p.pull_div && vload(&p.garc[cur]) >= ((u64)G.n * W + p.pull_div - 1) / p.pull_div;
                     if (pulled)
                         pull_level<W>(G, S.F[cur], s_alive32, S.vis, S.F[cur ^ 1], s_cg, s_cs, p.footnote, nq, lq,
-                                      &p.gchunk[cur], st);
+                                      &p.gchunk[cur], st, bm[cur], bm[cur ^ 1]);
                     else
                         expand_entries<W>(G, S.list[cur], cnt, S.F[cur], s_alive32, S.vis, S.F[cur ^ 1], s_cg,
-                                          s_cs, p.footnote, nq, lq, &p.gchunk[cur], gnw, Hg, st);
+                                          s_cs, p.footnote, nq, lq, &p.gchunk[cur], gnw, Hg, st, bm[cur ^ 1]);
                 }
                 nq.flush();
                 lq.flush();
@@ -1104,7 +1216,7 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
                         WarpQueue nq{&s_stage[(2 * wid) * QCAP], S.list[cur ^ 1], &p.glist_n[cur ^ 1], QCAP, 0};
                         WarpQueue lq{&s_stage[(2 * wid + 1) * QCAP], S.clog, p.glog_n, QCAP, 0};
                         expand_heavy<W>(G, p.gheavy, hn, S.vis, S.F[cur ^ 1], s_cg, s_cs, p.footnote, nq, lq, gw,
-                                        gnw, st);
+                                        gnw, st, bm[cur ^ 1]);
                         nq.flush();
                         lq.flush();
                         flush_fwarcs(st, &p.garc[cur ^ 1]);
@@ -1124,6 +1236,8 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
                 pulled = false;
                 __syncthreads();
             }
+            // the consumed level's bitmap, for reuse two levels on
+            for (u32 i = blockIdx.x * THREADS + tid; i < p.nbw; i += gridDim.x * THREADS) bm[cur][i] = 0;
             if (tid < L) {
                 bool a = (s_alive32[tid >> 5] >> lane) & 1u;
                 if (a) {
@@ -1176,6 +1290,7 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
             u32 w = __ldcg(&S.clog[i]);
             clear_record(S.vis, w);
         }
+        for (u32 i = blockIdx.x * THREADS + tid; i < 2 * p.nbw; i += gridDim.x * THREADS) p.gbm[i] = 0;
         if (leader && tid == 0) bstat_add(s_bst, ST_CLEARED, nlog);
         if (!(ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err))) break;
         if (leader && tid == 0) trace_record(p, TR_GRID_WAVE, wave, d, nlog, wave_entries, global_ns());

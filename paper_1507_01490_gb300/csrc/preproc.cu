@@ -29,6 +29,30 @@ __global__ void k_validate(const uint64_t* rp, const uint32_t* col, uint32_t n, 
         if (col[e] >= n) atomicOr(err, DEV_ERR_INVALID_CSR);
 }
 
+// *not_simple |= 1 if some row is not strictly increasing or holds its own
+// vertex (a repeated arc or a self-loop).  One warp per row.
+__global__ void k_simple_check(const uint32_t* rp, const uint32_t* col, uint32_t n, int* not_simple) {
+    const uint32_t lane = threadIdx.x & 31;
+    for (size_t u = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5; u < n;
+         u += ((size_t)gridDim.x * blockDim.x) >> 5) {
+        const uint32_t b = rp[u], e = rp[u + 1];
+        bool bad = false;
+        for (uint32_t i = b + lane; i < e; i += 32)
+            bad = bad || col[i] == u || (i > b && col[i - 1] >= col[i]);
+        if (__any_sync(0xffffffffu, bad)) {
+            if (lane == 0) atomicOr(not_simple, 1);
+            return;
+        }
+    }
+}
+
+int launch_simple_check(const uint32_t* rp32, const uint32_t* col, uint32_t n, int* not_simple, cudaStream_t s) {
+    if (n == 0) return 0;
+    k_simple_check<<<blocks_for((size_t)n * 32, 256), 256, 0, s>>>(rp32, col, n, not_simple);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int launch_validate(const uint64_t* rp64, const uint32_t* col, uint32_t n, uint64_t m, int* err,
                     cudaStream_t s) {
     k_validate<<<blocks_for(m > n ? m : n, 256), 256, 0, s>>>(rp64, col, n, m, err);

@@ -37,6 +37,28 @@ static inline unsigned grid_for(size_t work, int threads = 256) {
     for (size_t u = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5; u < (n); \
          u += ((size_t)gridDim.x * blockDim.x) >> 5)
 
+// Items of a frontier (vertices, or SCCs of the DAG) with more than
+// kHeavyEdges arcs: each is taken by the whole grid in a second kernel
+// instead of one warp.  A full list leaves the item with its warp.
+constexpr uint32_t kHeavyEdges = 2048;
+constexpr uint32_t kSccHeavyCap = 256;
+struct SccHeavy {
+    uint32_t n;
+    uint32_t pad;
+    uint32_t item[kSccHeavyCap];
+    unsigned long long acc[kSccHeavyCap][3];   // k_dp_eval_heavy: max alpha, sum omega, sum Wm
+};
+
+__device__ __forceinline__ bool heavy_claim(SccHeavy* H, uint32_t c, uint32_t deg) {
+    if (deg <= kHeavyEdges) return false;
+    uint32_t slot = 0;
+    if ((threadIdx.x & 31) == 0) slot = atomicAdd(&H->n, 1u);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    if (slot >= kSccHeavyCap) return false;
+    if ((threadIdx.x & 31) == 0) H->item[slot] = c;
+    return true;
+}
+
 __global__ void k_count_in(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t* indeg) {
     WARP_PER_ITEM(u, n) {
         for (uint32_t e = rp[u] + lane_; e < rp[u + 1]; e += 32) atomicAdd(&indeg[col[e]], 1u);
@@ -94,24 +116,43 @@ __global__ void k_seed_mark(uint32_t v, uint32_t* mark, uint32_t* list, uint32_t
 }
 
 // one BFS level over unassigned vertices; same_color restricts to color[w] == color[u]
+__device__ __forceinline__ void reach_arc(const uint32_t* col, uint32_t e, bool valid, uint32_t cu, uint32_t* next,
+                                          uint32_t* ncnt, uint32_t* mark, const uint32_t* scc, const uint32_t* color,
+                                          int same_color) {
+    bool app = false;
+    uint32_t w = 0;
+    if (valid) {
+        w = col[e];
+        if (scc[w] == UNSET && (!same_color || color[w] == cu) && vload(&mark[w]) == 0 &&
+            atomicExch(&mark[w], 1u) == 0)
+            app = true;
+    }
+    warp_append(app, w, next, ncnt);
+}
+
 __global__ void k_reach(const uint32_t* rp, const uint32_t* col, const uint32_t* front, const uint32_t* fcnt,
                         uint32_t* next, uint32_t* ncnt, uint32_t* mark, const uint32_t* scc, const uint32_t* color,
-                        int same_color) {
+                        int same_color, SccHeavy* H) {
     const uint32_t cnt = *fcnt;
     WARP_PER_ITEM(i, cnt) {
         uint32_t u = front[i];
+        if (H && heavy_claim(H, u, rp[u + 1] - rp[u])) continue;
         uint32_t cu = same_color ? color[u] : 0;
-        for (uint32_t e0 = rp[u]; e0 < rp[u + 1]; e0 += 32) {
-            uint32_t e = e0 + lane_;
-            bool app = false;
-            uint32_t w = 0;
-            if (e < rp[u + 1]) {
-                w = col[e];
-                if (scc[w] == UNSET && (!same_color || color[w] == cu) && vload(&mark[w]) == 0 &&
-                    atomicExch(&mark[w], 1u) == 0)
-                    app = true;
-            }
-            warp_append(app, w, next, ncnt);
+        for (uint32_t e0 = rp[u]; e0 < rp[u + 1]; e0 += 32)
+            reach_arc(col, e0 + lane_, e0 + lane_ < rp[u + 1], cu, next, ncnt, mark, scc, color, same_color);
+    }
+}
+
+__global__ void k_reach_heavy(const uint32_t* rp, const uint32_t* col, uint32_t* next, uint32_t* ncnt,
+                              uint32_t* mark, const uint32_t* scc, const uint32_t* color, int same_color,
+                              const SccHeavy* H) {
+    const uint32_t hn = H->n < kSccHeavyCap ? H->n : kSccHeavyCap;
+    for (uint32_t h = 0; h < hn; ++h) {
+        const uint32_t u = H->item[h], b = rp[u], e = rp[u + 1];
+        const uint32_t cu = same_color ? color[u] : 0;
+        WARP_PER_ITEM(j, ((size_t)(e - b) + 31) / 32) {
+            const size_t a = b + j * 32 + lane_;
+            reach_arc(col, (uint32_t)a, a < e, cu, next, ncnt, mark, scc, color, same_color);
         }
     }
 }
@@ -246,58 +287,128 @@ struct Refine {
     uint32_t* Wm;
 };
 
+// The programme's value of SCC c from its successors' max alpha and sums.
+__device__ void dp_finish(uint32_t c, uint32_t amax, unsigned long long osum, unsigned long long msum,
+                          const uint32_t* wsz, uint32_t* A, uint32_t* Om, uint32_t n, const Refine& rf) {
+    const bool refine = rf.big != 0xffffffffu;
+    if (refine && c == rf.big) {
+        A[c] = *rf.R;
+        Om[c] = *rf.R;
+        rf.Wm[c] = 0;
+        return;
+    }
+    A[c] = wsz[c] + amax;
+    unsigned long long o = wsz[c] + (osum > n ? n : osum);
+    o = o > n ? n : o;
+    if (refine) {
+        unsigned long long wm = rf.desc[c] ? 0 : wsz[c] + (msum > n ? n : msum);
+        wm = wm > n ? n : wm;
+        rf.Wm[c] = (uint32_t)wm;
+        if (rf.anc[c] && wm + *rf.R < o) o = wm + *rf.R;
+    }
+    Om[c] = (uint32_t)o;
+}
+
+// One warp per SCC of the level: lanes take its successors 32 at a time
+// and the warp reduces max alpha and the sums (exact in 64 bits: at most
+// 2^32 terms below 2^30; held at n at the end, as the programme's running
+// minimum with n gives the same value for non-negative terms).  An SCC with
+// more than kHeavyEdges successors goes to the heavy list (k_dp_eval_heavy).
 __global__ void k_dp_eval(const uint32_t* front, const uint32_t* fcnt, const uint32_t* drp, const uint32_t* ddst,
-                          const uint32_t* wsz, uint32_t* A, uint32_t* Om, uint32_t n, Refine rf) {
+                          const uint32_t* wsz, uint32_t* A, uint32_t* Om, uint32_t n, Refine rf, SccHeavy* H) {
     const uint32_t cnt = *fcnt;
     const bool refine = rf.big != 0xffffffffu;
-    GRID_STRIDE(i, cnt) {
-        uint32_t c = front[i];
+    WARP_PER_ITEM(i, cnt) {
+        const uint32_t c = front[i];
+        const uint32_t b = drp[c], e = drp[c + 1];
+        if (heavy_claim(H, c, e - b)) continue;
         uint32_t amax = 0;
         unsigned long long osum = 0, msum = 0;
-        for (uint32_t e = drp[c]; e < drp[c + 1]; ++e) {
-            uint32_t d = ddst[e];
-            uint32_t a = vload(&A[d]);
+        for (uint32_t k = b + lane_; k < e; k += 32) {
+            const uint32_t d = ddst[k];
+            const uint32_t a = A[d];
             amax = a > amax ? a : amax;
-            osum += vload(&Om[d]);
-            if (osum > n) osum = n;
-            if (refine && !rf.desc[d]) {
-                msum += vload(&rf.Wm[d]);
-                if (msum > n) msum = n;
-            }
+            osum += Om[d];
+            if (refine && !rf.desc[d]) msum += rf.Wm[d];
         }
-        if (refine && c == rf.big) {
-            A[c] = *rf.R;
-            Om[c] = *rf.R;
-            rf.Wm[c] = 0;
-            continue;
+        for (int o = 16; o; o >>= 1) {
+            const uint32_t t = __shfl_xor_sync(0xffffffffu, amax, o);
+            amax = t > amax ? t : amax;
+            osum += __shfl_xor_sync(0xffffffffu, osum, o);
+            msum += __shfl_xor_sync(0xffffffffu, msum, o);
         }
-        A[c] = wsz[c] + amax;
-        unsigned long long o = wsz[c] + osum;
-        o = o > n ? n : o;
-        if (refine) {
-            unsigned long long wm = rf.desc[c] ? 0 : wsz[c] + msum;
-            wm = wm > n ? n : wm;
-            rf.Wm[c] = (uint32_t)wm;
-            if (rf.anc[c] && wm + *rf.R < o) o = wm + *rf.R;
-        }
-        Om[c] = (uint32_t)o;
+        if (lane_ == 0) dp_finish(c, amax, osum, msum, wsz, A, Om, n, rf);
     }
 }
 
+// the heavy SCCs' successors over the whole grid, into per-SCC accumulators
+__global__ void k_dp_eval_heavy(const uint32_t* drp, const uint32_t* ddst, const uint32_t* A, const uint32_t* Om,
+                                Refine rf, SccHeavy* H) {
+    const uint32_t hn = H->n < kSccHeavyCap ? H->n : kSccHeavyCap;
+    const bool refine = rf.big != 0xffffffffu;
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t h = 0; h < hn; ++h) {
+        const uint32_t c = H->item[h], b = drp[c], e = drp[c + 1];
+        uint32_t amax = 0;
+        unsigned long long osum = 0, msum = 0;
+        GRID_STRIDE(k, (size_t)(e - b)) {
+            const uint32_t d = ddst[b + k];
+            const uint32_t a = A[d];
+            amax = a > amax ? a : amax;
+            osum += Om[d];
+            if (refine && !rf.desc[d]) msum += rf.Wm[d];
+        }
+        for (int o = 16; o; o >>= 1) {
+            const uint32_t t = __shfl_xor_sync(0xffffffffu, amax, o);
+            amax = t > amax ? t : amax;
+            osum += __shfl_xor_sync(0xffffffffu, osum, o);
+            msum += __shfl_xor_sync(0xffffffffu, msum, o);
+        }
+        if (lane == 0) {
+            atomicMax(&H->acc[h][0], (unsigned long long)amax);
+            atomicAdd(&H->acc[h][1], osum);
+            atomicAdd(&H->acc[h][2], msum);
+        }
+    }
+}
+
+__global__ void k_dp_heavy_finish(const uint32_t* wsz, uint32_t* A, uint32_t* Om, uint32_t n, Refine rf,
+                                  const SccHeavy* H) {
+    const uint32_t hn = H->n < kSccHeavyCap ? H->n : kSccHeavyCap;
+    GRID_STRIDE(h, hn)
+    dp_finish(H->item[h], (uint32_t)H->acc[h][0], H->acc[h][1], H->acc[h][2], wsz, A, Om, n, rf);
+}
+
+__device__ __forceinline__ void dp_release_arc(const uint32_t* pred, uint32_t e, bool valid, uint32_t* outcnt,
+                                               uint32_t* next, uint32_t* ncnt) {
+    bool ready = false;
+    uint32_t p = 0;
+    if (valid) {
+        p = pred[e];
+        ready = atomicSub(&outcnt[p], 1u) == 1u;
+    }
+    warp_append(ready, p, next, ncnt);
+}
+
 __global__ void k_dp_release(const uint32_t* front, const uint32_t* fcnt, const uint32_t* prp, const uint32_t* pred,
-                             uint32_t* outcnt, uint32_t* next, uint32_t* ncnt) {
+                             uint32_t* outcnt, uint32_t* next, uint32_t* ncnt, SccHeavy* H) {
     const uint32_t cnt = *fcnt;
     WARP_PER_ITEM(i, cnt) {
         uint32_t c = front[i];
-        for (uint32_t e0 = prp[c]; e0 < prp[c + 1]; e0 += 32) {
-            uint32_t e = e0 + lane_;
-            bool ready = false;
-            uint32_t p = 0;
-            if (e < prp[c + 1]) {
-                p = pred[e];
-                ready = atomicSub(&outcnt[p], 1u) == 1u;
-            }
-            warp_append(ready, p, next, ncnt);
+        if (heavy_claim(H, c, prp[c + 1] - prp[c])) continue;
+        for (uint32_t e0 = prp[c]; e0 < prp[c + 1]; e0 += 32)
+            dp_release_arc(pred, e0 + lane_, e0 + lane_ < prp[c + 1], outcnt, next, ncnt);
+    }
+}
+
+__global__ void k_dp_release_heavy(const uint32_t* prp, const uint32_t* pred, uint32_t* outcnt, uint32_t* next,
+                                   uint32_t* ncnt, const SccHeavy* H) {
+    const uint32_t hn = H->n < kSccHeavyCap ? H->n : kSccHeavyCap;
+    for (uint32_t h = 0; h < hn; ++h) {
+        const uint32_t c = H->item[h], b = prp[c], e = prp[c + 1];
+        WARP_PER_ITEM(j, ((size_t)(e - b) + 31) / 32) {
+            const size_t a = b + j * 32 + lane_;
+            dp_release_arc(pred, (uint32_t)a, a < e, outcnt, next, ncnt);
         }
     }
 }
@@ -325,21 +436,39 @@ __global__ void k_mark_seed(const unsigned long long* best, uint32_t* mark, uint
     *big = c;
 }
 
-// one BFS level over a DAG given as CSR (successors or predecessors)
+// one BFS level over a DAG given as CSR (successors or predecessors); an
+// SCC with more than kHeavyEdges arcs goes to the heavy list, whose arcs
+// k_dag_reach_heavy spreads over the whole grid
+__device__ __forceinline__ void dag_reach_arc(const uint32_t* adj, uint32_t e, bool valid, uint32_t* next,
+                                              uint32_t* ncnt, uint32_t* mark) {
+    bool app = false;
+    uint32_t d = 0;
+    if (valid) {
+        d = adj[e];
+        app = vload(&mark[d]) == 0 && atomicExch(&mark[d], 1u) == 0;
+    }
+    warp_append(app, d, next, ncnt);
+}
+
 __global__ void k_dag_reach(const uint32_t* ptr, const uint32_t* adj, const uint32_t* front, const uint32_t* fcnt,
-                            uint32_t* next, uint32_t* ncnt, uint32_t* mark) {
+                            uint32_t* next, uint32_t* ncnt, uint32_t* mark, SccHeavy* H) {
     const uint32_t cnt = *fcnt;
     WARP_PER_ITEM(i, cnt) {
         uint32_t c = front[i];
-        for (uint32_t e0 = ptr[c]; e0 < ptr[c + 1]; e0 += 32) {
-            uint32_t e = e0 + lane_;
-            bool app = false;
-            uint32_t d = 0;
-            if (e < ptr[c + 1]) {
-                d = adj[e];
-                app = vload(&mark[d]) == 0 && atomicExch(&mark[d], 1u) == 0;
-            }
-            warp_append(app, d, next, ncnt);
+        if (heavy_claim(H, c, ptr[c + 1] - ptr[c])) continue;
+        for (uint32_t e0 = ptr[c]; e0 < ptr[c + 1]; e0 += 32)
+            dag_reach_arc(adj, e0 + lane_, e0 + lane_ < ptr[c + 1], next, ncnt, mark);
+    }
+}
+
+__global__ void k_dag_reach_heavy(const uint32_t* ptr, const uint32_t* adj, uint32_t* next, uint32_t* ncnt,
+                                  uint32_t* mark, const SccHeavy* H) {
+    const uint32_t hn = H->n < kSccHeavyCap ? H->n : kSccHeavyCap;
+    for (uint32_t h = 0; h < hn; ++h) {
+        const uint32_t c = H->item[h], b = ptr[c], e = ptr[c + 1];
+        WARP_PER_ITEM(j, ((size_t)(e - b) + 31) / 32) {
+            const size_t a = b + j * 32 + lane_;
+            dag_reach_arc(adj, (uint32_t)a, a < e, next, ncnt, mark);
         }
     }
 }
@@ -371,6 +500,7 @@ size_t scc_scratch_bytes(uint32_t n, uint64_t m) {
     s += al(scan_scratch_bytes((m > n ? m : n) + 1));
     s += al(radix_scratch_bytes(m ? m : 1));
     s += nb * 5 + 4096;           // refinement: desc, anc, Wm, two queues
+    s += al(sizeof(SccHeavy));
     return s;
 }
 
@@ -436,6 +566,8 @@ int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, const uint32_t* r
     uint32_t* minv = (uint32_t*)B.take(((size_t)n + 1) * 4);
     uint32_t* flags = (uint32_t*)B.take(((size_t)(m > n ? m : n) + 1) * 4);
     uint32_t* cnts = (uint32_t*)B.take(256);     // [0] changed, [1],[2] list counts, [3] total, [4] remaining
+    SccHeavy* heavy = (SccHeavy*)B.take(sizeof(SccHeavy));
+    if (!heavy) return -1;
     unsigned long long* best = (unsigned long long*)B.take(64);
     void* scan_scr = B.take(scan_scratch_bytes((m > n ? m : n) + 1));
     if (!cursor || !drp_buf || !pred_buf || !color || !fw || !bw || !L0 || !L1 || !minv || !flags || !cnts ||
@@ -468,8 +600,11 @@ int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, const uint32_t* r
             uint32_t *cur = L0, *nxt = L1, *cc = &cnts[1], *nc = &cnts[2];
             for (;;) {
                 cudaMemsetAsync(nc, 0, 4, s);
+                cudaMemsetAsync(&heavy->n, 0, 4, s);
                 LAUNCH(k_reach<<<gw, 256, 0, s>>>(dir ? rrp : rp, dir ? rcol : col, cur, cc, nxt, nc, mark, sccv,
-                                                  color, 0));
+                                                  color, 0, heavy));
+                LAUNCH(k_reach_heavy<<<152 * 8, 256, 0, s>>>(dir ? rrp : rp, dir ? rcol : col, nxt, nc, mark, sccv,
+                                                             color, 0, heavy));
                 if (read_u32(nc, &h, s)) return -1;
                 if (!h) break;
                 uint32_t* t = cur; cur = nxt; nxt = t;
@@ -503,7 +638,9 @@ int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, const uint32_t* r
         uint32_t *cur = L0, *nxt = L1, *cc = &cnts[1], *nc = &cnts[2];
         for (;;) {
             cudaMemsetAsync(nc, 0, 4, s);
-            LAUNCH(k_reach<<<gw, 256, 0, s>>>(rrp, rcol, cur, cc, nxt, nc, bw, sccv, color, 1));
+            cudaMemsetAsync(&heavy->n, 0, 4, s);
+            LAUNCH(k_reach<<<gw, 256, 0, s>>>(rrp, rcol, cur, cc, nxt, nc, bw, sccv, color, 1, heavy));
+            LAUNCH(k_reach_heavy<<<152 * 8, 256, 0, s>>>(rrp, rcol, nxt, nc, bw, sccv, color, 1, heavy));
             if (read_u32(nc, &h, s)) return -1;
             if (!h) break;
             uint32_t* t = cur; cur = nxt; nxt = t;
@@ -590,8 +727,11 @@ int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, const uint32_t* r
             uint32_t *cur = Q0, *nxt = Q1, *cc = &cnts[1], *nc2 = &cnts[2];
             for (;;) {
                 cudaMemsetAsync(nc2, 0, 4, s);
+                cudaMemsetAsync(&heavy->n, 0, 4, s);
                 LAUNCH(k_dag_reach<<<grid_for((size_t)nscc * 32), 256, 0, s>>>(dir ? prp : drp, dir ? pred : ddst,
-                                                                               cur, cc, nxt, nc2, mark));
+                                                                               cur, cc, nxt, nc2, mark, heavy));
+                LAUNCH(k_dag_reach_heavy<<<152 * 8, 256, 0, s>>>(dir ? prp : drp, dir ? pred : ddst, nxt, nc2, mark,
+                                                                  heavy));
                 if (read_u32(nc2, &h, s)) return -1;
                 if (!h) break;
                 uint32_t* t = cur; cur = nxt; nxt = t;
@@ -622,9 +762,14 @@ int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, const uint32_t* r
     uint32_t done = 0;
     while (fcount) {
         done += fcount;
-        LAUNCH(k_dp_eval<<<grid_for(fcount), 256, 0, s>>>(cur, cc, drp, ddst, wsz, A, Om, n, rf));
+        cudaMemsetAsync(heavy, 0, sizeof(SccHeavy), s);
+        LAUNCH(k_dp_eval<<<grid_for((size_t)fcount * 32), 256, 0, s>>>(cur, cc, drp, ddst, wsz, A, Om, n, rf, heavy));
+        LAUNCH(k_dp_eval_heavy<<<152 * 8, 256, 0, s>>>(drp, ddst, A, Om, rf, heavy));
+        LAUNCH(k_dp_heavy_finish<<<1, 256, 0, s>>>(wsz, A, Om, n, rf, heavy));
         cudaMemsetAsync(nc, 0, 4, s);
-        LAUNCH(k_dp_release<<<grid_for((size_t)fcount * 32), 256, 0, s>>>(cur, cc, prp, pred, outcnt, nxt, nc));
+        cudaMemsetAsync(&heavy->n, 0, 4, s);
+        LAUNCH(k_dp_release<<<grid_for((size_t)fcount * 32), 256, 0, s>>>(cur, cc, prp, pred, outcnt, nxt, nc, heavy));
+        LAUNCH(k_dp_release_heavy<<<152 * 8, 256, 0, s>>>(prp, pred, outcnt, nxt, nc, heavy));
         if (read_u32(nc, &fcount, s)) return -1;
         uint32_t* t = cur; cur = nxt; nxt = t;
         uint32_t* tc = cc; cc = nc; nc = tc;

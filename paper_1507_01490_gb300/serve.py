@@ -64,7 +64,12 @@ class Result:
 
 
 class Backend:
-    """What the scheduler needs from the device side."""
+    """What the scheduler needs from the device side.  `held` is the ledger of
+    graphs that hold a run workspace (graph -> bytes, least recently used
+    first); it belongs to the backend, so it stays true across schedulers."""
+
+    def __init__(self):
+        self.held: OrderedDict[int, int] = OrderedDict()
 
     def footprint(self, gid: int) -> int:          # workspace bytes of a run on graph gid
         raise NotImplementedError
@@ -94,7 +99,7 @@ class Scheduler:
         self.sleep = sleep
         self.idle_sleep = idle_sleep
         self.inflight: dict[int, tuple[Request, float]] = {}   # graph -> (request, admitted)
-        self.held: OrderedDict[int, int] = OrderedDict()       # graph -> workspace bytes it holds (LRU order)
+        self.held = backend.held                                # graph -> workspace bytes it holds (LRU order)
         self.peak_inflight = 0
         self.peak_held = 0
         self.trims = 0
@@ -117,7 +122,7 @@ class Scheduler:
             if g in self.inflight:
                 continue
             self.be.trim(g)
-            del self.held[g]
+            self.held.pop(g, None)
             self.trims += 1
         return self.held_bytes() + need <= self.budget
 
@@ -246,13 +251,19 @@ class GpuBackend(Backend):
     """Graphs resident on the device, one CUDA stream and one set of pinned
     output buffers per graph."""
 
+    # per-CTA blocks of a served run: runs share the GPU, so one run gains
+    # little from every SM's worth of CTAs, while each CTA holds a wave slot
+    # of 44 bytes per vertex (about 27 GB for 304 CTAs at n = 2e6)
+    SERVE_BLOCKS = 64
+
     def __init__(self, graphs, options=None, kmax: int = 1024, trace: bool = False):
         import torch
 
         from . import bcm
+        super().__init__()
         self.bcm = bcm
         bcm.load()
-        self.opts = options if options is not None else bcm.make_options()
+        self.opts = options if options is not None else bcm.make_options(blocks=self.SERVE_BLOCKS)
         # with trace, every run records its kernels' time stamps and collect()
         # reports the span of device time the run's waves occupied
         self.trace = trace
@@ -305,12 +316,22 @@ class GpuBackend(Backend):
 
     def trim(self, gid):
         self.bcm.bcm_graph_trim(self.handles[gid].h)
+        self.held.pop(gid, None)
+
+    def trim_all(self):
+        for gid in list(self.held.keys()):
+            self.trim(gid)
 
     def alone(self, gid, k):
-        """The same request run by itself, synchronously (no trace)."""
+        """The same request run by itself, synchronously (no trace); its
+        workspace is given back afterwards unless the graph already held one."""
         kw = _opts_kw(self.opts)
         kw["flags"] &= ~self.bcm.BCM_TRACE
-        return self.handles[gid].topk(k, **kw)
+        had = gid in self.held
+        res = self.handles[gid].topk(k, **kw)
+        if not had:
+            self.bcm.bcm_graph_trim(self.handles[gid].h)
+        return res
 
     def close(self):
         for h in self.handles:

@@ -134,6 +134,30 @@ def test_deferred_waves_rerun_exactly(B, gen, orc):
                 assert np.array_equal(ids, exp) and st["deferred"] == 0
 
 
+def test_prefilter_is_exact(B, gen, orc):
+    """The level-0/1 prefilter (simple graphs, after grid-wide waves) stops
+    sources from degrees alone; the top-k is the oracle's with or without
+    it, and it cuts the sources the waves would have.  A graph with
+    self-loops and repeated arcs is not simple: the prefilter stays off."""
+    graphs = undirected_graphs(gen)[::3] + [gen.chung_lu(1 << 14, 10.0, 2.3, seed=9), gen.rmat(12, 8, seed=4),
+                                            gen.gnp(400, 0.01, seed=8, directed=True),
+                                            gen.with_self_loops_and_repeats(gen.ba(300, 3, seed=2), seed=3)]
+    for g in graphs:
+        f, r = orc.farness_all(g)
+        with B.BcmGraph.from_graph(g) as h:
+            for k in (1, 10, 50):
+                exp = orc.topk(f, r, k)
+                for hw in (1, 64):                # grid-wide waves run, then the prefilter
+                    a = h.topk(k, heavy_words=hw)
+                    b = h.topk(k, heavy_words=hw, flags=B.BCM_NO_PREFILTER)
+                    for ids, gf, gr, st in (a, b):
+                        assert np.array_equal(ids, exp) and np.array_equal(gf, f[exp]) and \
+                            np.array_equal(gr, r[exp]), (g.name, k, hw)
+                    # every source ends once: completed or stopped (deferred ones are rerun)
+                    for st in (a[3], b[3]):
+                        assert st["completed"] + st["cut"] == g.n, (g.name, k, hw, st["completed"], st["cut"])
+
+
 def test_plain_equals_oracle_bcm(B, gen, orc):
     """One source per launch follows the oracle's Algorithm 1 step for step:
     same top-k and the same arcs scanned, completions and cuts."""

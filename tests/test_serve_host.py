@@ -14,12 +14,13 @@ class FakeBackend(serve.Backend):
     function of (graph, k) only."""
 
     def __init__(self, sizes, durations, sched_ref):
+        super().__init__()
         self.sizes = sizes
         self.dur = durations
         self.t = 0.0
         self.end = {}
         self.k = {}
-        self.held = set()
+        self.alloc = set()          # graphs holding device memory, as the fake device sees them
         self.sched = sched_ref
         self.log = []
 
@@ -37,8 +38,8 @@ class FakeBackend(serve.Backend):
         s = self.sched[0]
         assert gid not in self.end, "two runs on one graph"
         assert len(self.end) < s.max_inflight
-        self.held.add(gid)
-        assert sum(self.sizes[g] for g in self.held) <= s.budget
+        self.alloc.add(gid)
+        assert sum(self.sizes[g] for g in self.alloc) <= s.budget
         self.end[gid] = self.t + self.dur(gid, k)
         self.k[gid] = k
         self.log.append(("start", gid, self.t))
@@ -54,7 +55,8 @@ class FakeBackend(serve.Backend):
 
     def trim(self, gid):
         assert gid not in self.end, "trimmed a busy graph"
-        self.held.discard(gid)
+        self.alloc.discard(gid)
+        self.held.pop(gid, None)
         self.log.append(("trim", gid, self.t))
 
 
@@ -114,6 +116,20 @@ def test_request_waits_for_memory_not_for_order():
     reqs = [serve.Request(0, 0, 1, 0.0), serve.Request(1, 1, 1, 0.001), serve.Request(2, 2, 1, 0.002)]
     s, be, res = _run(reqs, sizes, lambda g, k: 0.1 if g == 0 else 0.01, max_inflight=4, hbm_budget=100)
     assert res[2].admitted < res[0].done <= res[1].admitted + 1e-9
+
+
+def test_ledger_survives_across_schedulers():
+    # graphs keep their workspace after a run; a second scheduler on the same
+    # backend sees them and trims to stay in budget
+    sizes = [40, 40, 40]
+    ref = [None]
+    be = FakeBackend(sizes, lambda g, k: 0.001, ref)
+    for gids in ([0, 1], [2, 0]):
+        s = serve.Scheduler(be, clock=be.clock, sleep=be.sleep, max_inflight=1, hbm_budget=100)
+        ref[0] = s
+        s.run([serve.Request(i, g, 1, 0.0) for i, g in enumerate(gids)])
+        assert sum(be.held.values()) <= 100 and sum(sizes[g] for g in be.alloc) <= 100
+    assert [g for kind, g, t in be.log if kind == "trim"] == [0, 1]   # LRU: 0 before 2 runs, then 1 before 0 does
 
 
 def test_oversized_request_is_an_error():
