@@ -207,13 +207,13 @@ def run_serve(args, rank, world):
     torch.cuda.set_device(0)
     import __graft_entry__
     __graft_entry__.build()
-    from paper_1507_01490_gb300 import serve
+    from paper_1507_01490_gb300 import bcm as B, serve
     t = time.perf_counter()
     specs = serve.mix_specs(args.serve_graphs)
     graphs = [serve.build_graph(sp) for sp in specs]
     t_gen = time.perf_counter() - t
     t = time.perf_counter()
-    be = serve.GpuBackend(graphs)
+    be = serve.GpuBackend(graphs, options=B.make_options(blocks=args.serve_blocks))
     torch.cuda.synchronize()
     t_load = time.perf_counter() - t
     csr_bytes = int(sum(g.row_ptr.nbytes // 2 + g.col.nbytes for g in graphs))
@@ -269,6 +269,7 @@ def run_serve(args, rank, world):
                                "graph uniform, k uniform in {1,10,100}, Poisson arrivals (seed 5)"
                                % (len(graphs), args.serve_requests),
                    "max_inflight": args.serve_inflight, "hbm_budget_gb": args.serve_budget_gb,
+                   "cta_blocks": args.serve_blocks or "library default",
                    "graphs_resident_bytes": csr_bytes, "vertices": int(sum(g.n for g in graphs)),
                    "arcs": int(sum(g.m for g in graphs))},
         "capacity_rps": capacity, "capacity_latency_ms": serve.summarize(cap_res, cap_span)["latency_ms"],
@@ -278,6 +279,83 @@ def run_serve(args, rank, world):
         "setup_s": {"generate": t_gen, "upload_and_preprocess": t_load},
     }
     be.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ batches
+def run_batch(args, rank, world):
+    """Many small graphs: one synchronous bcm_topk per graph against one
+    replay of their runs recorded as a CUDA graph (bcm_batch_*)."""
+    if rank != 0:
+        return 0
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1507_01490_gb300 import bcm as B, serve
+    specs = [sp for sp in serve.mix_specs(args.batch_graphs * 4, n_hi=args.batch_max_n, seed_base=3000)
+             if (sp[1] if sp[0] == "ba" else 1 << sp[1]) <= args.batch_max_n][:args.batch_graphs]
+    graphs = [serve.build_graph(sp) for sp in specs]
+    stream = torch.cuda.Stream()
+    hs = [B.BcmGraph.from_graph(g, stream=stream.cuda_stream) for g in graphs]
+    ks = [[1, 10, 100][i % 3] for i in range(len(graphs))]
+    outs = [(torch.zeros(k, dtype=torch.int32, device="cuda"), torch.zeros(k, dtype=torch.int64, device="cuda"),
+             torch.zeros(k, dtype=torch.int32, device="cuda")) for k in ks]
+    opts = B.make_options(flags=B.BCM_OUT_DEVICE)
+
+    def one_by_one():
+        for h, k, o in zip(hs, ks, outs):
+            B.bcm_topk(h.h, k, opts, o[0], o[1], o[2])
+
+    one_by_one()
+    batch = B.BcmBatch([h.h for h in hs], ks, outs, stream, opts)
+    batch.run()
+    ref = [tuple(t.clone() for t in o) for o in outs]
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t)
+        return float(np.median(ts))
+
+    # every graph on its own stream, all started, then all finished
+    streams = [torch.cuda.Stream() for _ in graphs]
+    hs2 = [B.BcmGraph.from_graph(g, stream=st.cuda_stream) for g, st in zip(graphs, streams)]
+
+    def all_streams():
+        for h, k, o in zip(hs2, ks, outs):
+            B.bcm_topk_start(h.h, k, opts, o[0], o[1], o[2])
+        for h in hs2:
+            B.bcm_topk_finish(h.h, wait=True)
+
+    all_streams()
+    l0 = B.bcm_launch_count()
+    t_seq = timed(one_by_one, args.steps)
+    seq_launches = (B.bcm_launch_count() - l0) // max(args.steps, 1)
+    t_str = timed(all_streams, args.steps)
+    t_bat = timed(batch.run, args.steps)
+    same = all(all(torch.equal(a, b) for a, b in zip(r, o)) for r, o in zip(ref, outs))
+    for h in hs2:
+        h.close()
+    line = {"metric": "top-k closeness of many small graphs: graphs/s, one bcm_topk per graph vs one CUDA graph",
+            "value": len(graphs) / t_bat, "unit": "graphs/s", "higher_is_better": True, "n_gpus": 1,
+            "steps": args.steps, "data": "synthetic", "dtype": "u64",
+            "config": {"workload": "%d graphs of the serving recipe (seed 3000+i) with n <= %d, k in {1,10,100}"
+                                   % (len(graphs), args.batch_max_n),
+                       "vertices": int(sum(g.n for g in graphs)), "arcs": int(sum(g.m for g in graphs))},
+            "one_by_one": {"s_per_batch": t_seq, "graphs_per_s": len(graphs) / t_seq,
+                           "kernel_launches": int(seq_launches)},
+            "one_stream_per_graph": {"s_per_batch": t_str, "graphs_per_s": len(graphs) / t_str},
+            "cuda_graph": {"s_per_batch": t_bat, "graphs_per_s": len(graphs) / t_bat, "branches": 16},
+            "speedup": t_seq / t_bat, "same_results": bool(same)}
+    batch.close()
+    for h in hs:
+        h.close()
     print(json.dumps(line), flush=True)
     return 0
 
@@ -375,6 +453,10 @@ def main():
     ap.add_argument("--serve-inflight", type=int, default=16)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--serve-check", type=int, default=300, help="results compared with the request alone")
+    ap.add_argument("--serve-blocks", type=int, default=0, help="per-CTA blocks of a served run (0: library default)")
+    ap.add_argument("--batch", action="store_true", help="many small graphs as one CUDA graph")
+    ap.add_argument("--batch-graphs", type=int, default=128)
+    ap.add_argument("--batch-max-n", type=int, default=8000)
     ap.add_argument("--sweep", choices=["ratio", "race"], help="a sweep instead of the benchmark")
     ap.add_argument("--sweep-lo", type=int, default=14, help="ratio sweep: smallest n = 2^lo")
     ap.add_argument("--sweep-hi", type=int, default=21)
@@ -388,6 +470,8 @@ def main():
         return run_serve(args, rank, world)
     if args.sweep:
         return run_sweep(args, rank, world)
+    if args.batch:
+        return run_batch(args, rank, world)
 
     import torch
     torch.cuda.set_device(local)

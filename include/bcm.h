@@ -282,6 +282,29 @@ bcm_status bcm_farness_all_noalloc(const uint64_t* row_ptr, const uint32_t* col,
                                    void* stream, uint64_t* farness, uint32_t* reach);
 
 /*
+ * bcm_batch_create / bcm_batch_run / bcm_batch_destroy -- top-k runs on many
+ * small graphs as one CUDA graph.  The runs of graphs[0..count) (k[i] each,
+ * options opt, which must set BCM_OUT_DEVICE) are executed once to allocate
+ * and check everything, then recorded back to back on `stream` (a
+ * cudaStream_t; not the legacy default stream) and instantiated;
+ * bcm_batch_run launches the recorded graph (one launch instead of several
+ * per graph) and, with wait != 0, waits and checks every run, writing each
+ * graph's min(k[i], n_i) entries to the device arrays ids[i], farness[i],
+ * reach[i] given at creation (they must stay valid).  Only graphs below the
+ * grid-wide threshold (n * grid_lanes/64 < heavy_words) can be batched: their
+ * runs hold no cooperative launch.  A graph of a batch must not run anything
+ * else while a batch run is in flight.  Errors: BCM_ERR_INVALID,
+ * BCM_ERR_UNSUPPORTED (a graph too large, or plain / traced / grid-only /
+ * sharded options), BCM_ERR_OOM, BCM_ERR_CUDA, BCM_ERR_TIMEOUT.
+ */
+typedef struct bcm_batch* bcm_batch_t;
+bcm_status bcm_batch_create(bcm_graph_t* graphs, uint32_t count, const uint32_t* k, const bcm_options* opt,
+                            void* stream, uint32_t* const* ids, uint64_t* const* farness, uint32_t* const* reach,
+                            bcm_batch_t* out);
+bcm_status bcm_batch_run(bcm_batch_t b, int wait);
+bcm_status bcm_batch_destroy(bcm_batch_t b);
+
+/*
  * bcm_topk_merge -- the best min(k, count) of `count` (id, farness, reach)
  * entries under the ranking above (exact 128-bit comparisons, equal scores
  * by id), written best first to out_ids / out_far / out_reach.  Host memory

@@ -41,8 +41,8 @@ TRACE_GRID_LEVEL, TRACE_GRID_WAVE, TRACE_CTA_WAVE = 0, 1, 2
 # every symbol include/bcm.h declares
 EXPORTS = ["bcm_graph_create", "bcm_graph_destroy", "bcm_preprocess", "bcm_scc_bounds", "bcm_topk",
            "bcm_topk_start", "bcm_topk_finish", "bcm_trace", "bcm_graph_trim",
-           "bcm_farness_all", "bcm_farness_all_noalloc", "bcm_topk_merge", "bcm_last_error", "bcm_launch_count",
-           "bcm_workspace_bytes"]
+           "bcm_farness_all", "bcm_farness_all_noalloc", "bcm_topk_merge", "bcm_batch_create", "bcm_batch_run",
+           "bcm_batch_destroy", "bcm_last_error", "bcm_launch_count", "bcm_workspace_bytes"]
 
 
 class bcm_options(ctypes.Structure):
@@ -101,6 +101,10 @@ def load():
         "bcm_farness_all": (i32, [vp, ctypes.POINTER(bcm_options), vp, vp, ctypes.POINTER(bcm_stats)]),
         "bcm_farness_all_noalloc": (i32, [vp, vp, u32, u64, vp, vp, vp]),
         "bcm_topk_merge": (i32, [vp, vp, vp, u32, u32, vp, vp, vp, ctypes.POINTER(u32)]),
+        "bcm_batch_create": (i32, [ctypes.POINTER(vp), u32, ctypes.POINTER(u32), ctypes.POINTER(bcm_options), vp,
+                                   ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]),
+        "bcm_batch_run": (i32, [vp, i32]),
+        "bcm_batch_destroy": (i32, [vp]),
         "bcm_last_error": (ctypes.c_char_p, []),
         "bcm_launch_count": (u64, []),
         "bcm_workspace_bytes": (u64, [vp, ctypes.POINTER(bcm_options)]),
@@ -256,6 +260,40 @@ def bcm_topk_merge(ids, farness, reach, k):
                                  ctypes.byref(written)))
     n = int(written.value)
     return oi[:n], of[:n], orr[:n]
+
+
+class BcmBatch:
+    """bcm_batch_*: the top-k runs of many small graphs recorded as one CUDA
+    graph.  `handles` are bcm graph handles (BcmGraph.h), `ks` their k, `outs`
+    (ids, farness, reach) device tensors per graph, `stream` a torch CUDA
+    stream (not the default one)."""
+
+    def __init__(self, handles, ks, outs, stream, options=None):
+        n = len(handles)
+        opts = options if options is not None else make_options(flags=BCM_OUT_DEVICE)
+        hv = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+        kv = (ctypes.c_uint32 * n)(*ks)
+        iv = (ctypes.c_void_p * n)(*[_ptr(o[0]) for o in outs])
+        fv = (ctypes.c_void_p * n)(*[_ptr(o[1]) for o in outs])
+        rv = (ctypes.c_void_p * n)(*[_ptr(o[2]) for o in outs])
+        self._keep = (outs, stream)
+        self.b = ctypes.c_void_p()
+        _check(load().bcm_batch_create(hv, n, kv, ctypes.byref(opts), _ptr(stream.cuda_stream), iv, fv, rv,
+                                       ctypes.byref(self.b)))
+
+    def run(self, wait=True):
+        _check(load().bcm_batch_run(self.b, int(bool(wait))))
+
+    def close(self):
+        if getattr(self, "b", None) is not None and self.b.value:
+            load().bcm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def bcm_workspace_bytes(h, options=None) -> int:

@@ -1,6 +1,7 @@
 // The C-ABI of include/bcm.h: graph handles, preprocessing, the wave
 // kernels' workspace and launch sequence, and error reporting.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <cstdarg>
@@ -65,6 +66,24 @@ static std::vector<Region> g_regions;
 static size_t g_cached_bytes = 0;
 static const size_t kCacheCap = 96ull << 30;   // clean regions kept for reuse, at most
 
+static void buf_drop_cache(int dev);
+
+static void regions_drop_cache(int dev) {
+    std::vector<Region> drop;
+    {
+        std::lock_guard<std::mutex> lk(g_region_mu);
+        for (size_t i = 0; i < g_regions.size();)
+            if (g_regions[i].dev == dev) {
+                drop.push_back(g_regions[i]);
+                g_cached_bytes -= g_regions[i].bytes;
+                g_regions.erase(g_regions.begin() + i);
+            } else {
+                ++i;
+            }
+    }
+    for (auto& r : drop) cudaFree(r.ptr);
+}
+
 static bcm_status region_acquire(size_t bytes, const Layout& lay, cudaStream_t s, Region* out) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -100,21 +119,10 @@ static bcm_status region_acquire(size_t bytes, const Layout& lay, cudaStream_t s
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
-        // drop cached regions of this device and retry once
-        std::vector<Region> drop;
-        {
-            std::lock_guard<std::mutex> lk(g_region_mu);
-            for (size_t i = 0; i < g_regions.size();)
-                if (g_regions[i].dev == dev) {
-                    drop.push_back(g_regions[i]);
-                    g_cached_bytes -= g_regions[i].bytes;
-                    g_regions.erase(g_regions.begin() + i);
-                } else {
-                    ++i;
-                }
-        }
+        // drop the cached regions and buffers of this device and retry once
         cudaGetLastError();
-        for (auto& r : drop) cudaFree(r.ptr);
+        regions_drop_cache(dev);
+        buf_drop_cache(dev);
         e = cudaMalloc(&p, bytes);
         if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
     }
@@ -139,6 +147,111 @@ static void region_release(Region& r, bool clean) {
     r.bytes = 0;
     r.layout = Layout{};
 }
+
+// ------------------------------------------------------------ buffers
+// Device buffers of graphs and runs (CSR copies, preprocessing arrays and
+// scratch, source lists, outputs) come from a cache of freed buffers: a
+// caller that creates and releases a graph per request (or per benchmark
+// step) then pays no cudaMalloc / cudaFree -- the latter synchronises the
+// device.  A cached buffer is reused for a request of at least half its size.
+struct Buf { int dev; void* ptr; size_t bytes; };
+static std::mutex g_buf_mu;
+static std::vector<Buf> g_bufs;                 // free
+static std::vector<Buf> g_live;                 // handed out
+static size_t g_buf_cached = 0;
+static const size_t kBufCap = 16ull << 30;
+
+static void buf_drop_cache(int dev) {
+    std::vector<Buf> drop;
+    {
+        std::lock_guard<std::mutex> lk(g_buf_mu);
+        for (size_t i = 0; i < g_bufs.size();)
+            if (g_bufs[i].dev == dev) {
+                drop.push_back(g_bufs[i]);
+                g_buf_cached -= g_bufs[i].bytes;
+                g_bufs.erase(g_bufs.begin() + i);
+            } else {
+                ++i;
+            }
+    }
+    for (auto& b : drop) cudaFree(b.ptr);
+}
+
+static void regions_drop_cache(int dev);
+
+static cudaError_t buf_get(void** out, size_t bytes) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (bytes == 0) bytes = 256;
+    {
+        std::lock_guard<std::mutex> lk(g_buf_mu);
+        int best = -1;
+        for (size_t i = 0; i < g_bufs.size(); ++i) {
+            const Buf& b = g_bufs[i];
+            if (b.dev != dev || b.bytes < bytes || b.bytes > 2 * bytes + (1u << 20)) continue;
+            if (best < 0 || b.bytes < g_bufs[best].bytes) best = (int)i;
+        }
+        if (best >= 0) {
+            Buf b = g_bufs[best];
+            g_buf_cached -= b.bytes;
+            g_bufs.erase(g_bufs.begin() + best);
+            g_live.push_back(b);
+            *out = b.ptr;
+            return cudaSuccess;
+        }
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        buf_drop_cache(dev);
+        regions_drop_cache(dev);
+        e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) return e;
+    }
+    std::lock_guard<std::mutex> lk(g_buf_mu);
+    g_live.push_back(Buf{dev, p, bytes});
+    *out = p;
+    return cudaSuccess;
+}
+
+static void buf_put(void* p) {
+    if (!p) return;
+    Buf b{0, nullptr, 0};
+    bool free_it = false;
+    {
+        std::lock_guard<std::mutex> lk(g_buf_mu);
+        for (size_t i = 0; i < g_live.size(); ++i)
+            if (g_live[i].ptr == p) {
+                b = g_live[i];
+                g_live[i] = g_live.back();
+                g_live.pop_back();
+                break;
+            }
+        if (!b.ptr) return;   // not from the pool
+        if (g_buf_cached + b.bytes <= kBufCap) {
+            g_bufs.push_back(b);
+            g_buf_cached += b.bytes;
+        } else {
+            free_it = true;
+        }
+    }
+    if (free_it) cudaFree(b.ptr);
+}
+
+template <class T>
+static cudaError_t buf_get_t(T** out, size_t bytes) {
+    void* p = nullptr;
+    cudaError_t e = buf_get(&p, bytes);
+    *out = (T*)p;
+    return e;
+}
+
+// Pinned host blocks and event sets of runs, reused across graphs.
+struct HostBlock;
+static std::mutex g_pool_mu;
+static std::vector<void*> g_pinned_free;
+static std::vector<std::pair<int, std::array<cudaEvent_t, 5>>> g_events_free;
 
 // Small per-run state of the wave kernels (all zeroed before a run).
 struct Aux {
@@ -300,7 +413,7 @@ Layout region_layout(bcm_graph* g, const Cfg& c) {
 
 bcm_status ensure_aux(bcm_graph* g) {
     if (g->d_aux) return BCM_OK;
-    CU(cudaMalloc(&g->d_aux, sizeof(Aux)), "aux allocation");
+    CU(buf_get_t(&g->d_aux, sizeof(Aux)), "aux allocation");
     return BCM_OK;
 }
 
@@ -331,13 +444,16 @@ double ms_since(std::chrono::steady_clock::time_point t0) {
 }
 
 // ------------------------------------------------------ preprocessing
+bcm_status ensure_run_state(bcm_graph* g, bool trace);
+
 bcm_status preprocess(bcm_graph* g, double* ms) {
     if (g->preprocessed) return BCM_OK;
     cudaStream_t s = g->stream;
     const uint32_t n = g->n;
-    cudaEvent_t e0, e1;
-    CU(cudaEventCreate(&e0), "event");
-    CU(cudaEventCreate(&e1), "event");
+    // timed with the graph's run events (no run is pending before preprocessing)
+    bcm_status est = ensure_run_state(g, false);
+    if (est) return est;
+    cudaEvent_t e0 = g->ev[0], e1 = g->ev[1];
     CU(cudaEventRecord(e0, s), "event record");
     size_t nb = ((size_t)n * sizeof(uint32_t) + 255) & ~(size_t)255;
     size_t scratch = 2 * nb + degree_order_scratch_bytes(n) + scan_scratch_bytes((size_t)n + 1) + 1024;
@@ -346,13 +462,13 @@ bcm_status preprocess(bcm_graph* g, double* ms) {
         if (sc > scratch) scratch = sc;
     }
     if (!g->d_order) {
-        CU(cudaMalloc(&g->d_order, nb * 4), "preprocess allocation");
+        CU(buf_get_t(&g->d_order, nb * 4), "preprocess allocation");
         g->d_xlo = (uint32_t*)((char*)g->d_order + nb);
         g->d_xhi = (uint32_t*)((char*)g->d_order + 2 * nb);
         g->d_comp = (uint32_t*)((char*)g->d_order + 3 * nb);
     }
     char* d_scr = nullptr;
-    CU(cudaMalloc(&d_scr, scratch), "preprocess scratch");
+    CU(buf_get_t(&d_scr, scratch), "preprocess scratch");
     int* d_err = (int*)(d_scr + scratch - 256);
     bcm_status st = BCM_OK;
     int herr = 0;
@@ -372,8 +488,8 @@ bcm_status preprocess(bcm_graph* g, double* ms) {
         } else {
             uint32_t nscc = 0;
             if (!g->d_rrp) {
-                if (cudaMalloc(&g->d_rrp, ((size_t)n + 1) * 4) != cudaSuccess ||
-                    cudaMalloc(&g->d_rcol, (g->m ? g->m : 1) * 4) != cudaSuccess) {
+                if (buf_get_t(&g->d_rrp, ((size_t)n + 1) * 4) != cudaSuccess ||
+                    buf_get_t(&g->d_rcol, (g->m ? g->m : 1) * 4) != cudaSuccess) {
                     st = fail(BCM_ERR_OOM, "in-arc CSR allocation");
                     break;
                 }
@@ -401,11 +517,9 @@ bcm_status preprocess(bcm_graph* g, double* ms) {
     } while (0);
     cudaEventRecord(e1, s);
     cudaError_t se = cudaStreamSynchronize(s);
-    cudaFree(d_scr);
+    buf_put(d_scr);
     float t = 0;
     cudaEventElapsedTime(&t, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if (st != BCM_OK) return st;
     if (se != cudaSuccess) return cuda_fail(se, "preprocessing");
     if (herr) return check_dev_err(herr);
@@ -424,7 +538,7 @@ bcm_status ensure_labels(bcm_graph* g) {
     size_t nb = ((size_t)n * sizeof(uint32_t) + 255) & ~(size_t)255;
     size_t bytes = nb + scan_scratch_bytes(n) + 512;
     char* d_scr = nullptr;
-    CU(cudaMalloc(&d_scr, bytes), "label scratch");
+    CU(buf_get_t(&d_scr, bytes), "label scratch");
     uint32_t* flags = (uint32_t*)d_scr;
     uint32_t* total = (uint32_t*)(d_scr + bytes - 256);
     bcm_status st = BCM_OK;
@@ -435,7 +549,7 @@ bcm_status ensure_labels(bcm_graph* g) {
         cudaMemcpyAsync(&g->n_comp, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         st = fail(BCM_ERR_CUDA, "copy");
     cudaError_t e = cudaStreamSynchronize(s);
-    cudaFree(d_scr);
+    buf_put(d_scr);
     if (st) return st;
     if (e != cudaSuccess) return cuda_fail(e, "component labels");
     g->labels_ready = true;
@@ -549,10 +663,24 @@ uint32_t shard_size(uint32_t n, uint32_t index, uint32_t count) {
 }
 
 bcm_status ensure_run_state(bcm_graph* g, bool trace) {
+    if (!g->ev[0] || !g->h) {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (!g->ev[0])
+            for (size_t i = 0; i < g_events_free.size(); ++i)
+                if (g_events_free[i].first == g->dev) {
+                    for (int j = 0; j < 5; ++j) g->ev[j] = g_events_free[i].second[j];
+                    g_events_free.erase(g_events_free.begin() + i);
+                    break;
+                }
+        if (!g->h && !g_pinned_free.empty()) {
+            g->h = (HostBlock*)g_pinned_free.back();
+            g_pinned_free.pop_back();
+        }
+    }
     for (int i = 0; i < 5; ++i)
         if (!g->ev[i]) CU(cudaEventCreate(&g->ev[i]), "event");
     if (!g->h) CU(cudaMallocHost(&g->h, sizeof(HostBlock)), "pinned host allocation");
-    if (trace && !g->d_trace) CU(cudaMalloc(&g->d_trace, (size_t)kTraceCap * 4 * sizeof(u64)), "trace allocation");
+    if (trace && !g->d_trace) CU(buf_get_t(&g->d_trace, (size_t)kTraceCap * 4 * sizeof(u64)), "trace allocation");
     return BCM_OK;
 }
 
@@ -570,11 +698,11 @@ bcm_status start_run(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, vo
     const bool plain = !exhaustive && (c.flags & BCM_PLAIN);
     if (!plain && (st = ensure_slots(g, c))) return st;
     if (exhaustive && !g->d_far) {
-        CU(cudaMalloc(&g->d_far, (size_t)g->n * sizeof(uint64_t) + 256), "output allocation");
-        CU(cudaMalloc(&g->d_reach, (size_t)g->n * sizeof(uint32_t) + 256), "output allocation");
+        CU(buf_get_t(&g->d_far, (size_t)g->n * sizeof(uint64_t) + 256), "output allocation");
+        CU(buf_get_t(&g->d_reach, (size_t)g->n * sizeof(uint32_t) + 256), "output allocation");
     }
     if (plain && !g->d_plain)
-        CU(cudaMalloc(&g->d_plain, (size_t)g->n * 3 * sizeof(uint32_t) + 256), "plain buffers");
+        CU(buf_get_t(&g->d_plain, (size_t)g->n * 3 * sizeof(uint32_t) + 256), "plain buffers");
     CU(cudaMemsetAsync(g->d_aux, 0, sizeof(Aux), s), "aux clear");
     WaveParams p = base_params(g, c);
     p.exhaustive = exhaustive ? 1u : 0u;
@@ -582,7 +710,7 @@ bcm_status start_run(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, vo
     uint32_t n_src = g->n;   // sources this run takes
     if (!exhaustive && c.shard_count > 1) {
         n_src = shard_size(g->n, c.shard_index, c.shard_count);
-        if (!g->d_shard) CU(cudaMalloc(&g->d_shard, (size_t)g->n * sizeof(uint32_t)), "shard list allocation");
+        if (!g->d_shard) CU(buf_get_t(&g->d_shard, (size_t)g->n * sizeof(uint32_t)), "shard list allocation");
         if (n_src) {
             unsigned blocks = (n_src + 255) / 256 < 4864 ? (n_src + 255) / 256 : 4864;
             k_shard_sources<<<blocks, 256, 0, s>>>(g->d_order, n_src, c.shard_index, c.shard_count, g->d_shard);
@@ -623,7 +751,7 @@ bcm_status start_run(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, vo
         const bool defer = !exhaustive && !(c.flags & (BCM_CTA_ONLY | BCM_GRID_ONLY)) && c.defer_words &&
                            (uint64_t)g->n * c.W >= c.defer_words;
         if (defer) {
-            if (!g->d_defer) CU(cudaMalloc(&g->d_defer, (size_t)g->n * sizeof(uint32_t)), "defer list allocation");
+            if (!g->d_defer) CU(buf_get_t(&g->d_defer, (size_t)g->n * sizeof(uint32_t)), "defer list allocation");
             p.defer_words = (uint32_t)(c.defer_words < 0xffffffffull ? c.defer_words : 0xffffffffull);
             p.defer_n = &g->d_aux->defer_n;
             p.defer_src = g->d_defer;
@@ -656,7 +784,7 @@ bcm_status start_run(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, vo
                                !(c.flags & (BCM_NO_PREFILTER | BCM_GRID_ONLY));
         if (prefilter) {
             if (!g->d_surv) {
-                cudaError_t e = cudaMalloc(&g->d_surv, (size_t)g->n * sizeof(uint32_t));
+                cudaError_t e = buf_get_t(&g->d_surv, (size_t)g->n * sizeof(uint32_t));
                 if (e != cudaSuccess) { cudaStreamSynchronize(s); return cuda_fail(e, "prefilter list allocation"); }
             }
             rc = launch_prefilter(p, g->d_surv, &g->d_aux->surv_n, s);
@@ -854,9 +982,9 @@ bcm_status bcm_graph_create(const uint64_t* row_ptr, const uint32_t* col, uint32
     int* d_err = nullptr;
     do {
         cudaError_t e;
-        if ((e = cudaMalloc(&g->d_rp, ((size_t)n + 1) * sizeof(uint32_t))) != cudaSuccess) { st = cuda_fail(e, "graph allocation"); break; }
-        if ((e = cudaMalloc(&g->d_col, (m ? m : 1) * sizeof(uint32_t))) != cudaSuccess) { st = cuda_fail(e, "graph allocation"); break; }
-        if ((e = cudaMalloc(&d_rp64, ((size_t)n + 1) * sizeof(uint64_t) + sizeof(int) * 4)) != cudaSuccess) { st = cuda_fail(e, "graph allocation"); break; }
+        if ((e = buf_get_t(&g->d_rp, ((size_t)n + 1) * sizeof(uint32_t))) != cudaSuccess) { st = cuda_fail(e, "graph allocation"); break; }
+        if ((e = buf_get_t(&g->d_col, (m ? m : 1) * sizeof(uint32_t))) != cudaSuccess) { st = cuda_fail(e, "graph allocation"); break; }
+        if ((e = buf_get_t(&d_rp64, ((size_t)n + 1) * sizeof(uint64_t) + sizeof(int) * 4)) != cudaSuccess) { st = cuda_fail(e, "graph allocation"); break; }
         d_err = (int*)(d_rp64 + n + 1);
         cudaMemcpyKind kind = ptr_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         if ((e = cudaMemcpyAsync(d_rp64, row_ptr, ((size_t)n + 1) * sizeof(uint64_t), kind, s)) != cudaSuccess) { st = cuda_fail(e, "row_ptr copy"); break; }
@@ -888,7 +1016,7 @@ bcm_status bcm_graph_create(const uint64_t* row_ptr, const uint32_t* col, uint32
             if (herr[1] & 1) { st = fail(BCM_ERR_NOT_SYMMETRIC, "undirected graph has an arc (u,w) without (w,u)"); break; }
         }
     } while (0);
-    if (d_rp64) cudaFree(d_rp64);
+    if (d_rp64) buf_put(d_rp64);
     if (st != BCM_OK) {
         bcm_graph_destroy(g);
         return st;
@@ -901,22 +1029,19 @@ bcm_status bcm_graph_destroy(bcm_graph_t g) {
     if (!g) return BCM_OK;
     if (g->stream) cudaStreamSynchronize(g->stream);
     else cudaDeviceSynchronize();
-    cudaFree(g->d_rp);
-    cudaFree(g->d_col);
-    cudaFree(g->d_order);
-    cudaFree(g->d_aux);
-    cudaFree(g->d_plain);
-    cudaFree(g->d_far);
-    cudaFree(g->d_reach);
-    cudaFree(g->d_rrp);
-    cudaFree(g->d_rcol);
-    cudaFree(g->d_trace);
-    cudaFree(g->d_defer);
-    cudaFree(g->d_shard);
-    cudaFree(g->d_surv);
-    for (int i = 0; i < 5; ++i)
-        if (g->ev[i]) cudaEventDestroy(g->ev[i]);
-    if (g->h) cudaFreeHost(g->h);
+    for (void* b : {(void*)g->d_rp, (void*)g->d_col, (void*)g->d_order, (void*)g->d_aux, (void*)g->d_plain,
+                    (void*)g->d_far, (void*)g->d_reach, (void*)g->d_rrp, (void*)g->d_rcol, (void*)g->d_trace,
+                    (void*)g->d_defer, (void*)g->d_shard, (void*)g->d_surv})
+        buf_put(b);
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (g->ev[0]) {
+            std::array<cudaEvent_t, 5> ev;
+            for (int i = 0; i < 5; ++i) ev[i] = g->ev[i];
+            g_events_free.push_back({g->dev, ev});
+        }
+        if (g->h) g_pinned_free.push_back(g->h);
+    }
     // a run that was started and never finished may not have left the region clean
     region_release(g->slots, !g->pend.active);
     delete g;
@@ -1064,13 +1189,9 @@ bcm_status bcm_graph_trim(bcm_graph_t g) {
     if (g->pend.active) return fail(BCM_ERR_INVALID, "a run on this graph has not been finished");
     CU(g->stream ? cudaStreamSynchronize(g->stream) : cudaDeviceSynchronize(), "synchronize");
     region_release(g->slots, true);
-    cudaFree(g->d_plain);
-    cudaFree(g->d_far);
-    cudaFree(g->d_reach);
-    cudaFree(g->d_trace);
-    cudaFree(g->d_defer);
-    cudaFree(g->d_shard);
-    cudaFree(g->d_surv);
+    for (void* b : {(void*)g->d_plain, (void*)g->d_far, (void*)g->d_reach, (void*)g->d_trace, (void*)g->d_defer,
+                    (void*)g->d_shard, (void*)g->d_surv})
+        buf_put(b);
     g->d_surv = nullptr;
     g->d_defer = nullptr;
     g->d_shard = nullptr;
@@ -1121,6 +1242,156 @@ bcm_status bcm_topk_merge(const uint32_t* ids, const uint64_t* farness, const ui
         out_reach[i] = reach[idx[i]];
     }
     *written = w;
+    return BCM_OK;
+}
+
+// --------------------------------------------------------------- batches
+struct bcm_batch {
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t stream = nullptr;
+    std::vector<bcm_graph*> graphs;
+    std::vector<uint32_t> kk;     // entries each run must hold
+};
+
+static bcm_status batch_fail(bcm_batch* b, bcm_status st) {
+    if (b) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        delete b;
+    }
+    return st;
+}
+
+bcm_status bcm_batch_create(bcm_graph_t* graphs, uint32_t count, const uint32_t* k, const bcm_options* opt,
+                            void* stream, uint32_t* const* ids, uint64_t* const* farness, uint32_t* const* reach,
+                            bcm_batch_t* out) {
+    t_err.clear();
+    if (!out || !graphs || !k || !ids || !farness || !reach || count == 0)
+        return fail(BCM_ERR_INVALID, "a pointer argument is NULL or count is 0");
+    *out = nullptr;
+    bcm_options o{};
+    if (opt) o = *opt;
+    if (!(o.flags & BCM_OUT_DEVICE)) return fail(BCM_ERR_INVALID, "batch outputs must be device memory (BCM_OUT_DEVICE)");
+    if (o.flags & (BCM_PLAIN | BCM_TRACE | BCM_GRID_ONLY) || o.shard_count > 1)
+        return fail(BCM_ERR_UNSUPPORTED, "plain, traced, grid-only and sharded runs cannot be batched");
+    bcm_batch* b = new (std::nothrow) bcm_batch();
+    if (!b) return fail(BCM_ERR_OOM, "host allocation");
+    b->stream = (cudaStream_t)stream;
+    std::vector<Cfg> cfg(count);
+    // every run once, outside the capture: preprocessing, workspaces and
+    // buffers are allocated here, and each run is checked
+    for (uint32_t i = 0; i < count; ++i) {
+        bcm_graph* g = graphs[i];
+        if (!g || !ids[i] || !farness[i] || !reach[i]) {
+            fail(BCM_ERR_INVALID, "graph or output %u is NULL", i);
+            return batch_fail(b, BCM_ERR_INVALID);
+        }
+        if (g->pend.active) {
+            fail(BCM_ERR_INVALID, "graph %u has a run that has not been finished", i);
+            return batch_fail(b, BCM_ERR_INVALID);
+        }
+        if (k[i] < 1 || k[i] > 1024) {
+            fail(BCM_ERR_INVALID, "k[%u] = %u: must be in 1..1024", i, k[i]);
+            return batch_fail(b, BCM_ERR_INVALID);
+        }
+        bcm_status st = preprocess(g, nullptr);
+        if (st) return batch_fail(b, st);
+        if ((st = resolve(g, &o, &cfg[i]))) return batch_fail(b, st);
+        // the batch holds no cooperative launch: only graphs below the
+        // grid-wide threshold, whose runs are a seed wave, the prefilter and
+        // per-CTA waves
+        if ((uint64_t)g->n * cfg[i].grid_W >= cfg[i].heavy_words || g->n == 0) {
+            fail(BCM_ERR_UNSUPPORTED, "graph %u (n = %u) is too large (or empty) for a batch; use bcm_topk", i, g->n);
+            return batch_fail(b, BCM_ERR_UNSUPPORTED);
+        }
+        cudaStream_t keep = g->stream;
+        g->stream = b->stream;
+        unsigned long long sv[ST_COUNT], wv[ST_COUNT];
+        RunTimes rt;
+        st = start_run(g, cfg[i], k[i], false, ids[i], farness[i], reach[i]);
+        if (st == BCM_OK) st = finish_run(g, true, sv, wv, &rt);
+        g->stream = keep;
+        if (st) return batch_fail(b, st);
+        b->graphs.push_back(g);
+        b->kk.push_back(k[i] < g->n ? k[i] : g->n);
+    }
+    // record the runs on kBatchBranches parallel branches (graph i on branch
+    // i mod kBatchBranches): streams forked from the batch stream by an event
+    // and joined back, so the recorded graph runs independent graphs at once
+    constexpr uint32_t kBatchBranches = 16;
+    const uint32_t nbr = count < kBatchBranches ? count : kBatchBranches;
+    std::vector<cudaStream_t> br(nbr, nullptr);
+    std::vector<cudaEvent_t> ev(nbr + 1, nullptr);
+    bcm_status st = BCM_OK;
+    for (uint32_t j = 0; j < nbr && st == BCM_OK; ++j)
+        if (cudaStreamCreateWithFlags(&br[j], cudaStreamNonBlocking) != cudaSuccess) st = fail(BCM_ERR_CUDA, "stream");
+    for (uint32_t j = 0; j <= nbr && st == BCM_OK; ++j)
+        if (cudaEventCreateWithFlags(&ev[j], cudaEventDisableTiming) != cudaSuccess) st = fail(BCM_ERR_CUDA, "event");
+    cudaError_t e = cudaSuccess;
+    if (st == BCM_OK) {
+        e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) st = cuda_fail(e, "stream capture");
+    }
+    const bool capturing = st == BCM_OK;
+    if (capturing) {
+        cudaEventRecord(ev[nbr], b->stream);                 // fork
+        for (uint32_t j = 0; j < nbr; ++j) cudaStreamWaitEvent(br[j], ev[nbr], 0);
+    }
+    for (uint32_t i = 0; i < count && st == BCM_OK; ++i) {
+        bcm_graph* g = graphs[i];
+        cudaStream_t keep = g->stream;
+        g->stream = br[i % nbr];
+        st = start_run(g, cfg[i], k[i], false, ids[i], farness[i], reach[i]);
+        g->pend.active = false;   // recorded, not running
+        g->stream = keep;
+    }
+    if (capturing) {
+        for (uint32_t j = 0; j < nbr; ++j) {                // join
+            cudaEventRecord(ev[j], br[j]);
+            cudaStreamWaitEvent(b->stream, ev[j], 0);
+        }
+    }
+    cudaGraph_t graph = nullptr;
+    if (capturing) e = cudaStreamEndCapture(b->stream, &graph);
+    if (st == BCM_OK && e != cudaSuccess) st = cuda_fail(e, "stream capture");
+    if (st == BCM_OK) {
+        e = cudaGraphInstantiate(&b->exec, graph, 0);
+        if (e != cudaSuccess) st = cuda_fail(e, "graph instantiation");
+    }
+    if (graph) cudaGraphDestroy(graph);
+    for (auto x : br)
+        if (x) cudaStreamDestroy(x);
+    for (auto x : ev)
+        if (x) cudaEventDestroy(x);
+    if (st) return batch_fail(b, st);
+    *out = b;
+    return BCM_OK;
+}
+
+bcm_status bcm_batch_run(bcm_batch_t b, int wait) {
+    t_err.clear();
+    if (!b) return fail(BCM_ERR_INVALID, "batch is NULL");
+    CU(cudaGraphLaunch(b->exec, b->stream), "graph launch");
+    if (!wait) return BCM_OK;
+    CU(cudaStreamSynchronize(b->stream), "batch run");
+    for (size_t i = 0; i < b->graphs.size(); ++i) {
+        const HostBlock* h = b->graphs[i]->h;
+        if (h->err) {
+            region_release(b->graphs[i]->slots, false);
+            bcm_status st = check_dev_err(h->err);
+            return fail(st, "graph %zu of the batch: %s", i, t_err.c_str());
+        }
+        if (h->topk_count != b->kk[i])
+            return fail(BCM_ERR_CUDA, "graph %zu of the batch: top-k holds %u entries, expected %u", i, h->topk_count,
+                        b->kk[i]);
+    }
+    return BCM_OK;
+}
+
+bcm_status bcm_batch_destroy(bcm_batch_t b) {
+    if (!b) return BCM_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    delete b;
     return BCM_OK;
 }
 

@@ -818,36 +818,73 @@ __global__ void __launch_bounds__(256) k_prefilter(WaveParams p, u32* out, u32* 
     const u32 lane = threadIdx.x & 31;
     const size_t gw = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5;
     const size_t gnw = ((size_t)gridDim.x * blockDim.x) >> 5;
-    for (size_t pos = s_begin + gw; pos < p.n_end; pos += gnw) {
-        const u32 v = __ldg(&p.sources[pos]);
-        const u32 b = __ldg(&G.rp[v]), deg = __ldg(&G.rp[v + 1]) - b;
-        bool cut = false;
-        if (s_thr.valid && deg == 0) {
+    // 32 sources per warp step, one per thread; a source with more than 32
+    // neighbours has its degree sum taken by the whole warp afterwards
+    for (size_t pos0 = s_begin + gw * 32; pos0 < p.n_end; pos0 += gnw * 32) {
+        const size_t pos = pos0 + lane;
+        const bool have = pos < p.n_end;
+        u32 v = 0, b = 0, deg = 0, xlo = 0, xhi = 0;
+        bool cut = false, done = !have || !s_thr.valid;
+        if (have) {
+            v = __ldg(&p.sources[pos]);
+            b = __ldg(&G.rp[v]);
+            deg = __ldg(&G.rp[v + 1]) - b;
+        }
+        if (!done && deg == 0) {
             // R(v) = {v}: complete with key (0, 1); it only goes on (to be
             // merged by a wave) if it ranks before the k-th
+            done = true;
             if (!ranks_before(0, 1, v, s_thr.N, s_thr.F, s_thr.id)) {
-                cut = true;   // done: not a stop by the bound, a completion that cannot enter
-                if (lane == 0) bstat_add(s_bst, ST_COMPLETED, 1);
+                cut = true;
+                bstat_add(s_bst, ST_COMPLETED, 1);
             }
-        } else if (s_thr.valid) {
-            const u32 xlo = __ldg(&G.xlo[v]), xhi = __ldg(&G.xhi[v]);
-            cut = bfscut_stops(0, deg, 0, 1, xlo, xhi, v, s_thr);
-            if (!cut) {
-                u64 g2 = 0;
-                for (u32 i = lane; i < deg; i += 32) {
-                    const u32 u = __ldg(&G.col[b + i]);
-                    g2 += __ldg(&G.rp[u + 1]) - __ldg(&G.rp[u]) - p.footnote;
-                }
-                for (int o = 16; o; o >>= 1) g2 += __shfl_xor_sync(0xffffffffu, g2, o);
-                cut = bfscut_stops(deg, g2, 1, 1 + deg, xlo, xhi, v, s_thr);
-                if (cut && lane == 0) {   // level 0 was expanded
-                    st.mvis += deg;
-                    st.arcwords += deg;
-                }
-            }
-            if (cut && lane == 0) bstat_add(s_bst, ST_CUT, 1);
         }
-        if (!cut && lane == 0) out[atomicAdd(out_n, 1u)] = v;
+        if (!done) {
+            xlo = __ldg(&G.xlo[v]);
+            xhi = __ldg(&G.xhi[v]);
+            if (bfscut_stops(0, deg, 0, 1, xlo, xhi, v, s_thr)) {
+                cut = done = true;
+                bstat_add(s_bst, ST_CUT, 1);
+            }
+        }
+        // level 1: gamma~_2 = sum over N(v) of deg(u) - footnote
+        u64 g2 = 0;
+        const bool serial = !done && deg <= 32;
+        if (serial) {
+            for (u32 i = 0; i < deg; ++i) {
+                const u32 u = __ldg(&G.col[b + i]);
+                g2 += __ldg(&G.rp[u + 1]) - __ldg(&G.rp[u]) - p.footnote;
+            }
+        }
+        u32 big = __ballot_sync(0xffffffffu, !done && !serial);
+        while (big) {
+            const int l0 = __ffs(big) - 1;
+            big &= big - 1;
+            const u32 cb = __shfl_sync(0xffffffffu, b, l0), cd = __shfl_sync(0xffffffffu, deg, l0);
+            u64 part = 0;
+            for (u32 i = lane; i < cd; i += 32) {
+                const u32 u = __ldg(&G.col[cb + i]);
+                part += __ldg(&G.rp[u + 1]) - __ldg(&G.rp[u]) - p.footnote;
+            }
+            for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            if (lane == (u32)l0) g2 = part;
+        }
+        if (!done) {
+            if (bfscut_stops(deg, g2, 1, 1 + deg, xlo, xhi, v, s_thr)) {
+                cut = true;
+                bstat_add(s_bst, ST_CUT, 1);
+                st.mvis += deg;       // level 0 was expanded
+                st.arcwords += deg;
+            }
+        }
+        const bool keep = have && !cut;
+        const u32 m = __ballot_sync(0xffffffffu, keep);
+        if (m) {
+            u32 at = 0;
+            if (lane == 0) at = atomicAdd(out_n, (u32)__popc(m));
+            at = __shfl_sync(0xffffffffu, at, 0);
+            if (keep) out[at + __popc(m & lanemask_lt())] = v;
+        }
     }
     __syncthreads();
     flush_stats(st, s_bst, p.stats);

@@ -251,11 +251,6 @@ class GpuBackend(Backend):
     """Graphs resident on the device, one CUDA stream and one set of pinned
     output buffers per graph."""
 
-    # per-CTA blocks of a served run: runs share the GPU, so one run gains
-    # little from every SM's worth of CTAs, while each CTA holds a wave slot
-    # of 44 bytes per vertex (about 27 GB for 304 CTAs at n = 2e6)
-    SERVE_BLOCKS = 64
-
     def __init__(self, graphs, options=None, kmax: int = 1024, trace: bool = False):
         import torch
 
@@ -263,7 +258,7 @@ class GpuBackend(Backend):
         super().__init__()
         self.bcm = bcm
         bcm.load()
-        self.opts = options if options is not None else bcm.make_options(blocks=self.SERVE_BLOCKS)
+        self.opts = options if options is not None else bcm.make_options()
         # with trace, every run records its kernels' time stamps and collect()
         # reports the span of device time the run's waves occupied
         self.trace = trace
