@@ -251,7 +251,12 @@ static cudaError_t buf_get_t(T** out, size_t bytes) {
 struct HostBlock;
 static std::mutex g_pool_mu;
 static std::vector<void*> g_pinned_free;
-static std::vector<std::pair<int, std::array<cudaEvent_t, 5>>> g_events_free;
+struct RunRes {                 // per-graph CUDA objects, reused across graphs
+    int dev;
+    std::array<cudaEvent_t, 7> ev; // run timing (5), preprocessing fork and join (2)
+    cudaStream_t aux;              // helper stream of preprocessing
+};
+static std::vector<RunRes> g_res_free;
 
 // Small per-run state of the wave kernels (all zeroed before a run).
 struct Aux {
@@ -286,7 +291,7 @@ struct HostBlock {
     int err;
     uint32_t topk_count;
     uint32_t trace_n;
-    uint32_t pad;
+    int not_simple;            // preprocessing: the simple-graph check
     unsigned long long stats[ST_COUNT];        // per-CTA wave kernel
     unsigned long long seed_stats[ST_COUNT];   // grid-wide or plain kernel
 };
@@ -314,7 +319,8 @@ struct bcm_graph {
     uint32_t* d_rcol = nullptr;
     uint32_t n_comp = 0;
     bool labels_ready = false;     // d_comp holds labels (else component roots)
-    bool simple = false;           // rows strictly increasing, no self-loops
+    bool simple = false;           // rows strictly increasing, no self-loops (found by preprocessing):
+                                   // level 1 of every BFS is then known from degrees alone (the prefilter)
     bool preprocessed = false;
     Aux* d_aux = nullptr;
     uint32_t* d_plain = nullptr;   // stamps [n], two vertex queues [2n]
@@ -333,8 +339,10 @@ struct bcm_graph {
         double pms = 0;           // preprocessing time of this call
         std::chrono::steady_clock::time_point t0;
     } pend;
-    // start, first grid pass done, per-CTA pass done, deferred grid pass done, copies done
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // start, first grid pass done, per-CTA pass done, deferred grid pass done, copies done;
+    // then the fork and join of preprocessing's helper stream
+    cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t aux = nullptr;
     uint32_t* d_defer = nullptr;   // [n] sources deferred by per-CTA waves
     uint32_t* d_shard = nullptr;   // [n] this shard's sources, in degree order
     uint32_t* d_surv = nullptr;    // [n] sources left for the per-CTA waves by the prefilter
@@ -470,11 +478,34 @@ bcm_status preprocess(bcm_graph* g, double* ms) {
     char* d_scr = nullptr;
     CU(buf_get_t(&d_scr, scratch), "preprocess scratch");
     int* d_err = (int*)(d_scr + scratch - 256);
+    // the degree order and the simple-graph check do not depend on the
+    // components: they run on the helper stream meanwhile, with their own
+    // scratch, and are joined below
+    const size_t dos = (degree_order_scratch_bytes(n) + 255) & ~(size_t)255;
+    char* d_scr2 = nullptr;
+    if (buf_get_t(&d_scr2, dos + 256) != cudaSuccess) {
+        buf_put(d_scr);
+        return fail(BCM_ERR_OOM, "preprocess scratch");
+    }
+    int* d_simple = (int*)(d_scr2 + dos);
     bcm_status st = BCM_OK;
     int herr = 0;
+    bool forked = false;
     do {
         if (cudaMemsetAsync(d_err, 0, sizeof(int), s) != cudaSuccess) { st = fail(BCM_ERR_CUDA, "memset"); break; }
         if (n == 0) break;
+        if (cudaEventRecord(g->ev[5], s) != cudaSuccess || cudaStreamWaitEvent(g->aux, g->ev[5], 0) != cudaSuccess) {
+            st = fail(BCM_ERR_CUDA, "stream fork");
+            break;
+        }
+        forked = true;
+        if (cudaMemsetAsync(d_simple, 0, sizeof(int), g->aux) != cudaSuccess ||
+            launch_degree_order(g->d_rp, n, g->d_order, d_scr2, dos, g->aux) ||
+            launch_simple_check(g->d_rp, g->d_col, n, d_simple, g->aux) ||
+            cudaMemcpyAsync(&g->h->not_simple, d_simple, sizeof(int), cudaMemcpyDeviceToHost, g->aux) != cudaSuccess) {
+            st = fail(BCM_ERR_CUDA, "degree order: %s", cudaGetErrorString(cudaGetLastError()));
+            break;
+        }
         if (!g->directed) {
             uint32_t* parent = g->d_comp;
             uint32_t* size = (uint32_t*)d_scr;
@@ -506,18 +537,21 @@ bcm_status preprocess(bcm_graph* g, double* ms) {
             g->n_comp = nscc;
             g->labels_ready = true;
         }
-        if (launch_degree_order(g->d_rp, n, g->d_order, d_scr, scratch - 1024, s)) {
-            st = fail(BCM_ERR_CUDA, "degree order: %s", cudaGetErrorString(cudaGetLastError()));
-            break;
-        }
         if (cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) {
             st = fail(BCM_ERR_CUDA, "copy");
             break;
         }
     } while (0);
+    if (forked) {   // join the helper stream
+        cudaEventRecord(g->ev[6], g->aux);
+        cudaStreamWaitEvent(s, g->ev[6], 0);
+    }
     cudaEventRecord(e1, s);
     cudaError_t se = cudaStreamSynchronize(s);
+    if (forked) cudaStreamSynchronize(g->aux);
     buf_put(d_scr);
+    buf_put(d_scr2);
+    if (forked) g->simple = g->h->not_simple == 0;
     float t = 0;
     cudaEventElapsedTime(&t, e0, e1);
     if (st != BCM_OK) return st;
@@ -666,10 +700,11 @@ bcm_status ensure_run_state(bcm_graph* g, bool trace) {
     if (!g->ev[0] || !g->h) {
         std::lock_guard<std::mutex> lk(g_pool_mu);
         if (!g->ev[0])
-            for (size_t i = 0; i < g_events_free.size(); ++i)
-                if (g_events_free[i].first == g->dev) {
-                    for (int j = 0; j < 5; ++j) g->ev[j] = g_events_free[i].second[j];
-                    g_events_free.erase(g_events_free.begin() + i);
+            for (size_t i = 0; i < g_res_free.size(); ++i)
+                if (g_res_free[i].dev == g->dev) {
+                    for (int j = 0; j < 7; ++j) g->ev[j] = g_res_free[i].ev[j];
+                    g->aux = g_res_free[i].aux;
+                    g_res_free.erase(g_res_free.begin() + i);
                     break;
                 }
         if (!g->h && !g_pinned_free.empty()) {
@@ -677,8 +712,9 @@ bcm_status ensure_run_state(bcm_graph* g, bool trace) {
             g_pinned_free.pop_back();
         }
     }
-    for (int i = 0; i < 5; ++i)
-        if (!g->ev[i]) CU(cudaEventCreate(&g->ev[i]), "event");
+    for (int i = 0; i < 7; ++i)
+        if (!g->ev[i]) CU(cudaEventCreateWithFlags(&g->ev[i], i < 5 ? cudaEventDefault : cudaEventDisableTiming), "event");
+    if (!g->aux) CU(cudaStreamCreateWithFlags(&g->aux, cudaStreamNonBlocking), "stream");
     if (!g->h) CU(cudaMallocHost(&g->h, sizeof(HostBlock)), "pinned host allocation");
     if (trace && !g->d_trace) CU(buf_get_t(&g->d_trace, (size_t)kTraceCap * 4 * sizeof(u64)), "trace allocation");
     return BCM_OK;
@@ -998,12 +1034,7 @@ bcm_status bcm_graph_create(const uint64_t* row_ptr, const uint32_t* col, uint32
         if ((e = cudaMemcpyAsync(herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) { st = cuda_fail(e, "copy"); break; }
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { st = cuda_fail(e, "graph upload"); break; }
         if (herr[0]) { st = fail(BCM_ERR_INVALID, "malformed CSR: row_ptr must rise from 0 to m and every col < n"); break; }
-        // simple (sorted rows, no repeated arc, no self-loop): level 1 of every
-        // BFS is then known from degrees alone (see the prefilter)
-        if (launch_simple_check(g->d_rp, g->d_col, n, d_err + 2, s)) { st = fail(BCM_ERR_CUDA, "simple-graph check"); break; }
-        if ((e = cudaMemcpyAsync(&herr[2], d_err + 2, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) { st = cuda_fail(e, "copy"); break; }
-        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { st = cuda_fail(e, "graph upload"); break; }
-        g->simple = herr[2] == 0;
+
         if (!directed && (flags & BCM_CHECK_SYMMETRIC) && n > 0) {
             if ((e = cudaMemsetAsync(d_err + 1, 0, sizeof(int), s)) != cudaSuccess) { st = cuda_fail(e, "memset"); break; }
             unsigned blocks = (unsigned)(((size_t)n * 32 + 255) / 256);
@@ -1036,9 +1067,11 @@ bcm_status bcm_graph_destroy(bcm_graph_t g) {
     {
         std::lock_guard<std::mutex> lk(g_pool_mu);
         if (g->ev[0]) {
-            std::array<cudaEvent_t, 5> ev;
-            for (int i = 0; i < 5; ++i) ev[i] = g->ev[i];
-            g_events_free.push_back({g->dev, ev});
+            RunRes r;
+            r.dev = g->dev;
+            for (int i = 0; i < 7; ++i) r.ev[i] = g->ev[i];
+            r.aux = g->aux;
+            g_res_free.push_back(r);
         }
         if (g->h) g_pinned_free.push_back(g->h);
     }

@@ -1180,6 +1180,7 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
         u32 d = 0, cur = 0;
         u64 wave_entries = 0;
         bool pulled = false;
+        u32 level_cnt = 0;   // entries of the level's frontier list, read before it can be reset
         for (;;) {
             if (!p.exhaustive && tid == 0) read_threshold(p.topk.thr, s_thr);
             __syncthreads();
@@ -1220,6 +1221,7 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
                                       st, bm[cur ^ 1]);
                 } else {
                     const u32 cnt = vload(&p.glist_n[cur]);
+                    level_cnt = cnt;
                     wave_entries += cnt;
                     // by pull once the frontier's out-arcs reach n*W/pull_div:
                     // push pays per arc (and a hub's arcs fall to one warp),
@@ -1268,7 +1270,9 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
                 }
             }
             if (pulled) {   // every block is past the pull: retire the frontier words
-                pull_retire<W>(G, S.list[cur], vload(&p.glist_n[cur]), S.F[cur], s_alive32,
+                // (the count read at the level's start: the leader resets
+                // glist_n[cur] below while slower blocks may still be here)
+                pull_retire<W>(G, S.list[cur], level_cnt, S.F[cur], s_alive32,
                                blockIdx.x * THREADS + tid, gridDim.x * THREADS, st);
                 pulled = false;
                 __syncthreads();
