@@ -482,12 +482,13 @@ bcm_status preprocess(bcm_graph* g, double* ms) {
     // components: they run on the helper stream meanwhile, with their own
     // scratch, and are joined below
     const size_t dos = (degree_order_scratch_bytes(n) + 255) & ~(size_t)255;
+    const size_t scs = simple_check_scratch_bytes(g->m);
     char* d_scr2 = nullptr;
-    if (buf_get_t(&d_scr2, dos + 256) != cudaSuccess) {
+    if (buf_get_t(&d_scr2, dos + scs + 256) != cudaSuccess) {
         buf_put(d_scr);
         return fail(BCM_ERR_OOM, "preprocess scratch");
     }
-    int* d_simple = (int*)(d_scr2 + dos);
+    int* d_simple = (int*)(d_scr2 + dos + scs);
     bcm_status st = BCM_OK;
     int herr = 0;
     bool forked = false;
@@ -501,7 +502,7 @@ bcm_status preprocess(bcm_graph* g, double* ms) {
         forked = true;
         if (cudaMemsetAsync(d_simple, 0, sizeof(int), g->aux) != cudaSuccess ||
             launch_degree_order(g->d_rp, n, g->d_order, d_scr2, dos, g->aux) ||
-            launch_simple_check(g->d_rp, g->d_col, n, d_simple, g->aux) ||
+            launch_simple_check(g->d_rp, g->d_col, n, g->m, d_simple, d_scr2 + dos, g->aux) ||
             cudaMemcpyAsync(&g->h->not_simple, d_simple, sizeof(int), cudaMemcpyDeviceToHost, g->aux) != cudaSuccess) {
             st = fail(BCM_ERR_CUDA, "degree order: %s", cudaGetErrorString(cudaGetLastError()));
             break;

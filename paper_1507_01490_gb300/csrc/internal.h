@@ -115,7 +115,10 @@ int launch_validate(const uint64_t* rp64, const uint32_t* col, uint32_t n, uint6
                     cudaStream_t s);
 int launch_narrow_offsets(const uint64_t* rp64, uint32_t* rp32, uint32_t n, cudaStream_t s);
 // *not_simple |= 1 unless every row is strictly increasing and free of its own vertex
-int launch_simple_check(const uint32_t* rp32, const uint32_t* col, uint32_t n, int* not_simple, cudaStream_t s);
+// (scratch: simple_check_scratch_bytes(m))
+size_t simple_check_scratch_bytes(uint64_t m);
+int launch_simple_check(const uint32_t* rp32, const uint32_t* col, uint32_t n, uint64_t m, int* not_simple,
+                        void* scratch, cudaStream_t s);
 int launch_cc_reach(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t* parent,
                     uint32_t* size, uint32_t* xlo, uint32_t* xhi, int* err, cudaStream_t s);
 int launch_degree_order(const uint32_t* rp, uint32_t n, uint32_t* order, void* scratch,

@@ -30,26 +30,44 @@ __global__ void k_validate(const uint64_t* rp, const uint32_t* col, uint32_t n, 
 }
 
 // *not_simple |= 1 if some row is not strictly increasing or holds its own
-// vertex (a repeated arc or a self-loop).  One warp per row.
-__global__ void k_simple_check(const uint32_t* rp, const uint32_t* col, uint32_t n, int* not_simple) {
-    const uint32_t lane = threadIdx.x & 31;
-    for (size_t u = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5; u < n;
-         u += ((size_t)gridDim.x * blockDim.x) >> 5) {
-        const uint32_t b = rp[u], e = rp[u + 1];
-        bool bad = false;
-        for (uint32_t i = b + lane; i < e; i += 32)
-            bad = bad || col[i] == u || (i > b && col[i - 1] >= col[i]);
-        if (__any_sync(0xffffffffu, bad)) {
-            if (lane == 0) atomicOr(not_simple, 1);
-            return;
+// vertex (a repeated arc or a self-loop).  Two balanced passes: per row,
+// mark where it starts and look for its own vertex by binary search (valid
+// when the row is sorted, which the second pass checks); per arc, compare it
+// with the arc before unless a row starts there.
+__global__ void k_simple_rows(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t* starts,
+                              int* not_simple) {
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < n; u += stride) {
+        uint32_t lo = rp[u], hi = rp[u + 1];
+        if (lo == hi) continue;
+        atomicOr(&starts[lo >> 5], 1u << (lo & 31));
+        while (lo < hi) {
+            const uint32_t mid = lo + (hi - lo) / 2;
+            const uint32_t c = col[mid];
+            if (c == u) { atomicOr(not_simple, 1); break; }
+            if (c < u) lo = mid + 1; else hi = mid;
         }
     }
 }
 
-int launch_simple_check(const uint32_t* rp32, const uint32_t* col, uint32_t n, int* not_simple, cudaStream_t s) {
-    if (n == 0) return 0;
-    k_simple_check<<<blocks_for((size_t)n * 32, 256), 256, 0, s>>>(rp32, col, n, not_simple);
-    note_launch();
+__global__ void k_simple_arcs(const uint32_t* col, uint64_t m, const uint32_t* starts, int* not_simple) {
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x + 1; e < m; e += stride)
+        bad = bad || (!((starts[e >> 5] >> (e & 31)) & 1u) && col[e - 1] >= col[e]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(not_simple, 1);
+}
+
+size_t simple_check_scratch_bytes(uint64_t m) { return (((size_t)m + 31) / 32 * 4 + 255) & ~(size_t)255; }
+
+int launch_simple_check(const uint32_t* rp32, const uint32_t* col, uint32_t n, uint64_t m, int* not_simple,
+                        void* scratch, cudaStream_t s) {
+    if (n == 0 || m == 0) return 0;
+    uint32_t* starts = (uint32_t*)scratch;
+    cudaMemsetAsync(starts, 0, ((size_t)m + 31) / 32 * 4, s);
+    k_simple_rows<<<blocks_for(n, 256), 256, 0, s>>>(rp32, col, n, starts, not_simple);
+    k_simple_arcs<<<blocks_for(m, 256), 256, 0, s>>>(col, m, starts, not_simple);
+    note_launch(2);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -144,14 +162,22 @@ __global__ void k_argmax_degree(const uint32_t* rp, uint32_t n, unsigned long lo
 // first kLink.
 __global__ void k_uf_link_rest(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t* parent,
                                const unsigned long long* best, int* err) {
-    const uint32_t giant = uf_find(parent, 0xffffffffu - (uint32_t)(*best & 0xffffffffull));
+    // the giant component's root, found once per block (every thread
+    // walking to it would read the same words a million times)
+    __shared__ uint32_t s_giant;
+    if (threadIdx.x == 0) s_giant = uf_find(parent, 0xffffffffu - (uint32_t)(*best & 0xffffffffull));
+    __syncthreads();
+    const uint32_t giant = s_giant;
     const uint32_t lane = threadIdx.x & 31;
     size_t warp = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5;
     size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
     for (size_t u = warp; u < n; u += nwarps) {
         uint32_t beg = rp[u], end = rp[u + 1];
         if (end - beg <= kLink) continue;
-        if (uf_find(parent, (uint32_t)u) == giant) continue;
+        // after k_uf_flatten every vertex points at its root: one load tells
+        // a giant vertex (roots only change by later links, which keep a
+        // giant vertex in the giant component)
+        if (vload(&parent[u]) == giant || uf_find(parent, (uint32_t)u) == giant) continue;
         for (uint32_t e = beg + kLink + lane; e < end; e += 32) uf_union(parent, (uint32_t)u, col[e], err);
     }
 }
