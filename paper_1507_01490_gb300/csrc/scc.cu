@@ -59,16 +59,55 @@ __device__ __forceinline__ bool heavy_claim(SccHeavy* H, uint32_t c, uint32_t de
     return true;
 }
 
-__global__ void k_count_in(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t* indeg) {
+// Rows (a vertex's out-arcs) longer than kHeavyEdges, for the per-arc
+// passes below: one warp per row would hold an R-MAT hub's tens of
+// thousands of arcs, so such rows go to a list whose arcs the whole grid
+// shares in a second kernel.  A full list leaves the row with its warp.
+constexpr uint32_t kRowHeavyCap = 4096;
+struct RowHeavy {
+    uint32_t n;
+    uint32_t item[kRowHeavyCap];
+};
+
+__device__ __forceinline__ bool row_claim(RowHeavy* H, uint32_t u, uint32_t deg) {
+    if (!H || deg <= kHeavyEdges) return false;
+    uint32_t slot = 0;
+    if ((threadIdx.x & 31) == 0) slot = atomicAdd(&H->n, 1u);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    if (slot >= kRowHeavyCap) return false;
+    if ((threadIdx.x & 31) == 0) H->item[slot] = u;
+    return true;
+}
+
+// The heavy rows' arcs over the whole grid: f(u, e) for each arc e of row u.
+#define ROW_HEAVY_LOOP(H, rp, u, e)                                                           \
+    const uint32_t hn_ = (H)->n < kRowHeavyCap ? (H)->n : kRowHeavyCap;                      \
+    for (uint32_t h_ = 0; h_ < hn_; ++h_)                                                    \
+        for (uint32_t u = (H)->item[h_], e = (rp)[u] + blockIdx.x * blockDim.x + threadIdx.x; \
+             e < (rp)[u + 1]; e += gridDim.x * blockDim.x)
+
+__global__ void k_count_in(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t* indeg, RowHeavy* H) {
     WARP_PER_ITEM(u, n) {
+        if (row_claim(H, (uint32_t)u, rp[u + 1] - rp[u])) continue;
         for (uint32_t e = rp[u] + lane_; e < rp[u + 1]; e += 32) atomicAdd(&indeg[col[e]], 1u);
     }
 }
 
-__global__ void k_fill_rev(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t* cursor, uint32_t* rcol) {
+__global__ void k_count_in_heavy(const uint32_t* rp, const uint32_t* col, uint32_t* indeg, const RowHeavy* H) {
+    ROW_HEAVY_LOOP(H, rp, u, e) atomicAdd(&indeg[col[e]], 1u);
+}
+
+__global__ void k_fill_rev(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t* cursor, uint32_t* rcol,
+                           RowHeavy* H) {
     WARP_PER_ITEM(u, n) {
+        if (row_claim(H, (uint32_t)u, rp[u + 1] - rp[u])) continue;
         for (uint32_t e = rp[u] + lane_; e < rp[u + 1]; e += 32) rcol[atomicAdd(&cursor[col[e]], 1u)] = (uint32_t)u;
     }
+}
+
+__global__ void k_fill_rev_heavy(const uint32_t* rp, const uint32_t* col, uint32_t* cursor, uint32_t* rcol,
+                                 const RowHeavy* H) {
+    ROW_HEAVY_LOOP(H, rp, u, e) rcol[atomicAdd(&cursor[col[e]], 1u)] = u;
 }
 
 __global__ void k_set_last(uint32_t* a, uint32_t idx, uint32_t v) { a[idx] = v; }
@@ -224,13 +263,22 @@ __global__ void k_label(uint32_t n, const uint32_t* scc, const uint32_t* minv, c
 
 // DAG
 __global__ void k_dag_keys(const uint32_t* rp, const uint32_t* col, uint32_t n, const uint32_t* comp, int b,
-                           unsigned long long* keys) {
+                           unsigned long long* keys, RowHeavy* H) {
     WARP_PER_ITEM(u, n) {
+        if (row_claim(H, (uint32_t)u, rp[u + 1] - rp[u])) continue;
         uint32_t cu = comp[u];
         for (uint32_t e = rp[u] + lane_; e < rp[u + 1]; e += 32) {
             uint32_t cw = comp[col[e]];
             keys[e] = (cu != cw) ? (((unsigned long long)cu << b) | cw) : ~0ull;
         }
+    }
+}
+
+__global__ void k_dag_keys_heavy(const uint32_t* rp, const uint32_t* col, const uint32_t* comp, int b,
+                                 unsigned long long* keys, const RowHeavy* H) {
+    ROW_HEAVY_LOOP(H, rp, u, e) {
+        const uint32_t cu = comp[u], cw = comp[col[e]];
+        keys[e] = (cu != cw) ? (((unsigned long long)cu << b) | cw) : ~0ull;
     }
 }
 
@@ -500,7 +548,7 @@ size_t scc_scratch_bytes(uint32_t n, uint64_t m) {
     s += al(scan_scratch_bytes((m > n ? m : n) + 1));
     s += al(radix_scratch_bytes(m ? m : 1));
     s += nb * 5 + 4096;           // refinement: desc, anc, Wm, two queues
-    s += al(sizeof(SccHeavy));
+    s += al(sizeof(SccHeavy) > sizeof(RowHeavy) ? sizeof(SccHeavy) : sizeof(RowHeavy));
     return s;
 }
 
@@ -538,14 +586,19 @@ int launch_reverse_csr(const uint32_t* rp, const uint32_t* col, uint32_t n, uint
     uint32_t* cursor = (uint32_t*)B.take(((size_t)n + 1) * 4);
     uint32_t* total = (uint32_t*)B.take(64);
     void* scan_scr = B.take(scan_scratch_bytes((size_t)n + 1));
-    if (!cursor || !total || !scan_scr) return -1;
+    RowHeavy* H = (RowHeavy*)B.take(sizeof(RowHeavy));
+    if (!cursor || !total || !scan_scr || !H) return -1;
     const unsigned gw = grid_for((size_t)n * 32);
     cudaMemsetAsync(cursor, 0, ((size_t)n + 1) * 4, s);
-    LAUNCH(k_count_in<<<gw, 256, 0, s>>>(rp, col, n, cursor));
+    cudaMemsetAsync(&H->n, 0, 4, s);
+    LAUNCH(k_count_in<<<gw, 256, 0, s>>>(rp, col, n, cursor, H));
+    LAUNCH(k_count_in_heavy<<<152 * 8, 256, 0, s>>>(rp, col, cursor, H));
     if (exclusive_scan_u32(cursor, rrp, n, total, scan_scr, s)) return -1;
     LAUNCH(k_set_last<<<1, 1, 0, s>>>(rrp, n, (uint32_t)m));
     cudaMemcpyAsync(cursor, rrp, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
-    LAUNCH(k_fill_rev<<<gw, 256, 0, s>>>(rp, col, n, cursor, rcol));
+    cudaMemsetAsync(&H->n, 0, 4, s);
+    LAUNCH(k_fill_rev<<<gw, 256, 0, s>>>(rp, col, n, cursor, rcol, H));
+    LAUNCH(k_fill_rev_heavy<<<152 * 8, 256, 0, s>>>(rp, col, cursor, rcol, H));
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -566,7 +619,7 @@ int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, const uint32_t* r
     uint32_t* minv = (uint32_t*)B.take(((size_t)n + 1) * 4);
     uint32_t* flags = (uint32_t*)B.take(((size_t)(m > n ? m : n) + 1) * 4);
     uint32_t* cnts = (uint32_t*)B.take(256);     // [0] changed, [1],[2] list counts, [3] total, [4] remaining
-    SccHeavy* heavy = (SccHeavy*)B.take(sizeof(SccHeavy));
+    SccHeavy* heavy = (SccHeavy*)B.take(sizeof(SccHeavy) > sizeof(RowHeavy) ? sizeof(SccHeavy) : sizeof(RowHeavy));
     if (!heavy) return -1;
     unsigned long long* best = (unsigned long long*)B.take(64);
     void* scan_scr = B.take(scan_scratch_bytes((m > n ? m : n) + 1));
@@ -682,7 +735,10 @@ int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, const uint32_t* r
         pred = pred_buf;
         void* rscr = B.take(radix_scratch_bytes(m));
         if (!keys || !ktmp || !dsrc || !ddst || !rscr) return -1;
-        LAUNCH(k_dag_keys<<<gw, 256, 0, s>>>(rp, col, n, comp, b, keys));
+        RowHeavy* RH = (RowHeavy*)heavy;   // the SCC heavy area is free here and at least as large
+        cudaMemsetAsync(&RH->n, 0, 4, s);
+        LAUNCH(k_dag_keys<<<gw, 256, 0, s>>>(rp, col, n, comp, b, keys, RH));
+        LAUNCH(k_dag_keys_heavy<<<152 * 8, 256, 0, s>>>(rp, col, comp, b, keys, RH));
         bool in_tmp = false;
         if (radix_sort_u64((uint64_t*)keys, (uint64_t*)ktmp, m, 2 * b, rscr, s, &in_tmp)) return -1;
         unsigned long long* sk = in_tmp ? ktmp : keys;
