@@ -639,12 +639,13 @@ WaveParams base_params(bcm_graph* g, const Cfg& c) {
 // it must move at minimum (word granularity, no cache or sector effects).
 //   started source            20 B  order entry, row_ptr pair, x_lo/x_hi
 //   frontier word expanded    28 B  list entry, F word read and clear, row_ptr pair
+//     (of a pulled level)     12 B  list entry, F word clear (its reads are the arcs')
 //   (arc, frontier word)      12 B  col entry, vis word
 //   new frontier word         32 B  vis and F-next atomics, row_ptr pair, list and log entries
 //   cleared word              28 B  log entry, vis/F/F' stores
 uint64_t wave_alg_bytes(const unsigned long long* w, uint64_t sources) {
-    return 20ull * sources + 28ull * w[ST_ENTRIES] + 12ull * w[ST_ARCWORDS] + 32ull * w[ST_DISCWORDS] +
-           28ull * w[ST_CLEARED];
+    return 20ull * sources + 28ull * (w[ST_ENTRIES] - w[ST_PULLENTRIES]) + 12ull * w[ST_PULLENTRIES] +
+           12ull * w[ST_ARCWORDS] + 32ull * w[ST_DISCWORDS] + 28ull * w[ST_CLEARED];
 }
 
 void fill_stats(bcm_stats* s, const unsigned long long* st, uint64_t launches, double kms, double pms, double tms) {

@@ -23,6 +23,7 @@ enum Stat {
     ST_DISCWORDS,       // frontier words created (first discovery in a level)
     ST_CLEARED,         // vertex words cleared at wave ends
     ST_DEFERRED,        // sources a per-CTA wave handed to the grid-wide pass
+    ST_PULLENTRIES,     // frontier words of pulled levels (also in ST_ENTRIES)
     ST_COUNT
 };
 

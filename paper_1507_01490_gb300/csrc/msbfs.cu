@@ -103,8 +103,9 @@ __device__ inline void flush_stats(const LocalStats& s, const BlockStats& b, uns
         if ((threadIdx.x & 31) == 0 && x) atomicAdd(&g[idx[i]], x);
     }
     if (threadIdx.x == 0) {
-        const int rare[7] = {ST_COMPLETED, ST_CUT, ST_WAVES, ST_LEVELS, ST_CLEARED, ST_MAXLEVEL, ST_DEFERRED};
-        for (int i = 0; i < 7; ++i) {
+        const int rare[9] = {ST_COMPLETED, ST_CUT,    ST_WAVES,   ST_LEVELS,     ST_CLEARED,
+                             ST_MAXLEVEL,  ST_DEFERRED, ST_ENTRIES, ST_PULLENTRIES};
+        for (int i = 0; i < 9; ++i) {
             u64 x = b.v[rare[i]];
             if (!x) continue;
             if (rare[i] == ST_MAXLEVEL) atomicMax(&g[rare[i]], x);
@@ -523,12 +524,19 @@ __device__ __noinline__ void expand_heavy(const GraphDev& G, const HeavyEntry* H
 // and the same early stop, so a hub's in-list does not hold one thread for
 // thousands of dependent loads.  vis/F-next of x are written by x's own
 // thread, without atomics.  The frontier words themselves are cleared
-// afterwards (pull_retire), once no thread can still be reading them.
+// afterwards (pull_clear), once no thread can still be reading them.
 constexpr u32 kPullSerial = 32;
 #ifndef BCM_PULL_UNROLL
 #define BCM_PULL_UNROLL 2
 #endif
 constexpr int kPullUnroll = BCM_PULL_UNROLL;   // in-neighbours per step of a thread's scan
+#ifndef BCM_PULL_PREFETCH
+#define BCM_PULL_PREFETCH 0
+#endif
+#ifndef BCM_PULL_COOP
+#define BCM_PULL_COOP 4
+#endif
+constexpr int kPullCoop = BCM_PULL_COOP;   // in-neighbours per thread and step of a warp's scan
 
 template <int W>
 __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32* s_alive32, u64* vis, u64* Fnext,
@@ -548,7 +556,7 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
         const u32 x = x0 + lane;
         u64 pend[W], acc[W], v0[W];
         bool any = false;
-        u32 b = 0, e = 0;
+        u32 b = 0, e = 0, dx = 0;
 #pragma unroll
         for (int g = 0; g < W; ++g) { pend[g] = 0; acc[g] = 0; v0[g] = 0; }
         if (x < G.n) {
@@ -558,9 +566,10 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
                 pend[g] = alive[g] & ~v0[g];
                 any = any || pend[g] != 0;
             }
-            if (any) {
+            if (any) {   // in-list bounds, and the out-degree used if x is reached
                 b = __ldg(&G.rrp[x]);
                 e = __ldg(&G.rrp[x + 1]);
+                dx = __ldg(&G.rp[x + 1]) - __ldg(&G.rp[x]);
             }
         }
         const bool coop = any && e - b > kPullSerial;
@@ -569,10 +578,26 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
             // their frontier words, are loaded together (independent loads
             // in flight), and the early stop is checked once per step
             u32 i = b;
+#if BCM_PULL_PREFETCH
+            // the next step's col entries are loaded before this step's
+            // frontier words are used, so the two latencies overlap
+            u32 un[kPullUnroll];
+#pragma unroll
+            for (int j = 0; j < kPullUnroll; ++j) un[j] = i + j < e ? __ldg(&G.rcol[i + j]) : 0xffffffffu;
+#endif
             while (i < e) {
                 u32 u[kPullUnroll];
+#if BCM_PULL_PREFETCH
+#pragma unroll
+                for (int j = 0; j < kPullUnroll; ++j) {
+                    u[j] = un[j];
+                    const u32 a = i + kPullUnroll + j;
+                    un[j] = a < e ? __ldg(&G.rcol[a]) : 0xffffffffu;
+                }
+#else
 #pragma unroll
                 for (int j = 0; j < kPullUnroll; ++j) u[j] = i + j < e ? __ldg(&G.rcol[i + j]) : 0xffffffffu;
+#endif
                 // in-neighbours outside the current frontier have no frontier words
 #pragma unroll
                 for (int j = 0; j < kPullUnroll; ++j)
@@ -608,17 +633,29 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
                 cp[g] = ((u64)hi << 32) | lo;
                 ca[g] = 0;
             }
+            // kPullCoop arcs per thread and step: a hub's in-list is the
+            // level's longest chain of dependent loads, so each step puts
+            // kPullCoop independent col / bitmap / frontier loads in flight
             u32 i = cb;
-            for (; i < ce; i += 32) {
+            for (; i < ce; i += 32 * kPullCoop) {
+                u32 u[kPullCoop];
+#pragma unroll
+                for (int j = 0; j < kPullCoop; ++j) {
+                    const u32 a = i + 32 * j + lane;
+                    u[j] = a < ce ? __ldg(&G.rcol[a]) : 0xffffffffu;
+                }
+#pragma unroll
+                for (int j = 0; j < kPullCoop; ++j)
+                    if (u[j] != 0xffffffffu && !((__ldcg(&bmc[u[j] >> 5]) >> (u[j] & 31)) & 1u)) u[j] = 0xffffffffu;
                 u64 f[W];
 #pragma unroll
-                for (int g = 0; g < W; ++g) f[g] = 0;
-                if (i + lane < ce) {
-                    const u32 u = __ldg(&G.rcol[i + lane]);
-                    if ((__ldcg(&bmc[u >> 5]) >> (u & 31)) & 1u) {
+                for (int g = 0; g < W; ++g) {
+                    f[g] = 0;
+                    if (cp[g] & ~ca[g]) {
 #pragma unroll
-                        for (int g = 0; g < W; ++g)
-                            if (cp[g] & ~ca[g]) f[g] = __ldcg(&Fcur[ri(u * W + g)]) & cp[g];
+                        for (int j = 0; j < kPullCoop; ++j)
+                            if (u[j] != 0xffffffffu) f[g] |= __ldcg(&Fcur[ri(u[j] * W + g)]);
+                        f[g] &= cp[g];
                     }
                 }
                 bool done = true;
@@ -629,7 +666,7 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
                     ca[g] |= ((u64)hi << 32) | lo;
                     done = done && !(cp[g] & ~ca[g]);
                 }
-                if (done) { i = (i + 32 < ce) ? i + 32 : ce; break; }
+                if (done) { i = (i + 32 * kPullCoop < ce) ? i + 32 * kPullCoop : ce; break; }
             }
             if (i > ce) i = ce;
             if (lane == (u32)l0) {
@@ -643,7 +680,7 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
 #pragma unroll
         for (int g = 0; g < W; ++g) nb[g] = 0;
         if (any) {
-            degp = __ldg(&G.rp[x + 1]) - __ldg(&G.rp[x]) - foot;
+            degp = dx - foot;
 #pragma unroll
             for (int g = 0; g < W; ++g) {
                 nb[g] = acc[g] & pend[g];
@@ -674,21 +711,20 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
     }
 }
 
-// After a pulled level: clear the frontier words just consumed and count the
-// arcs a push would have scanned for them (m_vis is the push-equivalent
-// count whichever direction ran).
-template <int W>
-__device__ inline void pull_retire(const GraphDev& G, const u32* list, u32 cnt, u64* Fcur, const u32* s_alive32,
-                                   u32 gtid, u32 gthreads, LocalStats& st) {
-    for (u32 i = gtid; i < cnt; i += gthreads) {
-        const u32 word = __ldcg(&list[i]);
-        const u32 u = word / W, g = word - u * W;
-        u64 F = __ldcg(&Fcur[ri(word)]);
-        Fcur[ri(word)] = 0;
-        F &= ((u64)s_alive32[2 * g + 1] << 32) | s_alive32[2 * g];
-        st.entries++;
-        if (F) st.mvis += (u64)__popcll(F) * (__ldg(&G.rp[u + 1]) - __ldg(&G.rp[u]));
+// After a pulled level: clear the frontier words just consumed.  Four list
+// entries per thread are loaded before any of their stores, so the loads
+// are in flight together (the stores could alias the list as far as the
+// compiler knows).
+__device__ inline void pull_clear(const u32* list, u32 cnt, u64* Fcur, u32 gtid, u32 gthreads) {
+    u64 i = gtid;
+    for (; i + 3ull * gthreads < cnt; i += 4ull * gthreads) {
+        u32 w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) w[j] = __ldcg(&list[i + (u64)j * gthreads]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Fcur[ri(w[j])] = 0;
     }
+    for (; i < cnt; i += gthreads) Fcur[ri(__ldcg(&list[i]))] = 0;
 }
 
 // Completed lanes: exhaustive runs write (f, r) by vertex id; top-k runs
@@ -1272,8 +1308,20 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
             if (pulled) {   // every block is past the pull: retire the frontier words
                 // (the count read at the level's start: the leader resets
                 // glist_n[cur] below while slower blocks may still be here)
-                pull_retire<W>(G, S.list[cur], level_cnt, S.F[cur], s_alive32,
-                               blockIdx.x * THREADS + tid, gridDim.x * THREADS, st);
+                pull_clear(S.list[cur], level_cnt, S.F[cur], blockIdx.x * THREADS + tid, gridDim.x * THREADS);
+                // the arcs a push would have scanned (m_vis counts those
+                // whichever direction ran): a live lane's frontier out-arcs
+                // are its gamma-tilde sum plus the footnote's 1 per vertex,
+                // and its frontier count is still in the previous level's
+                // counters (cleared at this level's end)
+                if (leader) {
+                    if (tid < L && ((s_alive32[tid >> 5] >> lane) & 1u))
+                        st.mvis += (u64)s_gt[tid] + (u64)p.footnote * vload(&p.gcnt[(par ^ 1) * 512 + tid]);
+                    if (tid == 0) {
+                        bstat_add(s_bst, ST_ENTRIES, level_cnt);
+                        bstat_add(s_bst, ST_PULLENTRIES, level_cnt);
+                    }
+                }
                 pulled = false;
                 __syncthreads();
             }

@@ -114,6 +114,28 @@ def test_topk_kernel_choices_and_footnote(B, gen, orc):
                         assert np.array_equal(ids, exp) and np.array_equal(gf, f[exp]), (g.name, k, gl, pd)
 
 
+def test_exhaustive_m_vis_is_the_push_count_either_way(B, gen):
+    """m_vis of an exhaustive run is, summed over sources v, the out-degree
+    of every vertex v reaches (v included): the arcs a push scans.  Pushed
+    levels count it entry by entry, pulled ones from the lanes' counters;
+    every direction choice, grid width and footnote setting must give this
+    closed form (reachability from scipy's BFS)."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import breadth_first_order
+    graphs = undirected_graphs(gen)[::2] + [gen.gnp(300, 0.01, seed=7, directed=True), gen.rmat(10, 8, seed=9),
+                                            gen.with_self_loops_and_repeats(gen.ba(300, 3, seed=2), seed=3)]
+    for g in graphs:
+        deg = g.degrees()
+        a = csr_matrix((np.ones(g.m), g.col.astype(np.int64), g.row_ptr.astype(np.int64)), shape=(g.n, g.n))
+        exp = sum(int(deg[breadth_first_order(a, v, directed=True, return_predecessors=False)].sum())
+                  for v in range(g.n))
+        with B.BcmGraph.from_graph(g) as h:
+            for gl in (64, 128, 256):
+                for pd, flags in ((1 << 30, 0), (1 << 30, B.BCM_NO_FOOTNOTE), (0, B.BCM_NO_PULL), (0, 0)):
+                    _, _, st = h.farness_all(grid_lanes=gl, pull_div=pd, flags=flags)
+                    assert st["m_vis"] == exp, (g.name, gl, pd, flags, st["m_vis"], exp)
+
+
 def test_deferred_waves_rerun_exactly(B, gen, orc):
     """Per-CTA waves that hand their sources to the second grid-wide pass
     (forced with tiny defer_words) give the exact top-k: a deferred source is
