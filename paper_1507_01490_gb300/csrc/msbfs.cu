@@ -219,6 +219,10 @@ __device__ __forceinline__ void push_next(u64* Fnext, Push& q, u64 old, u32 foot
 // bit lanes t and t+32 of the word group being walked, so the shared-memory
 // updates are one per thread and bit lane, with no two threads on one
 // counter.
+#ifndef BCM_COUNT_LOOP
+#define BCM_COUNT_LOOP 8
+#endif
+constexpr int kCountLoop = BCM_COUNT_LOOP;   // at most this many reaching lanes: count by the loop
 __device__ __forceinline__ void warp_count(u64 nb, u32 degp, u32 g, u32* cg, u32* cs) {
     const u32 lane = threadIdx.x & 31;
     u32 active = __ballot_sync(0xffffffffu, nb != 0);
@@ -239,6 +243,46 @@ __device__ __forceinline__ void warp_count(u64 nb, u32 degp, u32 g, u32* cg, u32
         if (c_lo) { atomicAdd(&cg[g0 * 64 + lane], c_lo); atomicAdd(&cs[g0 * 64 + lane], s_lo); }
         if (c_hi) { atomicAdd(&cg[g0 * 64 + 32 + lane], c_hi); atomicAdd(&cs[g0 * 64 + 32 + lane], s_hi); }
     }
+}
+
+// 32x32 bit transpose across the warp: lane i passes row i (bit j = entry
+// (i, j)) and gets column i back (bit j = entry (j, i)).  Five rounds of
+// swapping off-diagonal blocks of halving size.
+__device__ __forceinline__ u32 warp_transpose32(u32 x) {
+    const u32 lane = threadIdx.x & 31;
+    const u32 masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+        const int sh = 16 >> r;
+        const u32 m = masks[r];
+        const u32 y = __shfl_xor_sync(0xffffffffu, x, sh);
+        x = (lane & sh) ? ((x & ~m) | ((y >> sh) & m)) : ((x & m) | ((y & m) << sh));
+    }
+    return x;
+}
+
+// warp_count for a warp whose lanes all hold word g: with many lanes
+// reaching something, the counts come from the transposed bit matrix (lane
+// b's column word marks the lanes whose nb has bit b) and the degree sums
+// from its AND with each bit plane of degp; with few, warp_count's loop.
+__device__ __forceinline__ void warp_count_word(u64 nb, u32 degp, u32 g, u32* cg, u32* cs) {
+    const u32 lane = threadIdx.x & 31;
+    const u32 active = __ballot_sync(0xffffffffu, nb != 0);
+    if (__popc(active) <= kCountLoop) {
+        warp_count(nb, degp, g, cg, cs);
+        return;
+    }
+    const u32 lo = warp_transpose32((u32)nb), hi = warp_transpose32((u32)(nb >> 32));
+    const u32 dmax = __reduce_max_sync(0xffffffffu, nb ? degp : 0u);
+    u32 s_lo = 0, s_hi = 0;
+    for (int k = 0; k < 32 && (dmax >> k); ++k) {
+        const u32 plane = __ballot_sync(0xffffffffu, (degp >> k) & 1u);
+        s_lo += (u32)__popc(lo & plane) << k;
+        s_hi += (u32)__popc(hi & plane) << k;
+    }
+    const u32 c_lo = __popc(lo), c_hi = __popc(hi);
+    if (c_lo) { atomicAdd(&cg[g * 64 + lane], c_lo); atomicAdd(&cs[g * 64 + lane], s_lo); }
+    if (c_hi) { atomicAdd(&cg[g * 64 + 32 + lane], c_hi); atomicAdd(&cs[g * 64 + 32 + lane], s_hi); }
 }
 
 __device__ __forceinline__ void push_finish(const Push& q, u32* cg, u32* cs, WarpQueue& nq, WarpQueue& lq) {
@@ -530,9 +574,6 @@ constexpr u32 kPullSerial = 32;
 #define BCM_PULL_UNROLL 2
 #endif
 constexpr int kPullUnroll = BCM_PULL_UNROLL;   // in-neighbours per step of a thread's scan
-#ifndef BCM_PULL_PREFETCH
-#define BCM_PULL_PREFETCH 0
-#endif
 #ifndef BCM_PULL_COOP
 #define BCM_PULL_COOP 4
 #endif
@@ -560,16 +601,17 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
 #pragma unroll
         for (int g = 0; g < W; ++g) { pend[g] = 0; acc[g] = 0; v0[g] = 0; }
         if (x < G.n) {
+            // in-list bounds and the out-degree used if x is reached, loaded
+            // with the vis words rather than after them (32 consecutive
+            // vertices: a few lines per warp)
+            b = __ldg(&G.rrp[x]);
+            e = __ldg(&G.rrp[x + 1]);
+            dx = __ldg(&G.rp[x + 1]) - __ldg(&G.rp[x]);
 #pragma unroll
             for (int g = 0; g < W; ++g) {
                 v0[g] = __ldcg(&vis[ri(x * W + g)]);
                 pend[g] = alive[g] & ~v0[g];
                 any = any || pend[g] != 0;
-            }
-            if (any) {   // in-list bounds, and the out-degree used if x is reached
-                b = __ldg(&G.rrp[x]);
-                e = __ldg(&G.rrp[x + 1]);
-                dx = __ldg(&G.rp[x + 1]) - __ldg(&G.rp[x]);
             }
         }
         const bool coop = any && e - b > kPullSerial;
@@ -578,26 +620,10 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
             // their frontier words, are loaded together (independent loads
             // in flight), and the early stop is checked once per step
             u32 i = b;
-#if BCM_PULL_PREFETCH
-            // the next step's col entries are loaded before this step's
-            // frontier words are used, so the two latencies overlap
-            u32 un[kPullUnroll];
-#pragma unroll
-            for (int j = 0; j < kPullUnroll; ++j) un[j] = i + j < e ? __ldg(&G.rcol[i + j]) : 0xffffffffu;
-#endif
             while (i < e) {
                 u32 u[kPullUnroll];
-#if BCM_PULL_PREFETCH
-#pragma unroll
-                for (int j = 0; j < kPullUnroll; ++j) {
-                    u[j] = un[j];
-                    const u32 a = i + kPullUnroll + j;
-                    un[j] = a < e ? __ldg(&G.rcol[a]) : 0xffffffffu;
-                }
-#else
 #pragma unroll
                 for (int j = 0; j < kPullUnroll; ++j) u[j] = i + j < e ? __ldg(&G.rcol[i + j]) : 0xffffffffu;
-#endif
                 // in-neighbours outside the current frontier have no frontier words
 #pragma unroll
                 for (int j = 0; j < kPullUnroll; ++j)
@@ -704,7 +730,7 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
         for (int g = 0; g < W; ++g) {
             nq.reserve(32);
             lq.reserve(32);
-            warp_count(nb[g], degp, (u32)g, cg, cs);
+            warp_count_word(nb[g], degp, (u32)g, cg, cs);
             nq.push(nb[g] != 0, x * W + g);
             lq.push(nb[g] != 0 && v0[g] == 0, x * W + g);
         }
@@ -886,10 +912,14 @@ __global__ void __launch_bounds__(256) k_prefilter(WaveParams p, u32* out, u32* 
         // level 1: gamma~_2 = sum over N(v) of deg(u) - footnote
         u64 g2 = 0;
         const bool serial = !done && deg <= 32;
-        if (serial) {
-            for (u32 i = 0; i < deg; ++i) {
-                const u32 u = __ldg(&G.col[b + i]);
-                g2 += __ldg(&G.rp[u + 1]) - __ldg(&G.rp[u]) - p.footnote;
+        if (serial) {   // four neighbours per step: their col entries, then their degrees, in flight together
+            for (u32 i = 0; i < deg; i += 4) {
+                u32 u[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) u[j] = i + j < deg ? __ldg(&G.col[b + i + j]) : 0xffffffffu;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (u[j] != 0xffffffffu) g2 += __ldg(&G.rp[u[j] + 1]) - __ldg(&G.rp[u[j]]) - p.footnote;
             }
         }
         u32 big = __ballot_sync(0xffffffffu, !done && !serial);

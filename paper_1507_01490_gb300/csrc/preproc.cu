@@ -95,8 +95,11 @@ int launch_narrow_offsets(const uint64_t* rp64, uint32_t* rp32, uint32_t n, cuda
 // points to a smaller id and each component's root is its smallest vertex.
 __device__ __forceinline__ uint32_t uf_find(uint32_t* parent, uint32_t x) {
     for (;;) {
+        // vertex 0 is a root for good (nothing is smaller): its entry, where
+        // most walks would end, is never read
+        if (x == 0) return 0;
         uint32_t p = vload(&parent[x]);
-        if (p == x) return x;
+        if (p == x || p == 0) return p;
         uint32_t gp = vload(&parent[p]);
         if (gp != p) vstore(&parent[x], gp);   // path halving; gp is still an ancestor
         x = gp;
@@ -204,12 +207,20 @@ constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
 __global__ void k_uf_reach(uint32_t* parent, const uint32_t* size, uint32_t n, uint32_t* xlo, uint32_t* xhi) {
     size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += stride) {
-        uint32_t r = uf_find(parent, (uint32_t)v);
-        parent[v] = r;
-        uint32_t sz = size[r];
-        xlo[v] = sz;
-        xhi[v] = sz;
+    for (size_t v0 = (blockIdx.x * (size_t)blockDim.x) + (threadIdx.x & ~31u); v0 < n; v0 += stride) {
+        const size_t v = v0 + (threadIdx.x & 31);
+        const uint32_t r = v < n ? uf_find(parent, (uint32_t)v) : 0xffffffffu;
+        // lanes of one component read its size once (most share the giant one)
+        const uint32_t peers = __match_any_sync(0xffffffffu, r);
+        const int first = __ffs(peers) - 1;
+        uint32_t sz = 0;
+        if (r != 0xffffffffu && (threadIdx.x & 31) == (uint32_t)first) sz = size[r];
+        sz = __shfl_sync(0xffffffffu, sz, first);
+        if (v < n) {
+            parent[v] = r;
+            xlo[v] = sz;
+            xhi[v] = sz;
+        }
     }
 }
 
