@@ -881,9 +881,12 @@ __global__ void __launch_bounds__(256) k_prefilter(WaveParams p, u32* out, u32* 
     const size_t gw = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5;
     const size_t gnw = ((size_t)gridDim.x * blockDim.x) >> 5;
     // 32 sources per warp step, one per thread; a source with more than 32
-    // neighbours has its degree sum taken by the whole warp afterwards
-    for (size_t pos0 = s_begin + gw * 32; pos0 < p.n_end; pos0 += gnw * 32) {
-        const size_t pos = pos0 + lane;
+    // neighbours has its degree sum taken by the whole warp afterwards.  In
+    // each pass over gnw*32 positions, lane l of warp w takes position
+    // l*gnw + w: the sources come by degree, so consecutive positions would
+    // give the first warps all the hubs (and the step's critical path)
+    for (size_t base = s_begin; base < p.n_end; base += gnw * 32) {
+        const size_t pos = base + lane * gnw + gw;
         const bool have = pos < p.n_end;
         u32 v = 0, b = 0, deg = 0, xlo = 0, xhi = 0;
         bool cut = false, done = !have || !s_thr.valid;

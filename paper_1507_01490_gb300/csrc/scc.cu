@@ -262,23 +262,48 @@ __global__ void k_label(uint32_t n, const uint32_t* scc, const uint32_t* minv, c
 }
 
 // DAG
+// The key (comp[u] << b | comp[w]) of an arc between two SCCs, appended to
+// keys (in no particular order: they are sorted next); arcs inside an SCC,
+// most of a graph with a giant SCC, are left out of the sort.
+__device__ __forceinline__ void dag_key(const uint32_t* col, const uint32_t* comp, uint32_t cu, int b, uint32_t e,
+                                        bool valid, unsigned long long* keys, uint32_t* kcnt) {
+    unsigned long long key = 0;
+    bool inter = false;
+    if (valid) {
+        const uint32_t cw = comp[col[e]];
+        inter = cu != cw;
+        key = ((unsigned long long)cu << b) | cw;
+    }
+    const uint32_t m = __ballot_sync(0xffffffffu, inter);
+    if (m == 0) return;
+    const int leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if ((int)(threadIdx.x & 31) == leader) base = atomicAdd(kcnt, (uint32_t)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (inter) keys[base + __popc(m & ((1u << (threadIdx.x & 31)) - 1u))] = key;
+}
+
 __global__ void k_dag_keys(const uint32_t* rp, const uint32_t* col, uint32_t n, const uint32_t* comp, int b,
-                           unsigned long long* keys, RowHeavy* H) {
+                           unsigned long long* keys, uint32_t* kcnt, RowHeavy* H) {
     WARP_PER_ITEM(u, n) {
         if (row_claim(H, (uint32_t)u, rp[u + 1] - rp[u])) continue;
-        uint32_t cu = comp[u];
-        for (uint32_t e = rp[u] + lane_; e < rp[u + 1]; e += 32) {
-            uint32_t cw = comp[col[e]];
-            keys[e] = (cu != cw) ? (((unsigned long long)cu << b) | cw) : ~0ull;
-        }
+        const uint32_t cu = comp[u], end = rp[u + 1];
+        for (uint32_t e0 = rp[u]; e0 < end; e0 += 32)
+            dag_key(col, comp, cu, b, e0 + lane_, e0 + lane_ < end, keys, kcnt);
     }
 }
 
+// the rows row_claim listed, 32 arcs per warp at a time over the whole grid
 __global__ void k_dag_keys_heavy(const uint32_t* rp, const uint32_t* col, const uint32_t* comp, int b,
-                                 unsigned long long* keys, const RowHeavy* H) {
-    ROW_HEAVY_LOOP(H, rp, u, e) {
-        const uint32_t cu = comp[u], cw = comp[col[e]];
-        keys[e] = (cu != cw) ? (((unsigned long long)cu << b) | cw) : ~0ull;
+                                 unsigned long long* keys, uint32_t* kcnt, const RowHeavy* H) {
+    const uint32_t hn = H->n < kRowHeavyCap ? H->n : kRowHeavyCap;
+    const uint32_t lane = threadIdx.x & 31;
+    const size_t warp = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5;
+    const size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
+    for (uint32_t h = 0; h < hn; ++h) {
+        const uint32_t u = H->item[h], beg = rp[u], end = rp[u + 1], cu = comp[u];
+        for (size_t e0 = beg + warp * 32; e0 < end; e0 += nwarps * 32)
+            dag_key(col, comp, cu, b, (uint32_t)(e0 + lane), e0 + lane < end, keys, kcnt);
     }
 }
 
@@ -618,7 +643,8 @@ int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, const uint32_t* r
     uint32_t* L1 = (uint32_t*)B.take(((size_t)n + 1) * 4);
     uint32_t* minv = (uint32_t*)B.take(((size_t)n + 1) * 4);
     uint32_t* flags = (uint32_t*)B.take(((size_t)(m > n ? m : n) + 1) * 4);
-    uint32_t* cnts = (uint32_t*)B.take(256);     // [0] changed, [1],[2] list counts, [3] total, [4] remaining
+    uint32_t* cnts = (uint32_t*)B.take(256);     // [0] changed, [1],[2] list counts, [3] total, [4] remaining,
+                                                 // [5] arcs between SCCs
     SccHeavy* heavy = (SccHeavy*)B.take(sizeof(SccHeavy) > sizeof(RowHeavy) ? sizeof(SccHeavy) : sizeof(RowHeavy));
     if (!heavy) return -1;
     unsigned long long* best = (unsigned long long*)B.take(64);
@@ -737,16 +763,21 @@ int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, const uint32_t* r
         if (!keys || !ktmp || !dsrc || !ddst || !rscr) return -1;
         RowHeavy* RH = (RowHeavy*)heavy;   // the SCC heavy area is free here and at least as large
         cudaMemsetAsync(&RH->n, 0, 4, s);
-        LAUNCH(k_dag_keys<<<gw, 256, 0, s>>>(rp, col, n, comp, b, keys, RH));
-        LAUNCH(k_dag_keys_heavy<<<152 * 8, 256, 0, s>>>(rp, col, comp, b, keys, RH));
-        bool in_tmp = false;
-        if (radix_sort_u64((uint64_t*)keys, (uint64_t*)ktmp, m, 2 * b, rscr, s, &in_tmp)) return -1;
-        unsigned long long* sk = in_tmp ? ktmp : keys;
-        LAUNCH(k_unique_flags<<<grid_for(m), 256, 0, s>>>(sk, m, flags));
-        uint32_t* pos = (uint32_t*)(in_tmp ? (void*)keys : (void*)ktmp);   // the other key buffer as scratch
-        if (exclusive_scan_u32(flags, pos, m, &cnts[3], scan_scr, s)) return -1;
-        LAUNCH(k_unique_scatter<<<grid_for(m), 256, 0, s>>>(sk, m, flags, pos, b, dsrc, ddst));
-        if (read_u32(&cnts[3], &ndag, s)) return -1;
+        cudaMemsetAsync(&cnts[5], 0, 4, s);
+        LAUNCH(k_dag_keys<<<gw, 256, 0, s>>>(rp, col, n, comp, b, keys, &cnts[5], RH));
+        LAUNCH(k_dag_keys_heavy<<<152 * 8, 256, 0, s>>>(rp, col, comp, b, keys, &cnts[5], RH));
+        uint32_t mk = 0;   // arcs between SCCs
+        if (read_u32(&cnts[5], &mk, s)) return -1;
+        if (mk) {
+            bool in_tmp = false;
+            if (radix_sort_u64((uint64_t*)keys, (uint64_t*)ktmp, mk, 2 * b, rscr, s, &in_tmp)) return -1;
+            unsigned long long* sk = in_tmp ? ktmp : keys;
+            LAUNCH(k_unique_flags<<<grid_for(mk), 256, 0, s>>>(sk, mk, flags));
+            uint32_t* pos = (uint32_t*)(in_tmp ? (void*)keys : (void*)ktmp);   // the other key buffer as scratch
+            if (exclusive_scan_u32(flags, pos, mk, &cnts[3], scan_scr, s)) return -1;
+            LAUNCH(k_unique_scatter<<<grid_for(mk), 256, 0, s>>>(sk, mk, flags, pos, b, dsrc, ddst));
+            if (read_u32(&cnts[3], &ndag, s)) return -1;
+        }
     }
     // component sizes; DAG CSR (successors) and predecessor lists
     cudaMemsetAsync(wsz, 0, ((size_t)nscc + 1) * 4, s);
