@@ -21,6 +21,12 @@
 namespace bcm {
 
 static constexpr uint32_t UNSET = 0xffffffffu;
+// a reachability level is pulled once its frontier holds n / kReachPullDiv vertices
+#ifndef BCM_REACH_PULL_DIV
+#define BCM_REACH_PULL_DIV 64
+#endif
+static constexpr uint32_t kReachPullDiv = BCM_REACH_PULL_DIV;
+static inline bool reach_pull(uint32_t fsize, uint32_t n) { return kReachPullDiv && fsize >= n / kReachPullDiv; }
 
 static inline unsigned grid_for(size_t work, int threads = 256) {
     size_t b = (work + threads - 1) / threads;
@@ -193,6 +199,35 @@ __global__ void k_reach_heavy(const uint32_t* rp, const uint32_t* col, uint32_t*
             const size_t a = b + j * 32 + lane_;
             reach_arc(col, (uint32_t)a, a < e, cu, next, ncnt, mark, scc, color, same_color);
         }
+    }
+}
+
+// The same level by pull (direction-optimising BFS): every unassigned,
+// unmarked vertex v looks through its arcs of the other direction for a
+// marked unassigned vertex (of its colour) and stops at the first.  For
+// the reachable set a marked vertex of any earlier level serves as well as
+// one of the last, so marks need no level; each v is marked by its own
+// thread only.  Used when the frontier is a large part of the graph.
+__global__ void k_reach_pull(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t* next, uint32_t* ncnt,
+                             uint32_t* mark, const uint32_t* scc, const uint32_t* color, int same_color) {
+    const uint32_t lane = threadIdx.x & 31;
+    for (size_t v0 = blockIdx.x * (size_t)blockDim.x + (threadIdx.x & ~31u); v0 < n;
+         v0 += (size_t)gridDim.x * blockDim.x) {
+        const size_t v = v0 + lane;
+        bool app = false;
+        if (v < n && scc[v] == UNSET && vload(&mark[v]) == 0) {
+            const uint32_t cv = same_color ? color[v] : 0u;
+            const uint32_t end = rp[v + 1];
+            for (uint32_t e = rp[v]; e < end; ++e) {
+                const uint32_t u = col[e];
+                if (vload(&mark[u]) != 0 && scc[u] == UNSET && (!same_color || color[u] == cv)) {
+                    app = true;
+                    break;
+                }
+            }
+            if (app) vstore(&mark[v], 1u);
+        }
+        warp_append(app, (uint32_t)v, next, ncnt);
     }
 }
 
@@ -677,15 +712,22 @@ int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, const uint32_t* r
             cudaMemsetAsync(mark, 0, (size_t)n * 4, s);
             LAUNCH(k_seed_mark<<<1, 1, 0, s>>>(pivot, mark, L0, &cnts[1]));
             uint32_t *cur = L0, *nxt = L1, *cc = &cnts[1], *nc = &cnts[2];
+            uint32_t fsize = 1;   // frontier size: the pivot
             for (;;) {
                 cudaMemsetAsync(nc, 0, 4, s);
-                cudaMemsetAsync(&heavy->n, 0, 4, s);
-                LAUNCH(k_reach<<<gw, 256, 0, s>>>(dir ? rrp : rp, dir ? rcol : col, cur, cc, nxt, nc, mark, sccv,
-                                                  color, 0, heavy));
-                LAUNCH(k_reach_heavy<<<152 * 8, 256, 0, s>>>(dir ? rrp : rp, dir ? rcol : col, nxt, nc, mark, sccv,
-                                                             color, 0, heavy));
+                if (reach_pull(fsize, n)) {
+                    LAUNCH(k_reach_pull<<<gv, 256, 0, s>>>(dir ? rp : rrp, dir ? col : rcol, n, nxt, nc, mark, sccv,
+                                                           color, 0));
+                } else {
+                    cudaMemsetAsync(&heavy->n, 0, 4, s);
+                    LAUNCH(k_reach<<<gw, 256, 0, s>>>(dir ? rrp : rp, dir ? rcol : col, cur, cc, nxt, nc, mark, sccv,
+                                                      color, 0, heavy));
+                    LAUNCH(k_reach_heavy<<<152 * 8, 256, 0, s>>>(dir ? rrp : rp, dir ? rcol : col, nxt, nc, mark,
+                                                                 sccv, color, 0, heavy));
+                }
                 if (read_u32(nc, &h, s)) return -1;
                 if (!h) break;
+                fsize = h;
                 uint32_t* t = cur; cur = nxt; nxt = t;
                 uint32_t* tc = cc; cc = nc; nc = tc;
             }
@@ -715,13 +757,20 @@ int launch_scc_bounds(const uint32_t* rp, const uint32_t* col, const uint32_t* r
         cudaMemsetAsync(&cnts[1], 0, 8, s);
         LAUNCH(k_color_roots<<<gv, 256, 0, s>>>(n, sccv, color, bw, L0, &cnts[1]));
         uint32_t *cur = L0, *nxt = L1, *cc = &cnts[1], *nc = &cnts[2];
+        uint32_t fsize = 0;
+        if (read_u32(cc, &fsize, s)) return -1;   // the colour roots
         for (;;) {
             cudaMemsetAsync(nc, 0, 4, s);
-            cudaMemsetAsync(&heavy->n, 0, 4, s);
-            LAUNCH(k_reach<<<gw, 256, 0, s>>>(rrp, rcol, cur, cc, nxt, nc, bw, sccv, color, 1, heavy));
-            LAUNCH(k_reach_heavy<<<152 * 8, 256, 0, s>>>(rrp, rcol, nxt, nc, bw, sccv, color, 1, heavy));
+            if (reach_pull(fsize, n)) {
+                LAUNCH(k_reach_pull<<<gv, 256, 0, s>>>(rp, col, n, nxt, nc, bw, sccv, color, 1));
+            } else {
+                cudaMemsetAsync(&heavy->n, 0, 4, s);
+                LAUNCH(k_reach<<<gw, 256, 0, s>>>(rrp, rcol, cur, cc, nxt, nc, bw, sccv, color, 1, heavy));
+                LAUNCH(k_reach_heavy<<<152 * 8, 256, 0, s>>>(rrp, rcol, nxt, nc, bw, sccv, color, 1, heavy));
+            }
             if (read_u32(nc, &h, s)) return -1;
             if (!h) break;
+            fsize = h;
             uint32_t* t = cur; cur = nxt; nxt = t;
             uint32_t* tc = cc; cc = nc; nc = tc;
         }
