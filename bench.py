@@ -430,7 +430,7 @@ def run_sweep(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)   # ~1.2 s timed: several clock samples
+    ap.add_argument("--steps", type=int, default=500)   # ~1.3 s timed: several clock samples
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="chunglu1m", choices=sorted(WORKLOADS))

@@ -569,7 +569,10 @@ __device__ __noinline__ void expand_heavy(const GraphDev& G, const HeavyEntry* H
 // thousands of dependent loads.  vis/F-next of x are written by x's own
 // thread, without atomics.  The frontier words themselves are cleared
 // afterwards (pull_clear), once no thread can still be reading them.
-constexpr u32 kPullSerial = 32;
+#ifndef BCM_PULL_SERIAL
+#define BCM_PULL_SERIAL 32
+#endif
+constexpr u32 kPullSerial = BCM_PULL_SERIAL;
 #ifndef BCM_PULL_UNROLL
 #define BCM_PULL_UNROLL 2
 #endif
