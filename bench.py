@@ -213,11 +213,14 @@ def run_serve(args, rank, world):
     graphs = [serve.build_graph(sp) for sp in specs]
     t_gen = time.perf_counter() - t
     t = time.perf_counter()
-    be = serve.GpuBackend(graphs, options=B.make_options(blocks=args.serve_blocks))
+    budget = int(args.serve_budget_gb * (1 << 30))
+    # optional cap on each run's workspace (negative: the budget's share of
+    # one run in flight; 0, the default: none)
+    ws_cap = int(args.serve_ws_cap_gb * (1 << 30)) if args.serve_ws_cap_gb >= 0 else budget // args.serve_inflight
+    be = serve.GpuBackend(graphs, options=B.make_options(blocks=args.serve_blocks), workspace_cap=ws_cap)
     torch.cuda.synchronize()
     t_load = time.perf_counter() - t
     csr_bytes = int(sum(g.row_ptr.nbytes // 2 + g.col.nbytes for g in graphs))
-    budget = int(args.serve_budget_gb * (1 << 30))
 
     def sched():
         return serve.Scheduler(be, max_inflight=args.serve_inflight, hbm_budget=budget)
@@ -270,6 +273,7 @@ def run_serve(args, rank, world):
                                % (len(graphs), args.serve_requests),
                    "max_inflight": args.serve_inflight, "hbm_budget_gb": args.serve_budget_gb,
                    "cta_blocks": args.serve_blocks or "library default",
+                   "workspace_cap_gb": ws_cap / 2**30 if ws_cap else None,
                    "graphs_resident_bytes": csr_bytes, "vertices": int(sum(g.n for g in graphs)),
                    "arcs": int(sum(g.m for g in graphs))},
         "capacity_rps": capacity, "capacity_latency_ms": serve.summarize(cap_res, cap_span)["latency_ms"],
@@ -452,6 +456,8 @@ def main():
     ap.add_argument("--serve-rates", default="0.5,0.8,1.0", help="fractions of the measured capacity")
     ap.add_argument("--serve-inflight", type=int, default=16)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--serve-ws-cap-gb", type=float, default=0.0,
+                    help="per-run workspace cap (fewer per-CTA blocks on large graphs); <0: budget/inflight, 0: none")
     ap.add_argument("--serve-check", type=int, default=300, help="results compared with the request alone")
     ap.add_argument("--serve-blocks", type=int, default=0, help="per-CTA blocks of a served run (0: library default)")
     ap.add_argument("--batch", action="store_true", help="many small graphs as one CUDA graph")

@@ -251,7 +251,7 @@ class GpuBackend(Backend):
     """Graphs resident on the device, one CUDA stream and one set of pinned
     output buffers per graph."""
 
-    def __init__(self, graphs, options=None, kmax: int = 1024, trace: bool = False):
+    def __init__(self, graphs, options=None, kmax: int = 1024, trace: bool = False, workspace_cap: int = 0):
         import torch
 
         from . import bcm
@@ -259,6 +259,11 @@ class GpuBackend(Backend):
         self.bcm = bcm
         bcm.load()
         self.opts = options if options is not None else bcm.make_options()
+        # workspace_cap > 0: a run on a large graph uses fewer per-CTA blocks,
+        # so that its workspace (one n-vertex slot per block) stays under the
+        # cap; with cap = budget / max_inflight the runs in flight fit the
+        # budget together instead of trimming one another's workspaces
+        self.workspace_cap = int(workspace_cap)
         # with trace, every run records its kernels' time stamps and collect()
         # reports the span of device time the run's waves occupied
         self.trace = trace
@@ -280,10 +285,35 @@ class GpuBackend(Backend):
                               torch.zeros(kb, dtype=torch.int64).pin_memory(),
                               torch.zeros(kb, dtype=torch.int32).pin_memory()))
         self._fp = {}
+        self._gopts = {}
+
+    def options(self, gid):
+        """The run options of graph gid: the backend's, with the per-CTA
+        block count lowered (largest that fits) when the workspace cap asks."""
+        if gid not in self._gopts:
+            o = self.opts
+            h = self.handles[gid].h
+            if self.workspace_cap and not o.blocks and self.bcm.bcm_workspace_bytes(h, o) > self.workspace_cap:
+                kw = _opts_kw(o)
+                lo, hi = 1, 1
+                while self.bcm.bcm_workspace_bytes(h, self.bcm.make_options(**dict(kw, blocks=hi * 2))) <= \
+                        self.workspace_cap and hi < (1 << 16):
+                    hi *= 2
+                hi *= 2   # blocks=hi does not fit (or the library caps blocks below it)
+                while hi - lo > 1:
+                    mid = (lo + hi) // 2
+                    if self.bcm.bcm_workspace_bytes(h, self.bcm.make_options(**dict(kw, blocks=mid))) <= \
+                            self.workspace_cap:
+                        lo = mid
+                    else:
+                        hi = mid
+                o = self.bcm.make_options(**dict(kw, blocks=lo))
+            self._gopts[gid] = o
+        return self._gopts[gid]
 
     def footprint(self, gid):
         if gid not in self._fp:
-            self._fp[gid] = self.bcm.bcm_workspace_bytes(self.handles[gid].h, self.opts)
+            self._fp[gid] = self.bcm.bcm_workspace_bytes(self.handles[gid].h, self.options(gid))
         return self._fp[gid]
 
     def start(self, gid, k):
@@ -291,7 +321,7 @@ class GpuBackend(Backend):
         ids, far, reach = self.bufs[gid]
         self.kk[gid] = min(k, h.n)
         self.stats[gid] = self.bcm.bcm_stats()
-        self.bcm.bcm_topk_start(h.h, k, self.opts, ids, far, reach)
+        self.bcm.bcm_topk_start(h.h, k, self.options(gid), ids, far, reach)
 
     def poll(self, gid):
         return self.bcm.bcm_topk_finish(self.handles[gid].h, wait=False, stats=self.stats[gid])
@@ -320,7 +350,7 @@ class GpuBackend(Backend):
     def alone(self, gid, k):
         """The same request run by itself, synchronously (no trace); its
         workspace is given back afterwards unless the graph already held one."""
-        kw = _opts_kw(self.opts)
+        kw = _opts_kw(self.options(gid))
         kw["flags"] &= ~self.bcm.BCM_TRACE
         had = gid in self.held
         res = self.handles[gid].topk(k, **kw)

@@ -64,3 +64,29 @@ def test_budget_bounds_the_held_workspace(backend):
     for r in res[:40]:
         ids, far, reach, _ = backend.alone(r.graph, r.k)
         assert np.array_equal(r.ids, ids) and np.array_equal(r.farness, far) and np.array_equal(r.reach, reach)
+
+
+def test_workspace_cap_lowers_blocks_not_results(backend):
+    """A per-run workspace cap gives the large graphs fewer per-CTA blocks (the
+    largest count whose workspace fits) and leaves every result unchanged."""
+    from paper_1507_01490_gb300 import bcm, serve
+    fps = [backend.footprint(g) for g in range(16)]
+    cap = sorted(fps)[len(fps) // 2]
+    capped = serve.GpuBackend.__new__(serve.GpuBackend)
+    capped.__dict__.update(backend.__dict__)
+    capped._fp, capped._gopts, capped.workspace_cap = {}, {}, cap
+    capped.held = backend.held
+    for g in range(16):
+        o = capped.options(g)
+        if fps[g] <= cap:
+            assert o.blocks == 0 and capped.footprint(g) == fps[g]
+            continue
+        assert o.blocks >= 1 and capped.footprint(g) < fps[g]
+        if o.blocks > 1:
+            assert capped.footprint(g) <= cap
+            more = bcm.make_options(**dict(serve._opts_kw(o), blocks=o.blocks + 1))
+            assert bcm.bcm_workspace_bytes(backend.handles[g].h, more) > cap
+        for k in (1, 10, 100):
+            a = backend.alone(g, k)
+            b = capped.alone(g, k)
+            assert all(np.array_equal(x, y) for x, y in zip(a[:3], b[:3])), (g, k)
