@@ -564,9 +564,9 @@ __device__ __noinline__ void expand_heavy(const GraphDev& G, const HeavyEntry* H
 // words of its in-neighbours, stopping once every pending lane is found.
 // Warps take 32 consecutive vertices at a time from a shared counter.
 // A vertex with at most kPullSerial in-arcs is scanned by its own thread;
-// a larger one by the whole warp, 32 in-arcs per step with an OR-reduction
-// and the same early stop, so a hub's in-list does not hold one thread for
-// thousands of dependent loads.  vis/F-next of x are written by x's own
+// a larger one by the whole warp, 32*kPullCoop in-arcs per step with an
+// OR-reduction and the same early stop, so a hub's in-list does not hold one
+// thread for thousands of dependent loads.  vis/F-next of x are written by x's own
 // thread, without atomics.  The frontier words themselves are cleared
 // afterwards (pull_clear), once no thread can still be reading them.
 #ifndef BCM_PULL_SERIAL
