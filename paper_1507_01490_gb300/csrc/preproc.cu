@@ -132,12 +132,25 @@ __device__ __forceinline__ void uf_union(uint32_t* parent, uint32_t a, uint32_t 
 // giant-component u is either linked from w's side or joins two vertices
 // already in the giant set, so the components are exact.
 constexpr uint32_t kLink = 2;
+// A sampled arc to a vertex of more than kHubDeg arcs is not linked while
+// sampling but with the other arcs afterwards: thousands of rows sample the
+// same hub, and their atomics and walks on its entry serialise; once the
+// giant component exists the hub points straight at its root.
+#ifndef BCM_CC_HUB_DEG
+#define BCM_CC_HUB_DEG 64
+#endif
+constexpr uint32_t kHubDeg = BCM_CC_HUB_DEG;   // 0: every sampled arc is linked while sampling
+
+__device__ __forceinline__ bool sampled(const uint32_t* rp, uint32_t w, uint32_t pos) {
+    return pos < kLink && (kHubDeg == 0 || rp[w + 1] - rp[w] <= kHubDeg);
+}
 
 __global__ void k_uf_link_first(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t* parent, int* err) {
     size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < n; u += stride) {
         uint32_t beg = rp[u], end = rp[u + 1];
-        for (uint32_t e = beg; e < end && e < beg + kLink; ++e) uf_union(parent, (uint32_t)u, col[e], err);
+        for (uint32_t e = beg; e < end && e < beg + kLink; ++e)
+            if (sampled(rp, col[e], e - beg)) uf_union(parent, (uint32_t)u, col[e], err);
     }
 }
 
@@ -161,8 +174,8 @@ __global__ void k_argmax_degree(const uint32_t* rp, uint32_t n, unsigned long lo
     if ((threadIdx.x & 31) == 0) atomicMax(best, b);
 }
 
-// One warp per vertex outside the giant component: link its arcs beyond the
-// first kLink.
+// One warp per vertex outside the giant component: link its arcs that
+// sampling left (beyond the first kLink, and the sampled ones to hubs).
 __global__ void k_uf_link_rest(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t* parent,
                                const unsigned long long* best, int* err) {
     // the giant component's root, found once per block (every thread
@@ -176,12 +189,13 @@ __global__ void k_uf_link_rest(const uint32_t* rp, const uint32_t* col, uint32_t
     size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
     for (size_t u = warp; u < n; u += nwarps) {
         uint32_t beg = rp[u], end = rp[u + 1];
-        if (end - beg <= kLink) continue;
+        if (kHubDeg == 0 && end - beg <= kLink) continue;
         // after k_uf_flatten every vertex points at its root: one load tells
         // a giant vertex (roots only change by later links, which keep a
         // giant vertex in the giant component)
         if (vload(&parent[u]) == giant || uf_find(parent, (uint32_t)u) == giant) continue;
-        for (uint32_t e = beg + kLink + lane; e < end; e += 32) uf_union(parent, (uint32_t)u, col[e], err);
+        for (uint32_t e = beg + lane; e < end; e += 32)
+            if (!sampled(rp, col[e], e - beg)) uf_union(parent, (uint32_t)u, col[e], err);
     }
 }
 
