@@ -171,7 +171,14 @@ __global__ void k_argmax_degree(const uint32_t* rp, uint32_t n, unsigned long lo
         unsigned long long t = __shfl_xor_sync(0xffffffffu, b, o);
         b = t > b ? t : b;
     }
-    if ((threadIdx.x & 31) == 0) atomicMax(best, b);
+    // then across the block's warps: one atomic per block on the one word
+    __shared__ unsigned long long s_b[32];
+    if ((threadIdx.x & 31) == 0) s_b[threadIdx.x >> 5] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (unsigned w = 1; w < blockDim.x / 32; ++w) b = s_b[w] > b ? s_b[w] : b;
+        atomicMax(best, b);
+    }
 }
 
 // One warp per vertex outside the giant component: link its arcs that
@@ -245,7 +252,7 @@ int launch_cc_reach(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_
     unsigned long long* best = (unsigned long long*)(size + (((size_t)n + 63) & ~(size_t)63));
     cudaMemsetAsync(best, 0, sizeof(unsigned long long), s);
     k_uf_init<<<b, 256, 0, s>>>(parent, size, n);
-    k_argmax_degree<<<b, 256, 0, s>>>(rp, n, best);
+    k_argmax_degree<<<b < 152 * 4 ? b : 152 * 4, 256, 0, s>>>(rp, n, best);
     k_uf_link_first<<<b, 256, 0, s>>>(rp, col, n, parent, err);
     k_uf_flatten<<<b, 256, 0, s>>>(parent, n);
     k_uf_link_rest<<<blocks_for((size_t)n * 32, 256), 256, 0, s>>>(rp, col, n, parent, best, err);
@@ -471,11 +478,15 @@ __global__ void k_max_degree(const uint32_t* rp, uint32_t n, uint32_t* out) {
         uint32_t d = rp[v + 1] - rp[v];
         best = d > best ? d : best;
     }
-    for (int o = 16; o; o >>= 1) {
-        uint32_t t = __shfl_xor_sync(0xffffffffu, best, o);
-        best = t > best ? t : best;
+    best = __reduce_max_sync(0xffffffffu, best);
+    // then across the block's warps: one atomic per block on the one word
+    __shared__ uint32_t s_b[32];
+    if ((threadIdx.x & 31) == 0) s_b[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (unsigned w = 1; w < blockDim.x / 32; ++w) best = s_b[w] > best ? s_b[w] : best;
+        atomicMax(out, best);
     }
-    if ((threadIdx.x & 31) == 0) atomicMax(out, best);
 }
 
 __global__ void k_degree_keys(const uint32_t* rp, uint32_t n, const uint32_t* maxdeg, uint32_t* keys,
@@ -506,7 +517,7 @@ int launch_degree_order(const uint32_t* rp, uint32_t n, uint32_t* order, void* s
     uint32_t* d_max = (uint32_t*)(p + 3 * a);
     void* rscr = p + 3 * a + 256;
     cudaMemsetAsync(d_max, 0, sizeof(uint32_t), s);
-    k_max_degree<<<blocks_for(n, 256), 256, 0, s>>>(rp, n, d_max);
+    k_max_degree<<<blocks_for(n, 256, 152 * 4), 256, 0, s>>>(rp, n, d_max);
     k_degree_keys<<<blocks_for(n, 256), 256, 0, s>>>(rp, n, d_max, keys, order);
     note_launch(2);
     uint32_t maxdeg = 0;
