@@ -146,12 +146,20 @@ __global__ void k_trim(const uint32_t* rp, const uint32_t* col, const uint32_t* 
 
 __global__ void k_pivot(const uint32_t* rp, const uint32_t* rrp, uint32_t n, const uint32_t* scc,
                         unsigned long long* best) {
+    // each thread's best, then the warp's: one atomic per warp on the one word
+    unsigned long long b = 0;
     GRID_STRIDE(v, n) {
         if (scc[v] != UNSET) continue;
         unsigned long long p = (unsigned long long)(rp[v + 1] - rp[v]) * (rrp[v + 1] - rrp[v]);
         if (p > 0xffffffffull) p = 0xffffffffull;
-        atomicMax(best, (p << 32) | (0xffffffffull - v));
+        const unsigned long long key = (p << 32) | (0xffffffffull - v);
+        b = key > b ? key : b;
     }
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, b, o);
+        b = t > b ? t : b;
+    }
+    if ((threadIdx.x & 31) == 0 && b) atomicMax(best, b);
 }
 
 __global__ void k_seed_mark(uint32_t v, uint32_t* mark, uint32_t* list, uint32_t* cnt) {
@@ -284,8 +292,18 @@ __global__ void k_count_unset(uint32_t n, const uint32_t* scc, uint32_t* cnt) {
 }
 
 // labels ordered by smallest member
+// The smallest member of every SCC; lanes of one SCC (most of them, in a
+// graph with a giant SCC) take their minimum first, then one atomic.
 __global__ void k_minrep(uint32_t n, const uint32_t* scc, uint32_t* minv) {
-    GRID_STRIDE(v, n) atomicMin(&minv[scc[v]], (uint32_t)v);
+    const uint32_t lane = threadIdx.x & 31;
+    for (size_t v0 = blockIdx.x * (size_t)blockDim.x + (threadIdx.x & ~31u); v0 < n;
+         v0 += (size_t)gridDim.x * blockDim.x) {
+        const size_t v = v0 + lane;
+        const uint32_t c = v < n ? scc[v] : UNSET;
+        const uint32_t peers = __match_any_sync(0xffffffffu, c);
+        const uint32_t m = __reduce_min_sync(peers, v < n ? (uint32_t)v : UNSET);
+        if (c != UNSET && lane == (uint32_t)(__ffs(peers) - 1)) atomicMin(&minv[c], m);
+    }
 }
 
 __global__ void k_min_flags(uint32_t n, const uint32_t* scc, const uint32_t* minv, uint32_t* flags) {
@@ -299,9 +317,35 @@ __global__ void k_label(uint32_t n, const uint32_t* scc, const uint32_t* minv, c
 // DAG
 // The key (comp[u] << b | comp[w]) of an arc between two SCCs, appended to
 // keys (in no particular order: they are sorted next); arcs inside an SCC,
-// most of a graph with a giant SCC, are left out of the sort.
+// most of a graph with a giant SCC, are left out of the sort.  Each warp
+// stages its keys in shared memory and reserves room in keys once per
+// kKeyStage of them, not once per 32 arcs (the count is one word that
+// every warp of the grid would otherwise hit).
+constexpr uint32_t kKeyStage = 256;
+struct KeyStage {
+    unsigned long long* buf;   // this warp's kKeyStage shared entries
+    unsigned long long* dst;
+    uint32_t* cnt;
+    uint32_t n;                // staged (the same in every lane)
+    __device__ __forceinline__ void flush() {
+        __syncwarp();
+        uint32_t base = 0;
+        if ((threadIdx.x & 31) == 0 && n) base = atomicAdd(cnt, n);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (uint32_t i = threadIdx.x & 31; i < n; i += 32) dst[base + i] = buf[i];
+        __syncwarp();
+        n = 0;
+    }
+    __device__ __forceinline__ void push(bool want, unsigned long long key) {
+        const uint32_t m = __ballot_sync(0xffffffffu, want);
+        if (want) buf[n + __popc(m & ((1u << (threadIdx.x & 31)) - 1u))] = key;
+        n += __popc(m);
+        if (n + 32 > kKeyStage) flush();
+    }
+};
+
 __device__ __forceinline__ void dag_key(const uint32_t* col, const uint32_t* comp, uint32_t cu, int b, uint32_t e,
-                                        bool valid, unsigned long long* keys, uint32_t* kcnt) {
+                                        bool valid, KeyStage& ks) {
     unsigned long long key = 0;
     bool inter = false;
     if (valid) {
@@ -309,28 +353,27 @@ __device__ __forceinline__ void dag_key(const uint32_t* col, const uint32_t* com
         inter = cu != cw;
         key = ((unsigned long long)cu << b) | cw;
     }
-    const uint32_t m = __ballot_sync(0xffffffffu, inter);
-    if (m == 0) return;
-    const int leader = __ffs(m) - 1;
-    uint32_t base = 0;
-    if ((int)(threadIdx.x & 31) == leader) base = atomicAdd(kcnt, (uint32_t)__popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (inter) keys[base + __popc(m & ((1u << (threadIdx.x & 31)) - 1u))] = key;
+    ks.push(inter, key);
 }
 
+// launched with 256 threads: 8 warps' stages
 __global__ void k_dag_keys(const uint32_t* rp, const uint32_t* col, uint32_t n, const uint32_t* comp, int b,
                            unsigned long long* keys, uint32_t* kcnt, RowHeavy* H) {
+    __shared__ unsigned long long s_stage[8 * kKeyStage];
+    KeyStage ks{&s_stage[(threadIdx.x >> 5) * kKeyStage], keys, kcnt, 0};
     WARP_PER_ITEM(u, n) {
         if (row_claim(H, (uint32_t)u, rp[u + 1] - rp[u])) continue;
         const uint32_t cu = comp[u], end = rp[u + 1];
-        for (uint32_t e0 = rp[u]; e0 < end; e0 += 32)
-            dag_key(col, comp, cu, b, e0 + lane_, e0 + lane_ < end, keys, kcnt);
+        for (uint32_t e0 = rp[u]; e0 < end; e0 += 32) dag_key(col, comp, cu, b, e0 + lane_, e0 + lane_ < end, ks);
     }
+    ks.flush();
 }
 
 // the rows row_claim listed, 32 arcs per warp at a time over the whole grid
 __global__ void k_dag_keys_heavy(const uint32_t* rp, const uint32_t* col, const uint32_t* comp, int b,
                                  unsigned long long* keys, uint32_t* kcnt, const RowHeavy* H) {
+    __shared__ unsigned long long s_stage[8 * kKeyStage];
+    KeyStage ks{&s_stage[(threadIdx.x >> 5) * kKeyStage], keys, kcnt, 0};
     const uint32_t hn = H->n < kRowHeavyCap ? H->n : kRowHeavyCap;
     const uint32_t lane = threadIdx.x & 31;
     const size_t warp = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5;
@@ -338,8 +381,9 @@ __global__ void k_dag_keys_heavy(const uint32_t* rp, const uint32_t* col, const 
     for (uint32_t h = 0; h < hn; ++h) {
         const uint32_t u = H->item[h], beg = rp[u], end = rp[u + 1], cu = comp[u];
         for (size_t e0 = beg + warp * 32; e0 < end; e0 += nwarps * 32)
-            dag_key(col, comp, cu, b, (uint32_t)(e0 + lane), e0 + lane < end, keys, kcnt);
+            dag_key(col, comp, cu, b, (uint32_t)(e0 + lane), e0 + lane < end, ks);
     }
+    ks.flush();
 }
 
 __global__ void k_unique_flags(const unsigned long long* keys, uint64_t m, uint32_t* flags) {
@@ -359,8 +403,17 @@ __global__ void k_unique_scatter(const unsigned long long* keys, uint64_t m, con
     }
 }
 
+// Counts of each value; lanes holding the same value (a giant SCC's label,
+// runs of a sorted array) add their count with one atomic.
 __global__ void k_hist(const uint32_t* a, size_t cnt, uint32_t* h) {
-    GRID_STRIDE(i, cnt) atomicAdd(&h[a[i]], 1u);
+    const uint32_t lane = threadIdx.x & 31;
+    for (size_t i0 = blockIdx.x * (size_t)blockDim.x + (threadIdx.x & ~31u); i0 < cnt;
+         i0 += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = i0 + lane;
+        const uint32_t x = i < cnt ? a[i] : UNSET;
+        const uint32_t peers = __match_any_sync(0xffffffffu, x);
+        if (i < cnt && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&h[x], (uint32_t)__popc(peers));
+    }
 }
 
 __global__ void k_scatter_pred(const uint32_t* dsrc, const uint32_t* ddst, uint32_t nd, uint32_t* cursor,
