@@ -126,8 +126,8 @@ __device__ __forceinline__ void uf_union(uint32_t* parent, uint32_t a, uint32_t 
 }
 
 // Components after Afforest (Sutton, Ben-Nun, Barak, IPDPS 2018): link every
-// vertex to its first kLink neighbours, compress, take the component of the
-// highest-degree vertex as the giant one, then link the remaining arcs only
+// vertex to its first kLink neighbours, compress, take the most frequent
+// component of a sample as the giant one, then link the remaining arcs only
 // of vertices outside it.  For a symmetric arc set a skipped arc (u,w) of a
 // giant-component u is either linked from w's side or joins two vertices
 // already in the giant set, so the components are exact.
@@ -160,33 +160,44 @@ __global__ void k_uf_flatten(uint32_t* parent, uint32_t n) {
         parent[v] = uf_find(parent, (uint32_t)v);
 }
 
-__global__ void k_argmax_degree(const uint32_t* rp, uint32_t n, unsigned long long* best) {
-    unsigned long long b = 0;
-    size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += stride) {
-        unsigned long long key = ((unsigned long long)(rp[v + 1] - rp[v]) << 32) | (0xffffffffull - v);
-        b = key > b ? key : b;
-    }
-    for (int o = 16; o; o >>= 1) {
-        unsigned long long t = __shfl_xor_sync(0xffffffffu, b, o);
-        b = t > b ? t : b;
-    }
-    // then across the block's warps: one atomic per block on the one word
-    __shared__ unsigned long long s_b[32];
-    if ((threadIdx.x & 31) == 0) s_b[threadIdx.x >> 5] = b;
+// The giant component after sampling, as Afforest finds it: the most
+// frequent root among 1024 vertices spread evenly over the ids (one block
+// of 1024 threads: sort the roots in shared memory, take the longest run).
+// best gets (run length << 32 | ~root), the form k_uf_link_rest reads.
+__global__ void __launch_bounds__(1024) k_uf_giant_sample(const uint32_t* parent, uint32_t n,
+                                                           unsigned long long* best) {
+    __shared__ uint32_t s_r[1024];
+    __shared__ unsigned long long s_best;
+    const uint32_t i = threadIdx.x;
+    if (i == 0) s_best = 0;
+    s_r[i] = vload(&parent[(uint32_t)(((unsigned long long)i * n) >> 10)]);   // flattened: the root
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (unsigned w = 1; w < blockDim.x / 32; ++w) b = s_b[w] > b ? s_b[w] : b;
-        atomicMax(best, b);
+    for (uint32_t k = 2; k <= 1024; k <<= 1) {          // bitonic sort, ascending
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            const uint32_t l = i ^ j;
+            if (l > i) {
+                const uint32_t a = s_r[i], b = s_r[l];
+                if (((i & k) == 0) == (a > b)) { s_r[i] = b; s_r[l] = a; }
+            }
+            __syncthreads();
+        }
     }
+    if (i == 0 || s_r[i] != s_r[i - 1]) {               // a run starts here
+        uint32_t e = i + 1;
+        while (e < 1024 && s_r[e] == s_r[i]) ++e;
+        atomicMax(&s_best, ((unsigned long long)(e - i) << 32) | (0xffffffffull - s_r[i]));
+    }
+    __syncthreads();
+    if (i == 0) *best = s_best;
 }
 
 // One warp per vertex outside the giant component: link its arcs that
 // sampling left (beyond the first kLink, and the sampled ones to hubs).
 __global__ void k_uf_link_rest(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t* parent,
                                const unsigned long long* best, int* err) {
-    // the giant component's root, found once per block (every thread
-    // walking to it would read the same words a million times)
+    // the giant component's root (the sampled one, or the component of
+    // the vertex best names), found once per block (every thread walking to
+    // it would read the same words a million times)
     __shared__ uint32_t s_giant;
     if (threadIdx.x == 0) s_giant = uf_find(parent, 0xffffffffu - (uint32_t)(*best & 0xffffffffull));
     __syncthreads();
@@ -252,9 +263,9 @@ int launch_cc_reach(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_
     unsigned long long* best = (unsigned long long*)(size + (((size_t)n + 63) & ~(size_t)63));
     cudaMemsetAsync(best, 0, sizeof(unsigned long long), s);
     k_uf_init<<<b, 256, 0, s>>>(parent, size, n);
-    k_argmax_degree<<<b < 152 * 4 ? b : 152 * 4, 256, 0, s>>>(rp, n, best);
     k_uf_link_first<<<b, 256, 0, s>>>(rp, col, n, parent, err);
     k_uf_flatten<<<b, 256, 0, s>>>(parent, n);
+    k_uf_giant_sample<<<1, 1024, 0, s>>>(parent, n, best);
     k_uf_link_rest<<<blocks_for((size_t)n * 32, 256), 256, 0, s>>>(rp, col, n, parent, best, err);
     k_uf_compress_count<<<b, 256, 0, s>>>(parent, size, n);
     k_uf_reach<<<b, 256, 0, s>>>(parent, size, n, xlo, xhi);
