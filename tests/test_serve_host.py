@@ -164,3 +164,54 @@ def test_mix_and_stream_recipes():
     gids = np.array([r.graph for r in reqs])
     assert gids.min() == 0 and gids.max() == 199
     assert all(r.arrival == 0.0 for r in serve.request_stream(10, 3, rate=math.inf))
+
+
+class _FakeBcm:
+    """Workspace bytes linear in the per-CTA block count (0 = the library's
+    default of 608), the shape of bcm_workspace_bytes."""
+
+    def __init__(self, per_block, fixed, default_blocks=608, max_blocks=608):
+        self.per_block, self.fixed = per_block, fixed
+        self.default_blocks, self.max_blocks = default_blocks, max_blocks
+
+    class Opt:
+        def __init__(self, **kw):
+            self.__dict__.update(dict(lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0, grid_lanes=0,
+                                      heavy_words=0, pull_div=0, defer_words=0), **kw)
+
+    def make_options(self, **kw):
+        return self.Opt(**kw)
+
+    def bcm_workspace_bytes(self, h, o):
+        b = o.blocks or self.default_blocks
+        return self.fixed + self.per_block * min(b, self.max_blocks)
+
+
+class _Handle:
+    h = None
+
+
+@pytest.mark.parametrize("cap_blocks", [1, 7, 100, 607])
+def test_workspace_cap_picks_the_largest_block_count_that_fits(cap_blocks):
+    fb = _FakeBcm(per_block=1 << 20, fixed=5 << 20)
+    be = serve.GpuBackend.__new__(serve.GpuBackend)
+    be.bcm, be.opts, be.handles = fb, fb.make_options(), [_Handle()]
+    be._gopts, be._fp = {}, {}
+    be.workspace_cap = fb.fixed + fb.per_block * cap_blocks + (fb.per_block // 2)
+    o = be.options(0)
+    assert o.blocks == cap_blocks
+    assert be.footprint(0) <= be.workspace_cap < fb.bcm_workspace_bytes(None, fb.make_options(blocks=cap_blocks + 1))
+
+
+def test_workspace_cap_leaves_fitting_graphs_and_explicit_blocks_alone():
+    fb = _FakeBcm(per_block=1 << 20, fixed=5 << 20)
+    be = serve.GpuBackend.__new__(serve.GpuBackend)
+    be.bcm, be.handles = fb, [_Handle(), _Handle()]
+    be._gopts, be._fp = {}, {}
+    be.opts = fb.make_options()
+    be.workspace_cap = 1 << 40                   # everything fits: the backend's options as they are
+    assert be.options(0) is be.opts
+    be._gopts = {}
+    be.opts = fb.make_options(blocks=3)          # a fixed block count is the caller's choice
+    be.workspace_cap = 1 << 20
+    assert be.options(1).blocks == 3
