@@ -151,20 +151,24 @@ def m_tot_undirected(g, reach):
 # ------------------------------------------------------------------- oracle
 def cpu_sample(g, budget_s, seed=7):
     """Oracle (exhaustive BFS, all host cores) on a growing sample of sources
-    until ~budget_s of work; returns (seconds per graph, sources, cores)."""
+    until ~budget_s of work; returns (seconds per graph, sources, threads):
+    threads is the fewest threads that took work in any call of the sample."""
     import oracle
     from paper_1507_01490_gb300 import graphgen
     cores = oracle.default_threads()
-    done, spent, size = 0, 0.0, max(cores * 4, 64)
+    done, spent, size = 0, 0.0, max(cores * 16, 64)
+    used = cores
     while spent < budget_s and done < g.n:
         cnt = min(size, g.n - done)
         src = graphgen.uniform_u32(seed + done, cnt, g.n)
+        info = {}
         t = time.perf_counter()
-        oracle.farness_all(g, sources=src, threads=cores)
+        oracle.farness_all(g, sources=src, threads=cores, info=info)
         spent += time.perf_counter() - t
+        used = min(used, info["threads_used"])
         done += cnt
         size = min(size * 2, 1 << 16)
-    return spent / done * g.n, done, cores
+    return spent / done * g.n, done, used
 
 
 def run_reference(args, rank, world):
@@ -172,13 +176,15 @@ def run_reference(args, rank, world):
         return 0
     from paper_1507_01490_gb300 import graphgen
     g = graphgen.workload(args.workload)
-    per_step, dones = [], []
+    per_step, dones, used = [], [], []
     budget = args.ref_step_seconds
     for i in range(args.warmup + args.steps):
-        s_per_graph, done, cores = cpu_sample(g, budget, seed=1000 + i)
+        s_per_graph, done, threads = cpu_sample(g, budget, seed=1000 + i)
         if i >= args.warmup:
             per_step.append(s_per_graph)
             dones.append(done)
+            used.append(threads)
+    cores = min(used)
     v = float(np.mean(per_step))
     sample = "exhaustive BFS from %d to %d uniformly drawn sources per step (of n = %d), scaled by n" % (
         min(dones), max(dones), g.n)

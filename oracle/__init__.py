@@ -110,8 +110,9 @@ def default_threads() -> int:
     return max(1, len(os.sched_getaffinity(0)))
 
 
-def farness_all(g, sources=None, threads=None, arcs=False):
-    """(farness u64, reach u32[, arcs u64]) for every source (all vertices by default)."""
+def farness_all(g, sources=None, threads=None, arcs=False, info=None):
+    """(farness u64, reach u32[, arcs u64]) for every source (all vertices by default).
+    info (a dict, optional) receives "threads_used": how many threads took work."""
     rp, col = _csr(g)
     if sources is None:
         src = None
@@ -128,8 +129,12 @@ def farness_all(g, sources=None, threads=None, arcs=False):
                                        _p(f, _u64p), _p(r, _u32p),
                                        None if a is None else _p(a, _u64p),
                                        threads or default_threads())
-        if rc != 0:
+        if rc < 0:
             raise MemoryError("oracle_farness_all failed")
+        if info is not None:
+            info["threads_used"] = int(rc)
+    elif info is not None:
+        info["threads_used"] = 0
     out = (f[:cnt], r[:cnt])
     return out + (a[:cnt],) if arcs else out
 

@@ -117,17 +117,28 @@ typedef struct {
     const uint32_t *sources; uint64_t nsrc;
     uint64_t *farness; uint32_t *reach; uint64_t *arcs;
     uint64_t next;      /* shared work counter */
+    uint64_t grain;     /* sources per grab */
     int failed;
+    int workers;        /* threads that took at least one source */
 } fa_job;
 
+typedef struct { fa_job *J; uint64_t first; } fa_arg;
+
+/* Grab `first` (a block fixed per thread, so that every thread has work
+ * whenever there are enough sources), then blocks from the shared counter. */
 static void *fa_worker(void *arg) {
-    fa_job *J = (fa_job *)arg;
+    fa_job *J = ((fa_arg *)arg)->J;
+    uint64_t first = ((fa_arg *)arg)->first;
     bfs_ws ws;
     if (!ws_init(&ws, J->n)) { __atomic_store_n(&J->failed, 1, __ATOMIC_RELAXED); ws_free(&ws); return NULL; }
+    int took = 0;
     for (;;) {
-        uint64_t i0 = __atomic_fetch_add(&J->next, 64, __ATOMIC_RELAXED);
+        uint64_t i0 = first;
+        first = UINT64_MAX;
+        if (i0 == UINT64_MAX) i0 = __atomic_fetch_add(&J->next, J->grain, __ATOMIC_RELAXED);
         if (i0 >= J->nsrc) break;
-        uint64_t i1 = i0 + 64 < J->nsrc ? i0 + 64 : J->nsrc;
+        if (!took) { took = 1; __atomic_fetch_add(&J->workers, 1, __ATOMIC_RELAXED); }
+        uint64_t i1 = i0 + J->grain < J->nsrc ? i0 + J->grain : J->nsrc;
         for (uint64_t i = i0; i < i1; ++i) {
             uint32_t v = J->sources ? J->sources[i] : (uint32_t)i;
             uint64_t f, a; uint32_t r;
@@ -144,20 +155,31 @@ static void *fa_worker(void *arg) {
 /* f and r of each listed source (all vertices when sources == NULL, nsrc = n).
  * Output i belongs to sources[i].  arcs (nullable) receives the arcs each BFS
  * scanned, whose sum over all v is the textbook algorithm's m_tot (Section 3.1).
- * Returns 0, or -1 on allocation failure. */
+ * Threads take sources in grabs of nsrc / (4 threads), at least 1 and at most
+ * 64, so that every thread gets work even on a short list.  Returns the
+ * number of threads that took work (0 when nsrc = 0), or -1 on allocation
+ * failure. */
 int oracle_farness_all(uint32_t n, const uint64_t *row_ptr, const uint32_t *col,
                        const uint32_t *sources, uint64_t nsrc,
                        uint64_t *farness, uint32_t *reach, uint64_t *arcs, int threads) {
-    fa_job J = { n, row_ptr, col, sources, sources ? nsrc : n, farness, reach, arcs, 0, 0 };
     if (threads < 1) threads = 1;
     if (threads > 256) threads = 256;
+    uint64_t total = sources ? nsrc : n;
+    uint64_t grain = total / (4 * (uint64_t)threads);
+    if (grain < 1) grain = 1;
+    if (grain > 64) grain = 64;
+    fa_job J = { n, row_ptr, col, sources, total, farness, reach, arcs, grain * (uint64_t)threads, grain, 0, 0 };
     pthread_t th[256];
+    fa_arg args[256];
     int started = 0;
-    for (int t = 0; t < threads; ++t)
-        if (pthread_create(&th[t], NULL, fa_worker, &J) == 0) ++started;
-    if (started == 0) fa_worker(&J);
+    for (int t = 0; t < threads; ++t) {
+        args[t].J = &J;
+        args[t].first = grain * (uint64_t)t;
+        if (pthread_create(&th[started], NULL, fa_worker, &args[t]) == 0) ++started;
+        else fa_worker(&args[t]);   /* no thread: its block (and whatever is left) runs here */
+    }
     for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
-    return J.failed ? -1 : 0;
+    return J.failed ? -1 : J.workers;
 }
 
 /* ------------------------------------------------------------- top-k */

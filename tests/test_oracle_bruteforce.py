@@ -85,3 +85,20 @@ def test_workload_recipes_small_scale(orc, gen):
         f, r = orc.farness_all(g, sources=src)
         assert (f.astype(np.int64) == np.where(fin, d, 0).sum(axis=1)).all(), g.name
         assert (r == fin.sum(axis=1)).all(), g.name
+
+
+def test_threads_share_short_lists(orc, gen):
+    """The exhaustive oracle hands out sources in grabs small enough that
+    every thread takes work on a 64-source call, and the result does not
+    depend on how many threads ran (each BFS is independent)."""
+    g = gen.ba(3000, 3, seed=12)
+    src = gen.uniform_u32(21, 64, g.n)
+    f1, r1 = orc.farness_all(g, sources=src, threads=1)
+    for t in (4, 16):
+        info = {}
+        f, r = orc.farness_all(g, sources=src, threads=t, info=info)
+        assert info["threads_used"] == t
+        assert np.array_equal(f, f1) and np.array_equal(r, r1)
+    info = {}
+    orc.farness_all(g, sources=src[:0], threads=8, info=info)
+    assert info["threads_used"] == 0
