@@ -1,6 +1,13 @@
 """Full-size workloads, in the launch configuration bench.py uses (library
-defaults).  The oracle cannot run every BFS of a million-vertex graph in a
-test, so the check is on sampled outputs it computes one by one:
+defaults).
+
+Complete check: tests/golden/fullsize_<workload>_k<k>.json hold the exact
+top-k of chunglu1m and rmat20 (k = 1, 10, 100) as the oracle's sequential
+Algorithm 1 computed it (tests/golden/make_fullsize.py, which calls only the
+oracle); the GPU's ids, farness and reach must equal them element by element.
+
+The oracle cannot run every BFS of a million-vertex graph inside a test, so
+the remaining checks are on sampled outputs it computes one by one:
 
 * the k returned vertices: farness and reach equal one oracle BFS each;
 * no sampled vertex (the highest-degree ones, where the top-k lives, plus a
@@ -11,10 +18,30 @@ test, so the check is on sampled outputs it computes one by one:
   whole graph (Tarjan and the Section 2.3 programme are cheap on the CPU),
   and sampled r(v) lie in [alpha(v), omega(v)].
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden(name, k):
+    p = os.path.join(GOLDEN, "fullsize_%s_k%d.json" % (name, k))
+    if not os.path.exists(p):
+        pytest.fail("missing golden %s (tests/golden/make_fullsize.py writes it)" % p)
+    return json.load(open(p))
+
+
+def _check_golden(gold, g, ids, far, reach):
+    assert gold["csr_sha256_16"] == g.hash64(), "the workload generator no longer makes the golden's graph"
+    assert gold["n"] == g.n and gold["m"] == g.m
+    assert ids.tolist() == gold["ids"]
+    assert far.tolist() == gold["farness"]
+    assert reach.tolist() == gold["reach"]
 
 
 @pytest.fixture(scope="module")
@@ -68,18 +95,20 @@ def test_chunglu1m(B, gen, orc, chunglu, k):
     with B.BcmGraph.from_graph(g) as h:
         ids, far, reach, st = h.topk(k)
     assert len(ids) == k
+    _check_golden(_golden("chunglu1m", k), g, ids, far, reach)
     _check_topk(orc, gen, g, ids, far, reach)
     assert st["m_vis"] < 0.01 * g.m * g.n
 
 
 def test_chunglu1m_lane_widths_agree(B, chunglu):
+    """Every lane width of either kernel gives the oracle's exact top-100."""
     g = chunglu
+    gold = _golden("chunglu1m", 100)
     with B.BcmGraph.from_graph(g) as h:
-        ref = h.topk(100)
         for lanes in (64, 128, 256):
             for grid_lanes in (64, 256):
-                got = h.topk(100, lanes=lanes, grid_lanes=grid_lanes)
-                assert all(np.array_equal(a, b) for a, b in zip(ref[:3], got[:3])), (lanes, grid_lanes)
+                ids, far, reach, _ = h.topk(100, lanes=lanes, grid_lanes=grid_lanes)
+                _check_golden(gold, g, ids, far, reach)
 
 
 @pytest.fixture(scope="module")
@@ -107,6 +136,7 @@ def test_rmat20_topk(B, gen, orc, rmat, k):
     g = rmat
     with B.BcmGraph.from_graph(g) as h:
         ids, far, reach, st = h.topk(k)
+    _check_golden(_golden("rmat20", k), g, ids, far, reach)
     _check_topk(orc, gen, g, ids, far, reach)
 
 
