@@ -15,6 +15,8 @@ Simple Computation of Top-k Closeness Centralities" (arXiv 1507.01490):
   ``alpha_omega_refined``  the same with Section 2.3's biggest-SCC refinement.
 * ``bound_trace``   Lemma 1's lower bound f~_d(v, x) along one BFS.
 * ``bcm``           Algorithm 1 with BFSCut (Algorithm 2), sequential.
+* ``ShardRun``      the same loop over one shard's sources, resumable, with
+  an outside k-th key (Section 2: parallel threads share x_k).
 
 All of these are pinned by tests/test_oracle_*.py against closed forms,
 brute force and library routines; none is "parity unpinned".
@@ -86,6 +88,11 @@ def _get():
                                            ctypes.c_int, ctypes.c_uint64, _i64p, ctypes.c_uint64]
         lib.oracle_order.restype = None
         lib.oracle_order.argtypes = [ctypes.c_uint32, _u64p, _u32p]
+        lib.oracle_bcm_sources.restype = ctypes.c_int64
+        lib.oracle_bcm_sources.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int, ctypes.c_uint32,
+                                           ctypes.c_int, _u32p, _u32p, _u32p, ctypes.c_uint64, ctypes.c_uint64,
+                                           ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                                           _u32p, _u64p, _u32p, _u32p, ctypes.POINTER(_Stats)]
         lib.oracle_bcm.restype = ctypes.c_int64
         lib.oracle_bcm.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int, ctypes.c_uint32,
                                    ctypes.c_int, ctypes.c_int, _u32p, _u64p, _u32p,
@@ -233,3 +240,71 @@ def bcm(g, k, gamma_mode=None, early_test=True, refined=False):
         raise MemoryError("oracle_bcm failed")
     stats = {"m_vis": st.m_vis, "completed": st.completed, "cut": st.cut, "max_level": st.max_level}
     return ids[:got], f[:got], r[:got], stats
+
+
+class ShardRun:
+    """Algorithm 1 over one shard of the sources (its part of the processing
+    order), run a chunk at a time so that shards can exchange their k-th keys
+    in between (Section 2's shared x_k).  bounds: (xa, xb) = (r, r) on
+    undirected graphs, (alpha, omega) on digraphs."""
+
+    def __init__(self, g, k, sources, bounds, gamma_mode=None):
+        if gamma_mode is None:
+            gamma_mode = GT_TABLE1 if g.directed else GT_FOOTNOTE
+        self.g, self.k, self.mode = g, k, gamma_mode
+        self.rp, self.col = _csr(g)
+        self.src = np.ascontiguousarray(sources, dtype=np.uint32)
+        if self.src.size == 0:
+            self.src = np.zeros(1, np.uint32)[:0]
+        self.xa = np.ascontiguousarray(bounds[0], dtype=np.uint32)
+        self.xb = np.ascontiguousarray(bounds[1], dtype=np.uint32)
+        kk = max(k, 1)
+        self.ids = np.zeros(kk, np.uint32)
+        self.f = np.zeros(kk, np.uint64)
+        self.r = np.zeros(kk, np.uint32)
+        self.count = np.zeros(1, np.uint32)
+        self.stats = _Stats()
+        self.pos = 0
+        self.ext = (0, 0, 1, 0)      # (valid, N, F, id)
+
+    @property
+    def done(self):
+        return self.pos >= len(self.src)
+
+    def offer(self, key):
+        """Use key (valid, N, F, id) from now on if it ranks before the one held."""
+        valid, N, F, vid = key
+        if not valid:
+            return
+        if self.ext[0]:
+            _, N0, F0, i0 = self.ext
+            if not (N * F0 > N0 * F or (N * F0 == N0 * F and vid < i0)):
+                return
+        self.ext = (1, int(N), int(F), int(vid))
+
+    def key(self):
+        """This shard's own k-th key (valid, N, F, id); valid = 0 below k entries."""
+        c = int(self.count[0])
+        if c < self.k:
+            return (0, 0, 1, 0)
+        f, r, vid = int(self.f[self.k - 1]), int(self.r[self.k - 1]), int(self.ids[self.k - 1])
+        return (1, 0, 1, vid) if r <= 1 or f == 0 else (1, (r - 1) ** 2, f, vid)
+
+    def step(self, count):
+        """Run the next `count` sources; returns True once all are done."""
+        to = min(self.pos + count, len(self.src))
+        src = self.src if self.src.size else np.zeros(1, np.uint32)
+        got = _get().oracle_bcm_sources(self.g.n, _p(self.rp, _u64p), _p(self.col, _u32p), int(self.g.directed),
+                                        self.k, self.mode, _p(self.xa, _u32p), _p(self.xb, _u32p),
+                                        _p(src, _u32p), self.pos, to, self.ext[0], self.ext[1], self.ext[2],
+                                        self.ext[3], _p(self.ids, _u32p), _p(self.f, _u64p), _p(self.r, _u32p),
+                                        _p(self.count, _u32p), ctypes.byref(self.stats))
+        if got < 0:
+            raise MemoryError("oracle_bcm_sources failed")
+        self.pos = to
+        return self.done
+
+    def result(self):
+        c = int(self.count[0])
+        return self.ids[:c].copy(), self.f[:c].copy(), self.r[:c].copy(), {
+            "m_vis": self.stats.m_vis, "completed": self.stats.completed, "cut": self.stats.cut}

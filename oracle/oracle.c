@@ -22,6 +22,8 @@
  *   oracle_bound_trace  Lemma 1's bound f~_d(v,x) at every level of one BFS.
  *   oracle_bcm          Algorithm 1 driving BFSCut (Algorithm 2, generalised
  *                       as Sections 2.2-2.3 describe), sequential.
+ *   oracle_bcm_sources  the same loop over one shard's sources, resumable,
+ *                       with an outside k-th key (Section 2's shared x_k).
  *
  * Ranking key.  c(v) = (r-1)^2 / ((n-1) f) (Section 1).  n-1 is common to all
  * vertices, so the ranking uses s(v) = (r-1)^2 / f kept as the exact pair
@@ -34,6 +36,7 @@
  * graphs, scipy's BFS and SCC routines, brute-force ranking with exact
  * fractions, alpha <= r <= omega, and BCM's top-k = exhaustive top-k.
  */
+#define _GNU_SOURCE   /* qsort_r */
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -549,6 +552,63 @@ static int bfscut_stops(uint64_t f_d, uint64_t g, uint32_t d, uint64_t n_d,
     return all_strict || (all_weak && v > idk);
 }
 
+/* Algorithm 1's loop over sources[from..to): BFSCut(v, x_k) for each v in
+ * turn, the exact ones kept in T (the best k, rank order).  x_k is T's own
+ * k-th entry once T holds k, or -- when ext != 0 -- the outside key (eN, eF,
+ * eid) if that ranks first: the k-th entry of another shard of the same
+ * graph (Section 2's shared x_k), valid because at least k vertices of the
+ * graph rank at or before it.  X of v: xa[v], xb[v] (r(v) twice, or
+ * alpha(v), omega(v)).  S accumulates the counters. */
+static void bcm_loop(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, int gamma_mode, int early_test,
+                     const uint32_t *xa, const uint32_t *xb, const uint32_t *sources, uint64_t from, uint64_t to,
+                     int ext, uint64_t eN, uint64_t eF, uint32_t eid, topk_buf *T, lvl_ws *L,
+                     bcm_oracle_stats *S) {
+    for (uint64_t it = from; it < to; ++it) {
+        uint32_t v = sources[it];
+        uint64_t X[2] = { xa[v], xb[v] };
+        int nx = (X[0] == X[1]) ? 1 : 2;
+        int have_xk = (T->cnt == T->k);
+        uint64_t Nk = 0, Fk = 1; uint32_t idk = 0;
+        if (have_xk) { score_key(T->f[T->k - 1], T->r[T->k - 1], &Nk, &Fk); idk = T->id[T->k - 1]; }
+        if (ext && (!have_xk || ranks_before(eN, eF, eid, Nk, Fk, idk))) { Nk = eN; Fk = eF; idk = eid; have_xk = 1; }
+
+        /* BFSCut(v, x_k), level by level: Gamma_d in L->cur */
+        if (++L->epoch == 0) { memset(L->seen, 0, sizeof(uint32_t) * n); L->epoch = 1; }
+        uint32_t ncur = 1, d = 0;
+        L->cur[0] = v; L->seen[v] = L->epoch;
+        uint64_t f = 0, nd = 1, g = 0;
+        int stopped = 0;
+        for (;;) {
+            uint64_t gl = gamma_tilde(row_ptr, L->cur, ncur, d, gamma_mode);
+            g = (gamma_mode == GT_ALG2) ? g + gl : gl;
+            if (early_test && have_xk && bfscut_stops(f, g, d, nd, X, nx, v, Nk, Fk, idk)) {
+                stopped = 1; break;
+            }
+            uint32_t nn = 0;
+            for (uint32_t i = 0; i < ncur; ++i) {
+                uint32_t u = L->cur[i];
+                for (uint64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+                    uint32_t w = col[e];
+                    if (L->seen[w] != L->epoch) { L->seen[w] = L->epoch; L->nxt[nn++] = w; }
+                }
+                S->m_vis += row_ptr[u + 1] - row_ptr[u];
+            }
+            if (nn == 0) break;
+            if (!early_test && have_xk && bfscut_stops(f, g, d, nd, X, nx, v, Nk, Fk, idk)) {
+                stopped = 1; break;
+            }
+            ++d;
+            nd += nn;
+            f += (uint64_t)d * nn;
+            uint32_t *t = L->cur; L->cur = L->nxt; L->nxt = t; ncur = nn;
+        }
+        if (d > S->max_level) S->max_level = d;
+        if (stopped) { S->cut++; continue; }
+        S->completed++;
+        topk_insert(T, v, f, (uint32_t)nd);
+    }
+}
+
 static int cmp_order(const void *pa, const void *pb, void *pc) {
     const uint64_t *rp = (const uint64_t *)pc;
     uint32_t a = *(const uint32_t *)pa, b = *(const uint32_t *)pb;
@@ -634,49 +694,7 @@ int64_t oracle_bcm2(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, in
     qsort_r(order, n, sizeof(uint32_t), cmp_order, (void *)row_ptr);
 
     bcm_oracle_stats S = { 0, 0, 0, 0 };
-    for (uint32_t it = 0; it < n; ++it) {
-        uint32_t v = order[it];
-        uint64_t X[2] = { xa[v], xb[v] };
-        int nx = (X[0] == X[1]) ? 1 : 2;
-        int have_xk = (T.cnt == T.k);
-        uint64_t Nk = 0, Fk = 1; uint32_t idk = 0;
-        if (have_xk) { score_key(T.f[T.k - 1], T.r[T.k - 1], &Nk, &Fk); idk = T.id[T.k - 1]; }
-
-        /* BFSCut(v, x_k), level by level: Gamma_d in L.cur */
-        if (++L.epoch == 0) { memset(L.seen, 0, sizeof(uint32_t) * n); L.epoch = 1; }
-        uint32_t ncur = 1, d = 0;
-        L.cur[0] = v; L.seen[v] = L.epoch;
-        uint64_t f = 0, nd = 1, g = 0;
-        int stopped = 0;
-        for (;;) {
-            uint64_t gl = gamma_tilde(row_ptr, L.cur, ncur, d, gamma_mode);
-            g = (gamma_mode == GT_ALG2) ? g + gl : gl;
-            if (early_test && have_xk && bfscut_stops(f, g, d, nd, X, nx, v, Nk, Fk, idk)) {
-                stopped = 1; break;
-            }
-            uint32_t nn = 0;
-            for (uint32_t i = 0; i < ncur; ++i) {
-                uint32_t u = L.cur[i];
-                for (uint64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
-                    uint32_t w = col[e];
-                    if (L.seen[w] != L.epoch) { L.seen[w] = L.epoch; L.nxt[nn++] = w; }
-                }
-                S.m_vis += row_ptr[u + 1] - row_ptr[u];
-            }
-            if (nn == 0) break;
-            if (!early_test && have_xk && bfscut_stops(f, g, d, nd, X, nx, v, Nk, Fk, idk)) {
-                stopped = 1; break;
-            }
-            ++d;
-            nd += nn;
-            f += (uint64_t)d * nn;
-            uint32_t *t = L.cur; L.cur = L.nxt; L.nxt = t; ncur = nn;
-        }
-        if (d > S.max_level) S.max_level = d;
-        if (stopped) { S.cut++; continue; }
-        S.completed++;
-        topk_insert(&T, v, f, (uint32_t)nd);
-    }
+    bcm_loop(n, row_ptr, col, gamma_mode, early_test, xa, xb, order, 0, n, 0, 0, 1, 0, &T, &L, &S);
     for (uint32_t i = 0; i < T.cnt; ++i) { ids[i] = T.id[i]; f_out[i] = T.f[i]; r_out[i] = T.r[i]; }
     if (st) *st = S;
 done:
@@ -685,4 +703,29 @@ done:
     int64_t ret = ok ? (int64_t)T.cnt : -1;
     free(T.id); free(T.f); free(T.r);
     return ret;
+}
+
+/* Algorithm 1 over the sources of one shard, resumable (the threshold
+ * exchange of Section 2's parallel version, run between calls).  The caller
+ * gives the preprocessing results xa, xb (r(v), or alpha(v) and omega(v)),
+ * the shard's sources in processing order, and the range [from, to) to run
+ * now; ids/f/r/count (capacity k) carry the shard's top-k from call to call
+ * (count = 0 before the first).  ext_valid != 0 offers the outside key
+ * (ext_N, ext_F, ext_id).  st accumulates.  Returns the entries held, or -1
+ * on allocation failure. */
+int64_t oracle_bcm_sources(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, int directed, uint32_t k,
+                           int gamma_mode, const uint32_t *xa, const uint32_t *xb, const uint32_t *sources,
+                           uint64_t from, uint64_t to, int ext_valid, uint64_t ext_N, uint64_t ext_F,
+                           uint32_t ext_id, uint32_t *ids, uint64_t *f, uint32_t *r, uint32_t *count,
+                           bcm_oracle_stats *st) {
+    if (k == 0) return 0;
+    if (gamma_mode == GT_FOOTNOTE && directed) gamma_mode = GT_TABLE1;
+    lvl_ws L;
+    if (!lvl_init(&L, n)) { lvl_free(&L); return -1; }
+    topk_buf T = { k, *count, ids, f, r };
+    bcm_loop(n, row_ptr, col, gamma_mode, 1, xa, xb, sources, from, to, ext_valid, ext_N, ext_F, ext_id, &T, &L,
+             st);
+    lvl_free(&L);
+    *count = T.cnt;
+    return (int64_t)T.cnt;
 }

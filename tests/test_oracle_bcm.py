@@ -156,3 +156,72 @@ def test_bcm_refined_bounds_equal_exhaustive(orc, gen):
     b = orc.bcm(g, 10, refined=True)
     assert a[0].tolist() == ids.tolist() == b[0].tolist()
     assert b[3]["m_vis"] <= a[3]["m_vis"]
+
+
+def _bounds(orc, g):
+    if g.directed:
+        _, al, om, _ = orc.alpha_omega(g)
+        return al, om
+    _, r = orc.farness_all(g)
+    return r, r
+
+
+def _shard(n, index, count, chunk=64):
+    p = np.arange(n)
+    return p[(p // chunk) % count == index]
+
+
+def _key(f, r, v):
+    return (1, 0, 1, int(v)) if r <= 1 or f == 0 else (1, (int(r) - 1) ** 2, int(f), int(v))
+
+
+def test_shard_runner_whole_order_is_bcm(orc, gen):
+    """One shard holding every source, with no outside key, is Algorithm 1
+    itself, whether run at once or a few sources at a time."""
+    for g in _graphs(gen)[::3]:
+        order = orc.order(g)
+        for k in (1, 3, 10):
+            ids, f, r, st = orc.bcm(g, k)
+            for step in (g.n + 1, 7):
+                run = orc.ShardRun(g, k, order, _bounds(orc, g))
+                while not run.step(step):
+                    pass
+                gi, gf, gr, gst = run.result()
+                assert np.array_equal(gi, ids) and np.array_equal(gf, f) and np.array_equal(gr, r), (g.name, k)
+                assert gst["m_vis"] == st["m_vis"] and gst["cut"] == st["cut"], (g.name, k, step)
+
+
+@pytest.mark.parametrize("count", [2, 3])
+def test_shard_runner_with_the_global_kth_key(orc, gen, count):
+    """Offered the graph's exact k-th key, each shard still returns every
+    top-k member it holds, the merged lists are the textbook top-k, and no
+    shard scans more arcs than without the key (a stronger threshold can only
+    stop sources earlier)."""
+    with_key = without = 0
+    for g in _graphs(gen)[::2]:
+        f_all, r_all = orc.farness_all(g)
+        order = orc.order(g)
+        for k in (1, 5, 10):
+            exp = orc.topk(f_all, r_all, k)
+            if len(exp) < k:
+                continue
+            kth = _key(f_all[exp[-1]], r_all[exp[-1]], exp[-1])
+            lists = []
+            for s in range(count):
+                src = order[_shard(g.n, s, count)]
+                base = orc.ShardRun(g, k, src, _bounds(orc, g))
+                base.step(len(src) + 1)
+                run = orc.ShardRun(g, k, src, _bounds(orc, g))
+                run.offer(kth)
+                run.step(len(src) + 1)
+                ids, f, r, st = run.result()
+                assert set(exp.tolist()) & set(src.tolist()) <= set(ids.tolist()), (g.name, k, s)
+                assert st["m_vis"] <= base.result()[3]["m_vis"], (g.name, k, s)
+                with_key += st["m_vis"]
+                without += base.result()[3]["m_vis"]
+                lists.append(ids)
+            # the merge: the best k of the union (sorted by id, since the oracle's
+            # top-k breaks ties by array position)
+            cat = np.sort(np.concatenate(lists)).astype(np.uint32)
+            assert np.array_equal(cat[orc.topk(f_all[cat], r_all[cat], k)], exp), (g.name, k)
+    assert with_key < without
