@@ -270,11 +270,15 @@ bcm_status bcm_farness_all(bcm_graph_t g, const bcm_options* opt, uint64_t* farn
  *   stream           : cudaStream_t for the work (NULL = legacy default); the call
  *                      returns once it has finished.
  *   farness, reach   : DEVICE outputs, n entries each, indexed by vertex id.
- * All working memory is one fixed 64 MiB device array inside the library,
- * looked up on the first call on each device (make that first call before
- * any stream capture).  Every call on a device shares that array and clears
- * what it needs; calls whose GPU work overlaps (other streams or threads on
- * the same device) race on it and must be serialised by the caller.
+ * All working memory is one fixed 64 MiB device array inside the library;
+ * its device address is looked up on the first call on each device (make
+ * that first call before any stream capture) and kept for the life of the
+ * process.  So only the device's primary context (the runtime API's) is
+ * supported, and the device must not be reset (cudaDeviceReset) between
+ * calls.  The call is synchronous: it returns after its work on the stream
+ * has finished.  Every call on a device shares the array and clears what it
+ * needs; calls whose GPU work overlaps (other streams or threads on the same
+ * device) race on it and must be serialised by the caller.
  * Errors: BCM_ERR_INVALID (NULL pointer, malformed CSR), BCM_ERR_UNSUPPORTED,
  * BCM_ERR_CUDA, BCM_ERR_TIMEOUT; the message is in bcm_last_error().
  */

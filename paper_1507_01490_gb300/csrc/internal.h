@@ -44,9 +44,9 @@ struct GraphDev {
 // vertex.  Word index of (vertex v, word g) is v*W + g; each word has a
 // 32-byte record (vis, F[0], F[1], padding), then two frontier lists and a
 // clear log of 4-byte word indices.
-inline size_t bitmap_bytes(uint32_t n) { return ((((size_t)n + 31) / 32) * 2 * sizeof(uint32_t) + 255) & ~(size_t)255; }
+constexpr size_t bitmap_bytes(uint32_t n) { return ((((size_t)n + 31) / 32) * 2 * sizeof(uint32_t) + 255) & ~(size_t)255; }
 
-inline size_t slot_bytes(uint32_t n, int W) {
+constexpr size_t slot_bytes(uint32_t n, int W) {
     size_t nw = (size_t)n * W;
     size_t b = nw * (4 * sizeof(uint64_t) + 3 * sizeof(uint32_t));
     return (b + 255) & ~(size_t)255;

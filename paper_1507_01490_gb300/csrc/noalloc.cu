@@ -41,7 +41,16 @@ struct NoAllocHeader {
     unsigned long long stats[ST_COUNT];
 };
 
-static inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Layout: header (256 bytes) | offsets u32[n+1] | order u32[n] | CTA slots.
+constexpr size_t kHeaderBytes = 256;
+static_assert(sizeof(NoAllocHeader) <= kHeaderBytes, "the header must fit before the offsets");
+constexpr size_t noalloc_fixed_bytes(uint32_t n) {
+    return kHeaderBytes + al256(((size_t)n + 1) * 4) + al256((size_t)n * 4);
+}
+static_assert(noalloc_fixed_bytes(kNoAllocMaxN) + slot_bytes(kNoAllocMaxN, 1) <= kNoAllocBytes,
+              "at the vertex limit one CTA slot must still fit in the array");
 
 __global__ void k_noalloc_identity(uint32_t* order, uint32_t n) {
     size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -49,7 +58,10 @@ __global__ void k_noalloc_identity(uint32_t* order, uint32_t n) {
 }
 
 // Device address of the array, looked up once per device (with that device
-// current) on the first call there.
+// current) on the first call there and kept for the life of the process.
+// It belongs to the device's primary context (the one the runtime API uses);
+// a cudaDeviceReset or a call made under another context would leave it
+// stale, which is why both are outside what this entry point supports.
 static std::mutex g_noalloc_mu;
 static void* g_noalloc_ptr[64] = {nullptr};
 
@@ -104,13 +116,26 @@ extern "C" bcm_status bcm_farness_all_noalloc(const uint64_t* row_ptr, const uin
     // layout: header | 32-bit offsets | source order | CTA slots
     char* p = (char*)base;
     NoAllocHeader* hdr = (NoAllocHeader*)p;
-    uint32_t* rp32 = (uint32_t*)(p + 256);
+    uint32_t* rp32 = (uint32_t*)(p + kHeaderBytes);
     uint32_t* order = (uint32_t*)((char*)rp32 + al256(((size_t)n + 1) * 4));
     char* slots = (char*)order + al256((size_t)n * 4);
-    const size_t fixed = (size_t)(slots - p);
+    const size_t fixed = noalloc_fixed_bytes(n);
     const size_t sb = slot_bytes(n, 1);
-    int per = cta_blocks_per_sm(1, 512), sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per = cta_blocks_per_sm(1, 512);
+    if (per <= 0) {
+        const cudaError_t oe = cudaGetLastError();
+        char buf[256];
+        snprintf(buf, sizeof(buf), "bcm_farness_all_noalloc: the occupancy query of the wave kernel failed: %s",
+                 cudaGetErrorString(oe));
+        return noalloc_fail(BCM_ERR_CUDA, buf);
+    }
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess || sms <= 0) {
+        char buf[256];
+        snprintf(buf, sizeof(buf), "bcm_farness_all_noalloc: reading the SM count failed: %s", cudaGetErrorString(e));
+        return noalloc_fail(BCM_ERR_CUDA, buf);
+    }
     size_t fit = (kNoAllocBytes - fixed) / sb;
     size_t blocks = (size_t)per * (size_t)sms;
     if (blocks > fit) blocks = fit;
