@@ -16,10 +16,11 @@ against the oracle on sampled outputs.
 
 --gpus N (under torchrun, one rank per GPU) shares each step's graph among
 the N GPUs: rank r runs the top-k over its shard of the sources (every N-th
-chunk of 64 positions of the degree order), one all-gather brings the
-k-entry lists to every rank and rank 0 merges them (bcm_topk_merge) into the
-graph's top-k.  Preprocessing is repeated on every rank.  Total work per
-step is fixed, so scaling is strong.
+chunk of 64 positions of the degree order) while the ranks exchange their
+k-th keys on the host (paper_1507_01490_gb300.exchange), one all-gather
+brings the k-entry lists to every rank and rank 0 merges them
+(bcm_topk_merge) into the graph's top-k.  Preprocessing is repeated on every
+rank.  Total work per step is fixed, so scaling is strong.
 --serve runs the serving benchmark (a graph mix and request streams) and
 --sweep ratio|race the performance-ratio and positive-race sweeps instead.
 --impl reference times the CPU oracle (one BFS per source, all host cores)
@@ -49,6 +50,8 @@ WORKLOADS = {
     "ba2000": "Barabasi-Albert n=2000, m=3, seed 1",
     "chunglu256k": "Chung-Lu power-law graph, n=2^18, mean degree 10, degree exponent 2.3, seed 2 "
                    "(profiling-size case of the same recipe)",
+    "rmat18": "R-MAT scale 18, edge factor 16, (0.57,0.19,0.19,0.05), seed 3, directed "
+              "(profiling-size case of the same recipe)",
 }
 
 
@@ -557,17 +560,25 @@ def main():
     # degree order, then one all-gather brings every shard's list to every
     # rank and rank 0 merges them (bcm_topk_merge) into the graph's top-k.
     merged = {}
+    exchange_rounds = []
     if world > 1:
+        from paper_1507_01490_gb300.exchange import ThresholdExchange
         sopts = mkopt(B.BCM_OUT_DEVICE, shard_index=rank, shard_count=world)
         kloc = min(k, B.shard_size(g.n, rank, world))
         gath = [torch.zeros((world, k), dtype=t, device=dev) for t in (torch.int32, torch.int64, torch.int32)]
         cnts = torch.zeros(world, dtype=torch.int64, device=dev)
+        # the shards' k-th keys travel on the host (gloo) while the runs go on
+        xgroup = dist.new_group(backend="gloo")
 
         def shard_step(stats=None):
             h = B.bcm_graph_create(rp_d, col_d, g.n, g.m, g.directed, ptr_on_device=True,
                                    stream=stream.cuda_stream)
             try:
-                B.bcm_topk(h, k, sopts, ids_d, far_d, reach_d, stats)
+                B.bcm_topk_start(h, k, sopts, ids_d, far_d, reach_d)
+                ex = ThresholdExchange(group=xgroup, period_s=1e-4)
+                ex.run(lambda: B.bcm_topk_threshold(h), lambda key: B.bcm_topk_offer(h, key),
+                       lambda: B.bcm_topk_finish(h, wait=False, stats=stats))
+                exchange_rounds.append((ex.rounds, ex.offers))
             finally:
                 B.bcm_graph_destroy(h)
             with torch.cuda.stream(stream):
@@ -808,7 +819,10 @@ def main():
         "clocks": clk,
         "shards": None if world == 1 else {"rank0_shard_stats": {kk_: shard_stats[kk_] for kk_ in
                                                                   ("m_vis", "kernel_ms", "seed_ms", "wave_ms")},
-                                           "merged_equals_single_gpu": same_as_single},
+                                           "merged_equals_single_gpu": same_as_single,
+                                           "threshold_exchange": {
+                                               "rounds_per_step": float(np.mean([x[0] for x in exchange_rounds])),
+                                               "offers_per_step": float(np.mean([x[1] for x in exchange_rounds]))}},
         "wall_s_timed_region": t_wall,
     }
     print(json.dumps(line), flush=True)

@@ -78,6 +78,13 @@ typedef enum {
 #define BCM_NO_PREFILTER  0x400u /* no level-0/1 prefilter before the per-CTA waves (it runs on simple
                                     graphs -- sorted rows, no repeated arc, no self-loop -- after the
                                     grid-wide waves; results are the same) */
+#define BCM_NO_CUT        0x800u /* bcm_topk: no source is ever stopped by the bound, every BFS runs to its
+                                    end (Algorithm 1 without BFSCut is the textbook algorithm of Section
+                                    2.1); the top-k is the same -- a check of the cut, not a fast path */
+#define BCM_TRACE_LANES   0x1000u /* with BCM_TRACE: also record every lane's state at every level and how
+                                     it ended (record kinds 3 and 4 of bcm_trace); meant for small graphs */
+#define BCM_ALL_PULL      0x2000u /* grid-wide waves expand every level after the first by pull (a check of
+                                     the pull path; results are the same) */
 
 /* Sources are taken from the degree order in waves.  Waves run first on a
  * grid-wide kernel (all CTAs on one wave) while they are heavy, then on a
@@ -98,12 +105,15 @@ typedef struct {
     uint32_t grid_lanes;      /* sources per grid-wide wave: 64, 128 or 256; 0 = 128 */
     uint32_t flags;           /* BCM_* flags above */
     uint32_t blocks;          /* CTAs of the per-CTA kernel; 0 = all that fit on the GPU, at most
-                                 one per wave of sources (ceil(n / lanes)) */
+                                 one per wave of sources (ceil(n / lanes)), and at most as many as
+                                 keep their slots (44 n lanes/64 bytes each) within 2 GiB */
     uint32_t threads;         /* threads per CTA of the per-CTA kernel: 256, 512 or 1024; 0 = 512 */
     uint32_t heavy_words;     /* see above; 0 = default (4 per warp of the grid) */
     uint32_t pull_div;        /* a grid-wave level is expanded by pull when the out-arcs of its
                                  frontier's (vertex, word) entries number at least n*W/pull_div
-                                 (W = grid_lanes/64); 0 = default (32) */
+                                 (W = grid_lanes/64; 0 = default, 32) and at least a quarter of the
+                                 pull's estimated cost, n/4 + (n - n_min) m/n, n_min the fewest vertices
+                                 a live source has reached (so a lattice's thin frontiers stay push) */
     uint32_t defer_words;     /* a per-CTA wave about to expand a level of this many words (or of 8x
                                  as many out-arcs) stops and hands its live sources to a second
                                  grid-wide pass, which runs them from the start; 0 = default
@@ -225,6 +235,41 @@ bcm_status bcm_topk_start(bcm_graph_t g, uint32_t k, const bcm_options* opt, uin
 bcm_status bcm_topk_finish(bcm_graph_t g, int wait, bcm_stats* stats);
 
 /*
+ * bcm_key -- the rank key of one top-k entry, as the shards of one graph
+ * exchange it (Section 2: the threads of the parallel version share the
+ * current k-th value x_k):  N = (r-1)^2, F = f (N = 0, F = 1 when r = 1),
+ * id = the vertex; valid = 0 means no key.  a ranks before b iff
+ * N_a F_b > N_b F_a, or the products are equal and id_a < id_b.
+ */
+typedef struct {
+    uint64_t N, F;
+    uint32_t id, valid;
+} bcm_key;
+
+/*
+ * bcm_topk_threshold -- a consistent snapshot of the k-th key the graph's
+ * pending run has published so far (or of its last run's, once finished);
+ * valid = 0 while it holds fewer than k entries.
+ * bcm_topk_offer -- give the pending top-k run a key from outside: from then
+ * on (at its next level) the run stops sources with the better of its own
+ * k-th key and the best key offered.  Meant for the shards of one graph
+ * (bcm_options.shard_*): the k-th key of any shard is a valid threshold for
+ * all of them, because at least k vertices of the graph rank at or before
+ * it.  A shard run that was offered a key returns the best of the sources it
+ * did not stop, which still holds every member of the graph's top-k in its
+ * shard, and may hold fewer than min(k, shard size) of them: the unused
+ * entries are padding (id 0xFFFFFFFF, farness 0, reach 0), which
+ * bcm_topk_merge skips.  An offer no better than an earlier one is ignored.
+ * Both calls may be made from another thread while the run is pending (the
+ * exception to the one-thread rule above); they use the graph's helper
+ * stream, wait only for their own small copies, and do not wait for the run.
+ * Errors: BCM_ERR_INVALID (NULL pointer; offer: no top-k run pending, or a
+ * malformed key), BCM_ERR_CUDA.
+ */
+bcm_status bcm_topk_threshold(bcm_graph_t g, bcm_key* out);
+bcm_status bcm_topk_offer(bcm_graph_t g, const bcm_key* key);
+
+/*
  * bcm_trace -- the trace of the graph's last finished run made with
  * BCM_TRACE (none otherwise).  Up to cap records of 4 uint64 each are
  * copied to the host array records; *count receives how many records the
@@ -238,6 +283,16 @@ bcm_status bcm_topk_finish(bcm_graph_t g, int wait, bcm_stats* stats);
  *                                  [3] frontier entries over the wave)
  *       2  per-CTA wave end       (id = CTA;  [2] words cleared,
  *                                  [3] the wave's start time stamp)
+ *     and, with BCM_TRACE_LANES, per source v (id = v & 0xfffffff):
+ *       3  lane at level d        (Table 1's quantities before the stopping
+ *                                  rule is applied at level d: [2] f_d,
+ *                                  [3] n_d | gamma~_{d+1} << 32)
+ *       4  lane end               ([2] f_d, [3] n_d | 1 << 32 if the bound
+ *                                  stopped the source at level d; 0 << 32
+ *                                  if its BFS ended at level d, when
+ *                                  f_d = f(v) and n_d = r(v))
+ *     A source that runs twice (a per-CTA wave handing it to the grid-wide
+ *     pass, or the level-0/1 prefilter before its wave) repeats its records.
  * Records of one kind are in time order only per wave or CTA.
  */
 bcm_status bcm_trace(bcm_graph_t g, uint64_t* records, uint32_t cap, uint32_t* count);
@@ -313,9 +368,10 @@ bcm_status bcm_batch_destroy(bcm_batch_t b);
  * entries under the ranking above (exact 128-bit comparisons, equal scores
  * by id), written best first to out_ids / out_far / out_reach.  Host memory
  * only; runs on the CPU (it merges the k-entry lists of several shards,
- * whose union holds the graph's top-k).  Ids must be distinct.  Returns the
- * number of entries written in *written.  Errors: BCM_ERR_INVALID (NULL
- * pointer, k = 0), BCM_ERR_OOM.
+ * whose union holds the graph's top-k).  Ids must be distinct, except that
+ * entries with id 0xFFFFFFFF (the padding of a shard list, see
+ * bcm_topk_offer) are skipped.  Returns the number of entries written in
+ * *written.  Errors: BCM_ERR_INVALID (NULL pointer, k = 0), BCM_ERR_OOM.
  */
 bcm_status bcm_topk_merge(const uint32_t* ids, const uint64_t* farness, const uint32_t* reach, uint32_t count,
                           uint32_t k, uint32_t* out_ids, uint64_t* out_far, uint32_t* out_reach,

@@ -34,15 +34,22 @@ BCM_PLAIN_BOUNDS = 0x80
 BCM_TRACE = 0x100
 BCM_NO_DEFER = 0x200
 BCM_NO_PREFILTER = 0x400
+BCM_NO_CUT = 0x800
+BCM_TRACE_LANES = 0x1000
+BCM_ALL_PULL = 0x2000
 
 # trace record kinds (bits 60..63 of a record's second word)
-TRACE_GRID_LEVEL, TRACE_GRID_WAVE, TRACE_CTA_WAVE = 0, 1, 2
+TRACE_GRID_LEVEL, TRACE_GRID_WAVE, TRACE_CTA_WAVE, TRACE_LANE_LEVEL, TRACE_LANE_END = 0, 1, 2, 3, 4
 
 # every symbol include/bcm.h declares
 EXPORTS = ["bcm_graph_create", "bcm_graph_destroy", "bcm_preprocess", "bcm_scc_bounds", "bcm_topk",
            "bcm_topk_start", "bcm_topk_finish", "bcm_trace", "bcm_graph_trim",
            "bcm_farness_all", "bcm_farness_all_noalloc", "bcm_topk_merge", "bcm_batch_create", "bcm_batch_run",
-           "bcm_batch_destroy", "bcm_last_error", "bcm_launch_count", "bcm_workspace_bytes"]
+           "bcm_batch_destroy", "bcm_last_error", "bcm_launch_count", "bcm_workspace_bytes",
+           "bcm_topk_threshold", "bcm_topk_offer"]
+
+# id of the padding entries of a shard list (see bcm_topk_offer)
+PAD_ID = 0xFFFFFFFF
 
 
 class bcm_options(ctypes.Structure):
@@ -50,6 +57,14 @@ class bcm_options(ctypes.Structure):
                 ("blocks", ctypes.c_uint32), ("threads", ctypes.c_uint32), ("heavy_words", ctypes.c_uint32),
                 ("pull_div", ctypes.c_uint32), ("defer_words", ctypes.c_uint32), ("wait_limit_ns", ctypes.c_uint64),
                 ("shard_index", ctypes.c_uint32), ("shard_count", ctypes.c_uint32)]
+
+
+class bcm_key(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_uint64), ("F", ctypes.c_uint64), ("id", ctypes.c_uint32), ("valid", ctypes.c_uint32)]
+
+    def as_tuple(self):
+        """(valid, N, F, id)"""
+        return (int(self.valid), int(self.N), int(self.F), int(self.id))
 
 
 class bcm_stats(ctypes.Structure):
@@ -108,6 +123,8 @@ def load():
         "bcm_last_error": (ctypes.c_char_p, []),
         "bcm_launch_count": (u64, []),
         "bcm_workspace_bytes": (u64, [vp, ctypes.POINTER(bcm_options)]),
+        "bcm_topk_threshold": (i32, [vp, ctypes.POINTER(bcm_key)]),
+        "bcm_topk_offer": (i32, [vp, ctypes.POINTER(bcm_key)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -217,6 +234,20 @@ def bcm_topk_finish(h, wait=True, stats=None) -> bool:
         return False
     _check(st)
     return True
+
+
+def bcm_topk_threshold(h):
+    """The pending (or last) run's published k-th key as (valid, N, F, id)."""
+    k = bcm_key()
+    _check(load().bcm_topk_threshold(h, ctypes.byref(k)))
+    return k.as_tuple()
+
+
+def bcm_topk_offer(h, key):
+    """Offer the pending top-k run a key (valid, N, F, id) from another shard."""
+    valid, N, F, vid = key
+    k = bcm_key(N, F, vid, int(bool(valid)))
+    _check(load().bcm_topk_offer(h, ctypes.byref(k)))
 
 
 def bcm_trace(h, cap=1 << 16):

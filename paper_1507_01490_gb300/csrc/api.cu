@@ -268,10 +268,11 @@ struct Aux {
     uint32_t head;
     int err;
     Threshold thr;
+    Threshold ext;        // key offered by bcm_topk_offer (written by the host while the run goes on)
     unsigned long long stats[ST_COUNT];        // per-CTA wave kernel
     unsigned long long seed_stats[ST_COUNT];   // seed wave / plain kernel
     GridBarrier bar;
-    uint32_t gcnt[1024];
+    uint32_t gcnt[2 * kCntParity];
     uint32_t glist_n[2];
     uint32_t glog_n;
     uint32_t gchunk[2];
@@ -294,6 +295,11 @@ struct HostBlock {
     int not_simple;            // preprocessing: the simple-graph check
     unsigned long long stats[ST_COUNT];        // per-CTA wave kernel
     unsigned long long seed_stats[ST_COUNT];   // grid-wide or plain kernel
+    // bcm_topk_threshold / bcm_topk_offer staging (helper stream)
+    u64 rd_seq[2];
+    Threshold rd;
+    u64 wr_seq[2];             // odd, then even
+    Threshold wr;
 };
 
 constexpr uint32_t kTraceCap = 1u << 16;   // trace records kept per run
@@ -349,11 +355,19 @@ struct bcm_graph {
     HostBlock* h = nullptr;        // pinned
     unsigned long long* d_trace = nullptr;   // kTraceCap records of 4 words
     uint32_t trace_n = 0;          // records of the last finished traced run
+    // threshold exchange (bcm_topk_threshold / bcm_topk_offer), guarded by xmu: they may run on
+    // another thread while a run is pending
+    std::mutex xmu;
+    cudaEvent_t ev_x = nullptr;    // the run's state is cleared (recorded at its start)
+    bool offered = false;          // the pending run was given a key
+    bcm_key best{0, 0, 0, 0};      // the best key given to it
+    uint64_t xseq = 0;             // sequence count of the run's offered-key record
 };
 
 namespace {
 
 constexpr uint64_t kDefaultLimitNs = 20ull * 1000 * 1000 * 1000;
+constexpr uint64_t kCtaRegionCap = 2ull << 30;   // default bound on the per-CTA slots of a run
 
 struct Cfg {
     int W, threads, blocks, grid_W, grid_blocks;
@@ -382,9 +396,16 @@ bcm_status resolve(bcm_graph* g, const bcm_options* opt, Cfg* c) {
     if (per < 1) return fail(BCM_ERR_CUDA, "wave kernel does not fit on an SM");
     int maxb = per * g->sms;
     // default: every CTA that fits, but no more than there are waves of
-    // sources (a small graph then holds a small workspace)
+    // sources (a small graph then holds a small workspace), and no more than
+    // keep the per-CTA slots (dense in n) within kCtaRegionCap: on large
+    // graphs the grid-wide waves and the prefilter leave the per-CTA waves
+    // little to do, and a slot per resident CTA would hold tens of GB
     uint64_t waves = ((uint64_t)g->n + 64 * c->W - 1) / (64 * c->W);
     c->blocks = o.blocks ? (int)o.blocks : (waves < (uint64_t)maxb ? (int)(waves ? waves : 1) : maxb);
+    if (!o.blocks) {
+        const uint64_t fit = kCtaRegionCap / slot_bytes(g->n, c->W);
+        if ((uint64_t)c->blocks > fit) c->blocks = fit > 0 ? (int)fit : 1;
+    }
     if (c->blocks > maxb) c->blocks = maxb;
     c->limit_ns = o.wait_limit_ns ? o.wait_limit_ns : kDefaultLimitNs;
     uint32_t glanes = o.grid_lanes ? o.grid_lanes : 128;
@@ -406,10 +427,10 @@ bcm_status resolve(bcm_graph* g, const bcm_options* opt, Cfg* c) {
     return BCM_OK;
 }
 
-// CTA slots first, then one slot (4 words per vertex) for the grid-wide waves and their bitmaps.
+// CTA slots first, then one slot (4 words per vertex) for the grid-wide waves.
 size_t cta_region_bytes(bcm_graph* g, const Cfg& c) { return (size_t)c.blocks * slot_bytes(g->n, c.W); }
 size_t region_bytes(bcm_graph* g, const Cfg& c) {
-    return cta_region_bytes(g, c) + slot_bytes(g->n, 4) + bitmap_bytes(g->n);
+    return cta_region_bytes(g, c) + slot_bytes(g->n, 4);
 }
 Layout region_layout(bcm_graph* g, const Cfg& c) {
     Layout l;
@@ -614,11 +635,10 @@ WaveParams base_params(bcm_graph* g, const Cfg& c) {
     p.topk.count = &a->topk_count;
     p.topk.lock = &a->lock;
     p.topk.thr = &a->thr;
+    p.topk.ext = &a->ext;
     p.slot_base = (char*)g->slots.ptr;
     p.slot_stride = slot_bytes(g->n, c.W);
     p.seed_base = (char*)g->slots.ptr + cta_region_bytes(g, c);
-    p.gbm = (uint32_t*)(p.seed_base + slot_bytes(g->n, 4));
-    p.nbw = (g->n + 31) / 32;
     p.stats = a->stats;
     p.err = &a->err;
     p.lock_limit_ns = c.limit_ns;
@@ -742,6 +762,16 @@ bcm_status start_run(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, vo
     if (plain && !g->d_plain)
         CU(buf_get_t(&g->d_plain, (size_t)g->n * 3 * sizeof(uint32_t) + 256), "plain buffers");
     CU(cudaMemsetAsync(g->d_aux, 0, sizeof(Aux), s), "aux clear");
+    // ids of entries a run does not fill (a shard run with an offered key may hold fewer than k)
+    CU(cudaMemsetAsync(g->d_aux->topk_id, 0xff, sizeof(g->d_aux->topk_id), s), "aux clear");
+    {
+        std::lock_guard<std::mutex> lk(g->xmu);
+        if (!g->ev_x) CU(cudaEventCreateWithFlags(&g->ev_x, cudaEventDisableTiming), "event");
+        CU(cudaEventRecord(g->ev_x, s), "event record");
+        g->offered = false;
+        g->best = bcm_key{0, 0, 0, 0};
+        g->xseq = 0;
+    }
     WaveParams p = base_params(g, c);
     p.exhaustive = exhaustive ? 1u : 0u;
     p.topk.k = k;
@@ -764,7 +794,10 @@ bcm_status start_run(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, vo
         p.trace = g->d_trace;
         p.trace_cap = kTraceCap;
         p.trace_n = &g->d_aux->trace_n;
+        p.trace_lanes = (c.flags & BCM_TRACE_LANES) ? 1u : 0u;
     }
+    p.nocut = (!exhaustive && (c.flags & BCM_NO_CUT)) ? 1u : 0u;
+    p.all_pull = ((c.flags & BCM_ALL_PULL) && !(c.flags & BCM_NO_PULL)) ? 1u : 0u;
     CU(cudaEventRecord(g->ev[0], s), "event record");
     int rc = 0;
     p.stats = g->d_aux->seed_stats;
@@ -819,7 +852,7 @@ bcm_status start_run(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, vo
         // first tested at levels 0 and 1 from degrees alone; the waves take
         // the rest
         const bool prefilter = (grid || seed) && rc == 0 && g->simple &&
-                               !(c.flags & (BCM_NO_PREFILTER | BCM_GRID_ONLY));
+                               !(c.flags & (BCM_NO_PREFILTER | BCM_GRID_ONLY | BCM_NO_CUT));
         if (prefilter) {
             if (!g->d_surv) {
                 cudaError_t e = buf_get_t(&g->d_surv, (size_t)g->n * sizeof(uint32_t));
@@ -888,10 +921,19 @@ bcm_status finish_run(bcm_graph* g, bool wait, unsigned long long* sv, unsigned 
     if (!wait) {
         cudaError_t q = cudaEventQuery(g->ev[4]);
         if (q == cudaErrorNotReady) return BCM_ERR_PENDING;
-        if (q != cudaSuccess) { g->pend.active = false; return cuda_fail(q, "wave kernels"); }
+        if (q != cudaSuccess) {
+            std::lock_guard<std::mutex> lk(g->xmu);
+            g->pend.active = false;
+            return cuda_fail(q, "wave kernels");
+        }
     }
     cudaError_t se = cudaEventSynchronize(g->ev[4]);
-    g->pend.active = false;
+    bool offered = false;
+    {
+        std::lock_guard<std::mutex> lk(g->xmu);
+        g->pend.active = false;
+        offered = g->offered;
+    }
     if (se != cudaSuccess) return cuda_fail(se, "wave kernels");
     const HostBlock* h = g->h;
     float t = 0, t01 = 0, t12 = 0, t23 = 0;
@@ -915,7 +957,8 @@ bcm_status finish_run(bcm_graph* g, bool wait, unsigned long long* sv, unsigned 
         region_release(g->slots, false);
         return check_dev_err(h->err);
     }
-    if (!g->pend.exhaustive && h->topk_count != g->pend.kk)
+    // with an offered key a shard keeps only sources that rank before it: fewer entries are fine
+    if (!g->pend.exhaustive && (offered ? h->topk_count > g->pend.kk : h->topk_count != g->pend.kk))
         return fail(BCM_ERR_CUDA, "top-k holds %u entries, expected %u", h->topk_count, g->pend.kk);
     return BCM_OK;
 }
@@ -1079,6 +1122,7 @@ bcm_status bcm_graph_destroy(bcm_graph_t g) {
     }
     // a run that was started and never finished may not have left the region clean
     region_release(g->slots, !g->pend.active);
+    if (g->ev_x) cudaEventDestroy(g->ev_x);
     delete g;
     return BCM_OK;
 }
@@ -1170,6 +1214,67 @@ bcm_status bcm_topk(bcm_graph_t g, uint32_t k, const bcm_options* opt, uint32_t*
     return bcm_topk_finish(g, 1, stats);
 }
 
+namespace {
+bool key_before(const bcm_key& a, const bcm_key& b) {
+    const unsigned __int128 l = (unsigned __int128)a.N * b.F, r = (unsigned __int128)b.N * a.F;
+    if (l != r) return l > r;
+    return a.id < b.id;
+}
+}  // namespace
+
+bcm_status bcm_topk_threshold(bcm_graph_t g, bcm_key* out) {
+    t_err.clear();
+    if (!g || !out) return fail(BCM_ERR_INVALID, "a pointer argument is NULL");
+    std::lock_guard<std::mutex> lk(g->xmu);
+    *out = bcm_key{0, 0, 0, 0};
+    if (!g->d_aux || !g->ev_x || !g->aux || !g->h) return BCM_OK;   // no run yet
+    CU(cudaStreamWaitEvent(g->aux, g->ev_x, 0), "stream wait");
+    HostBlock* h = g->h;
+    const Aux* a = g->d_aux;
+    // the record's sequence count, its fields, the count again: a snapshot is
+    // consistent when both counts are equal and even (no write in between)
+    for (int tries = 0; tries < 64; ++tries) {
+        CU(cudaMemcpyAsync(&h->rd_seq[0], &a->thr.seq, sizeof(u64), cudaMemcpyDeviceToHost, g->aux), "copy");
+        CU(cudaMemcpyAsync(&h->rd, &a->thr, sizeof(Threshold), cudaMemcpyDeviceToHost, g->aux), "copy");
+        CU(cudaMemcpyAsync(&h->rd_seq[1], &a->thr.seq, sizeof(u64), cudaMemcpyDeviceToHost, g->aux), "copy");
+        CU(cudaStreamSynchronize(g->aux), "threshold copy");
+        if (h->rd_seq[0] == h->rd_seq[1] && !(h->rd_seq[0] & 1) && h->rd.seq == h->rd_seq[0]) {
+            if (h->rd.valid) *out = bcm_key{h->rd.N, h->rd.F, h->rd.id, 1};
+            return BCM_OK;
+        }
+    }
+    return BCM_OK;   // no consistent snapshot: no key (always safe)
+}
+
+bcm_status bcm_topk_offer(bcm_graph_t g, const bcm_key* key) {
+    t_err.clear();
+    if (!g || !key) return fail(BCM_ERR_INVALID, "a pointer argument is NULL");
+    std::lock_guard<std::mutex> lk(g->xmu);
+    if (!g->pend.active || g->pend.exhaustive) return fail(BCM_ERR_INVALID, "no top-k run is pending on this graph");
+    if (!key->valid) return BCM_OK;
+    if (key->F == 0 || (key->N == 0 && key->F != 1))
+        return fail(BCM_ERR_INVALID, "a key is (N, F) = ((r-1)^2, f) with f > 0, or (0, 1)");
+    if (g->best.valid && !key_before(*key, g->best)) return BCM_OK;   // not stronger than what the run has
+    HostBlock* h = g->h;
+    Aux* a = g->d_aux;
+    h->wr_seq[0] = g->xseq + 1;     // odd: write in progress
+    h->wr_seq[1] = g->xseq + 2;     // even: consistent
+    h->wr.seq = h->wr_seq[0];
+    h->wr.N = key->N;
+    h->wr.F = key->F;
+    h->wr.id = key->id;
+    h->wr.valid = 1;
+    CU(cudaStreamWaitEvent(g->aux, g->ev_x, 0), "stream wait");
+    CU(cudaMemcpyAsync(&a->ext.seq, &h->wr_seq[0], sizeof(u64), cudaMemcpyHostToDevice, g->aux), "copy");
+    CU(cudaMemcpyAsync(&a->ext, &h->wr, sizeof(Threshold), cudaMemcpyHostToDevice, g->aux), "copy");
+    CU(cudaMemcpyAsync(&a->ext.seq, &h->wr_seq[1], sizeof(u64), cudaMemcpyHostToDevice, g->aux), "copy");
+    CU(cudaStreamSynchronize(g->aux), "offer copy");
+    g->xseq += 2;
+    g->best = *key;
+    g->offered = true;
+    return BCM_OK;
+}
+
 bcm_status bcm_farness_all(bcm_graph_t g, const bcm_options* opt, uint64_t* farness, uint32_t* reach,
                            bcm_stats* stats) {
     t_err.clear();
@@ -1251,7 +1356,10 @@ bcm_status bcm_topk_merge(const uint32_t* ids, const uint64_t* farness, const ui
     } catch (...) {
         return fail(BCM_ERR_OOM, "host allocation");
     }
-    for (uint32_t i = 0; i < count; ++i) idx[i] = i;
+    uint32_t used = 0;
+    for (uint32_t i = 0; i < count; ++i)
+        if (ids[i] != 0xffffffffu) idx[used++] = i;   // padding of a shard list that holds fewer than k
+    idx.resize(used);
     // (N, F) = ((r-1)^2, f), or (0, 1) when r <= 1; a before b iff
     // N_a F_b > N_b F_a, or equal and id_a < id_b
     auto key = [&](uint32_t i, unsigned __int128& N, unsigned __int128& F) {
@@ -1269,7 +1377,7 @@ bcm_status bcm_topk_merge(const uint32_t* ids, const uint64_t* farness, const ui
         if (l != r) return l > r;
         return ids[a] < ids[b];
     };
-    const uint32_t w = k < count ? k : count;
+    const uint32_t w = k < used ? k : used;
     std::partial_sort(idx.begin(), idx.begin() + w, idx.end(), before);
     for (uint32_t i = 0; i < w; ++i) {
         out_ids[i] = ids[idx[i]];

@@ -114,8 +114,22 @@ struct TopK {
     u32* count;       // entries held (<= k)
     u32* lock;        // 0 free, 1 held
     Threshold* thr;   // published k-th key
+    Threshold* ext;   // a key offered from outside the run (another shard's k-th), or NULL
     u32 k;
 };
+
+// The threshold a run cuts with: its own published k-th key or the offered
+// one, whichever ranks first.  Both are valid: the offered key is the k-th of
+// another shard of the same graph, and at least k vertices of the graph rank
+// at or before it, so a source ranking after it cannot be in the top-k.
+__device__ __forceinline__ void read_thresholds(const TopK& T, ThrCache& c) {
+    read_threshold(T.thr, c);
+    if (!T.ext || vload(&T.ext->seq) == 0) return;   // nothing offered (yet)
+    ThrCache e;
+    e.valid = 0; e.N = 0; e.F = 1; e.id = 0;
+    read_threshold(T.ext, e);
+    if (e.valid && (!c.valid || ranks_before(e.N, e.F, e.id, c.N, c.F, c.id))) c = e;
+}
 
 __device__ __forceinline__ bool lock_acquire(u32* lock, u64 limit_ns, int* err) {
     u64 t0 = global_ns();

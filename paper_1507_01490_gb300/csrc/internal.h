@@ -44,13 +44,18 @@ struct GraphDev {
 // vertex.  Word index of (vertex v, word g) is v*W + g; each word has a
 // 32-byte record (vis, F[0], F[1], padding), then two frontier lists and a
 // clear log of 4-byte word indices.
-constexpr size_t bitmap_bytes(uint32_t n) { return ((((size_t)n + 31) / 32) * 2 * sizeof(uint32_t) + 255) & ~(size_t)255; }
-
 constexpr size_t slot_bytes(uint32_t n, int W) {
     size_t nw = (size_t)n * W;
     size_t b = nw * (4 * sizeof(uint64_t) + 3 * sizeof(uint32_t));
     return (b + 255) & ~(size_t)255;
 }
+
+// The grid kernel's per-lane level counters are summed in kCntCopies copies
+// (block b adds into copy b % kCntCopies, and every block sums the copies
+// after the barrier): 304 blocks adding into one set of 512 words made the
+// adds queue on a few cache lines.
+constexpr uint32_t kCntCopies = 16;
+constexpr uint32_t kCntParity = kCntCopies * 512;   // u32 per level parity
 
 // A frontier word whose vertex has many out-arcs, queued so that every warp
 // can take a share of its arcs.
@@ -73,15 +78,14 @@ struct WaveParams {
     char* slot_base;         // CTA i: slot_base + i * slot_stride
     size_t slot_stride;
     char* seed_base;         // the grid kernel's own slot (4 words per vertex)
-    uint32_t* gbm;           // grid kernel: two frontier bitmaps of nbw words (one bit per vertex), zero between runs
-    uint32_t nbw;
     unsigned long long* stats;   // [ST_COUNT]
     int* err;
     unsigned long long lock_limit_ns;
     unsigned long long barrier_limit_ns;
     // grid-wide (seed / plain) kernels only
     GridBarrier* bar;
-    uint32_t* gcnt;          // [2][2][256] per-lane level counters (gamma, degree sum)
+    uint32_t* gcnt;          // [2][kCntCopies][2][256] per-lane level counters (gamma, degree sum) by
+                             // level parity, in copies that blocks add into by blockIdx % kCntCopies
     uint32_t* glist_n;       // [2] frontier list sizes
     uint32_t* glog_n;        // [1] cleared-word log size
     uint32_t* gchunk;        // [2] chunk counters of the frontier lists
@@ -92,6 +96,7 @@ struct WaveParams {
     uint32_t max_grid_waves;  // grid kernel: at most this many waves
     uint64_t heavy_words;   // grid kernel: a wave with fewer frontier words in total is light
     uint32_t pull_div;      // grid kernel: pull a level whose frontier words have >= n*W/pull_div out-arcs (0: never)
+    uint32_t all_pull;      // grid kernel: pull every level after the first (a check of the pull path)
     // per-CTA kernel: a wave about to expand a level of at least defer_words
     // words, or of at least 8 * defer_words out-arcs, is given up and its
     // live sources appended to defer_src (0: never)
@@ -106,10 +111,12 @@ struct WaveParams {
     unsigned long long* trace;
     uint32_t trace_cap;      // records
     uint32_t* trace_n;       // records written (may exceed trace_cap; the excess is dropped)
+    uint32_t trace_lanes;    // also record every lane's level state and end (needs trace)
+    uint32_t nocut;          // top-k runs: never stop a source (every BFS runs to its end)
 };
 
 // Trace record kinds (bits 60..63 of a record's second word).
-enum TraceKind { TR_GRID_LEVEL = 0, TR_GRID_WAVE = 1, TR_CTA_WAVE = 2 };
+enum TraceKind { TR_GRID_LEVEL = 0, TR_GRID_WAVE = 1, TR_CTA_WAVE = 2, TR_LANE_LEVEL = 3, TR_LANE_END = 4 };
 
 // ---- preproc.cu
 int launch_validate(const uint64_t* rp64, const uint32_t* col, uint32_t n, uint64_t m, int* err,
@@ -157,6 +164,7 @@ int launch_cta_waves(const WaveParams& p, int W, int blocks, int threads, cudaSt
 int launch_prefilter(const WaveParams& p, uint32_t* out, uint32_t* out_n, cudaStream_t s);
 int launch_plain_source(const WaveParams& p, uint32_t it, uint32_t* stamp, uint32_t* lists,
                         int blocks, int threads, cudaStream_t s);
+
 int max_coop_blocks(int kind, int W, int threads);   // kind 0 grid waves, 1 plain
 int cta_blocks_per_sm(int W, int threads);
 

@@ -31,13 +31,22 @@
 
 namespace bcm {
 
-// The three bit words of one (vertex, 64-lane word) pair -- vis, F[0], F[1]
-// -- sit in one 32-byte record, so a push's check and atomics and the
-// wave-end clear touch a single sector.  vis, F[0] and F[1] below are
-// pointers to the fields; ri(word) is the stride to a word's record.
-constexpr int REC = 4;   // u64 per record (the fourth is padding)
+// Two layouts of the bit words of a (vertex, 64-lane word) pair -- vis,
+// F[0], F[1] -- chosen per kernel by the template parameter R, the stride
+// between consecutive words of one array:
+//   R = 4  records: the three words sit in one 32-byte record (the fourth
+//          u64 is padding), so a push's check and atomics and the wave-end
+//          clear touch a single sector (per-CTA waves: push only);
+//   R = 1  planes: each array is its own plane, and the W words of a vertex
+//          are consecutive in it, so a pulled level reads the vis words of 32
+//          consecutive vertices in one coalesced sweep and an in-neighbour's
+//          frontier words in one sector (grid-wide waves).
+// vis, F[0] and F[1] below point at word 0 of each array; ri<R>(word) is the
+// offset of a word.
+constexpr int REC = 4;
 
-__device__ __forceinline__ size_t ri(u32 word) { return (size_t)word * REC; }
+template <int R>
+__device__ __forceinline__ size_t ri(u32 word) { return (size_t)word * R; }
 
 struct SlotPtrs {
     u64* vis;
@@ -46,22 +55,37 @@ struct SlotPtrs {
     u32* clog;
 };
 
+// n vertices with W words each (the arrays' capacity; a run may use fewer).
+template <int R>
 __device__ __forceinline__ SlotPtrs slot_ptrs(char* base, u32 n, int W) {
     size_t nw = (size_t)n * W;
     SlotPtrs s;
     s.vis = (u64*)base;
-    s.F[0] = s.vis + 1;
-    s.F[1] = s.vis + 2;
-    s.list[0] = (u32*)(s.vis + REC * nw);
+    if (R == 1) {
+        s.F[0] = s.vis + nw;
+        s.F[1] = s.vis + 2 * nw;
+        s.list[0] = (u32*)(s.vis + 3 * nw);
+    } else {
+        s.F[0] = s.vis + 1;
+        s.F[1] = s.vis + 2;
+        s.list[0] = (u32*)(s.vis + REC * nw);
+    }
     s.list[1] = s.list[0] + nw;
     s.clog = s.list[1] + nw;
     return s;
 }
 
-__device__ __forceinline__ void clear_record(u64* vis, u32 word) {
-    ulonglong2* r = (ulonglong2*)&vis[ri(word)];
-    r[0] = make_ulonglong2(0, 0);
-    r[1] = make_ulonglong2(0, 0);
+template <int R>
+__device__ __forceinline__ void clear_word(const SlotPtrs& S, u32 word) {
+    if (R == 1) {
+        S.vis[word] = 0;
+        S.F[0][word] = 0;
+        S.F[1][word] = 0;
+    } else {
+        ulonglong2* r = (ulonglong2*)&S.vis[ri<R>(word)];
+        r[0] = make_ulonglong2(0, 0);
+        r[1] = make_ulonglong2(0, 0);
+    }
 }
 
 // Counters of the expansion loops, per thread (kept small: they live in
@@ -129,6 +153,15 @@ __device__ __forceinline__ void trace_record(const WaveParams& p, u32 kind, u32 
     r[3] = b;
 }
 
+// Lane records (BCM_TRACE_LANES): source v's Table 1 state before the
+// stopping rule at level d, and how its BFS ended.
+__device__ __noinline__ void lane_level(const WaveParams& p, u32 v, u32 d, u64 f, u32 nd, u32 gt) {
+    trace_record(p, TR_LANE_LEVEL, v, d, f, (u64)nd | ((u64)gt << 32), global_ns());
+}
+__device__ __noinline__ void lane_end(const WaveParams& p, u32 v, u32 d, u64 f, u32 nd, bool cut) {
+    trace_record(p, TR_LANE_END, v, d, f, (u64)nd | ((u64)(cut ? 1u : 0u) << 32), global_ns());
+}
+
 // ------------------------------------------------------- staged appends
 // Frontier and clear-log appends go first to a per-warp staging area in
 // shared memory and reach the list with one counter reservation per flush:
@@ -180,10 +213,10 @@ __device__ __forceinline__ void push_load(const u32* __restrict__ col, u32 e, u6
     q.g = g;
 }
 
-template <int W>
+template <int W, int R>
 __device__ __forceinline__ void push_check(const u32* __restrict__ rp, const u64* vis, Push& q) {
     q.word = q.x * W + q.g;
-    q.nb = q.F & ~__ldcg(&vis[ri(q.word)]);
+    q.nb = q.F & ~__ldcg(&vis[ri<R>(q.word)]);
     q.fl = 0;
     q.degp = 0;
     if (q.nb) {
@@ -192,21 +225,22 @@ __device__ __forceinline__ void push_check(const u32* __restrict__ rp, const u64
     }
 }
 
+template <int R>
 __device__ __forceinline__ void push_vis(u64* vis, Push& q, u64& old) {
-    old = q.nb ? atomicOr(&vis[ri(q.word)], q.nb) : ~0ull;
+    old = q.nb ? atomicOr(&vis[ri<R>(q.word)], q.nb) : ~0ull;
 }
 
-__device__ __forceinline__ void push_next(u64* Fnext, Push& q, u64 old, u32 foot, LocalStats& st, u32* bmn) {
+template <int R>
+__device__ __forceinline__ void push_next(u64* Fnext, Push& q, u64 old, u32 foot, LocalStats& st) {
     if (!q.nb) return;
     q.fl = (old == 0) ? 2u : 0u;
     q.nb &= ~old;
     if (!q.nb) return;
-    u64 oldF = atomicOr(&Fnext[ri(q.word)], q.nb);
+    u64 oldF = atomicOr(&Fnext[ri<R>(q.word)], q.nb);
     if (oldF == 0) {
         q.fl |= 1u;
         st.discwords++;
         st.fwarcs += q.r1 - q.r0;
-        if (bmn) atomicOr(&bmn[q.x >> 5], 1u << (q.x & 31));   // x is in the next frontier
     }
     q.degp = q.r1 - q.r0 - foot;
     st.disc += __popcll(q.nb);
@@ -332,11 +366,11 @@ __device__ inline void source_prefix(const GraphDev& G, const u32* s_src, const 
 // warps instead of one warp per source.  Each source's own bit is set by one
 // thread; an arc back to the lane's own source (a self-loop) is skipped, so
 // no arc can find the source before its bit is set.
-template <int W>
+template <int W, int R>
 __device__ inline void expand_sources(const GraphDev& G, const u32* s_src, const u32* s_alive32, const u32* s_pre,
                                       const u32* s_beg, int L, u64* vis, u64* Fnext, u32* cg, u32* cs, u32 foot,
                                       WarpQueue& nq, WarpQueue& lq, u32 wid, u32 nw, u32 tid, u32 nthreads,
-                                      LocalStats& st, u32* bmn) {
+                                      LocalStats& st) {
     const u32 lane = threadIdx.x & 31;
     lq.reserve(32);
     for (u32 j0 = tid - lane; j0 < (u32)L; j0 += nthreads) {
@@ -346,7 +380,7 @@ __device__ inline void expand_sources(const GraphDev& G, const u32* s_src, const
         if (j < (u32)L && ((s_alive32[j >> 5] >> (j & 31)) & 1u)) {
             const u32 deg = s_pre[j + 1] - s_pre[j];
             word = s_src[j] * W + (j >> 6);
-            first = atomicOr(&vis[ri(word)], 1ull << (j & 63)) == 0;
+            first = atomicOr(&vis[ri<R>(word)], 1ull << (j & 63)) == 0;
             st.mvis += deg;
             st.arcwords += deg;
         }
@@ -372,10 +406,10 @@ __device__ inline void expand_sources(const GraphDev& G, const u32* s_src, const
         nq.reserve(32);
         lq.reserve(32);
         if (v) {
-            push_check<W>(G.rp, vis, q);
+            push_check<W, R>(G.rp, vis, q);
             u64 old;
-            push_vis(vis, q, old);
-            push_next(Fnext, q, old, foot, st, bmn);
+            push_vis<R>(vis, q, old);
+            push_next<R>(Fnext, q, old, foot, st);
         } else {
             q.nb = 0;
         }
@@ -387,7 +421,7 @@ __device__ inline void expand_sources(const GraphDev& G, const u32* s_src, const
 // the warp that reads them: they go to a heavy list, and once every warp is
 // past the main pass, all warps share their arcs (expand_heavy).  A list
 // that is full leaves the entry with its warp.
-constexpr u32 kHeavyArcs = 1024;
+constexpr u32 kHeavyArcs = 256;
 constexpr u32 kHeavyCapCta = 64;
 struct HeavyList {
     HeavyEntry* e;
@@ -399,24 +433,36 @@ struct HeavyList {
 // from a shared counter (so a chunk holding a high-degree vertex does not
 // hold back the others), form the exclusive scan of the chunk's degrees and
 // walk the combined arc range 64 arcs at a time, two per thread.
-template <int W>
+template <int W, int R>
 __device__ inline void expand_entries(const GraphDev& G, const u32* list, u32 cnt, u64* Fcur,
                                       const u32* s_alive32, u64* vis, u64* Fnext, u32* cg, u32* cs,
-                                      u32 foot, WarpQueue& nq, WarpQueue& lq, u32* chunk_ctr, u32 nw,
-                                      const HeavyList& H, LocalStats& st, u32* bmn) {
+                                      u32 foot, WarpQueue& nq, WarpQueue& lq, u32* chunk_ctr, u32 wid, u32 nw,
+                                      const HeavyList& H, LocalStats& st) {
     const u32 lane = threadIdx.x & 31;
-    // entries taken per counter reservation: 32 when the frontier is small,
-    // up to 256 when it is large enough to keep every warp busy anyway
+    // entries taken per chunk: 32 when the frontier is small, up to 256 when
+    // it is large enough to keep every warp busy anyway.  Warp wid's first
+    // chunk is the wid-th; the rest come from the shared counter, which only
+    // runs past the first nw chunks -- a narrow level then costs no atomic.
     u32 grab = cnt / (nw * 8u);
     grab = grab < 32u ? 32u : (grab > 256u ? 256u : (grab & ~31u));
+    const u64 fixed = (u64)nw * grab;
     u32 base = 0, lim = 0;
+    bool first = true;
     for (;;) {
         if (base >= lim) {
-            u32 b = 0;
-            if (lane == 0) b = atomicAdd(chunk_ctr, grab);
-            base = __shfl_sync(0xffffffffu, b, 0);
+            // the warp's own first chunk, then chunks from the shared counter;
+            // every path either takes a chunk below cnt or leaves the loop
+            u64 b = first ? (u64)wid * grab : ~0ull;
+            first = false;
+            if (b >= cnt) {
+                if (fixed >= cnt) break;   // all entries lie in the first chunks
+                u32 c = 0;
+                if (lane == 0) c = atomicAdd(chunk_ctr, grab);
+                b = fixed + __shfl_sync(0xffffffffu, c, 0);
+                if (b >= cnt) break;
+            }
+            base = (u32)b;
             lim = base + grab < cnt ? base + grab : cnt;
-            if (base >= cnt) break;
         }
         const u32 e = base + lane;
         base += 32;
@@ -426,8 +472,8 @@ __device__ inline void expand_entries(const GraphDev& G, const u32* list, u32 cn
             u32 word = __ldcg(&list[e]);
             u32 u = word / W;
             g = word - u * W;
-            F = __ldcg(&Fcur[ri(word)]);
-            Fcur[ri(word)] = 0;
+            F = __ldcg(&Fcur[ri<R>(word)]);
+            Fcur[ri<R>(word)] = 0;
             F &= ((u64)s_alive32[2 * g + 1] << 32) | s_alive32[2 * g];
             st.entries++;
             if (F) {
@@ -479,12 +525,12 @@ __device__ inline void expand_entries(const GraphDev& G, const u32* list, u32 cn
             lq.reserve(64);
 #pragma unroll
             for (int h = 0; h < 2; ++h)
-                if (v[h]) push_check<W>(G.rp, vis, q[h]);
+                if (v[h]) push_check<W, R>(G.rp, vis, q[h]);
             u64 old[2];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) push_vis(vis, q[h], old[h]);
+            for (int h = 0; h < 2; ++h) push_vis<R>(vis, q[h], old[h]);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) push_next(Fnext, q[h], old[h], foot, st, bmn);
+            for (int h = 0; h < 2; ++h) push_next<R>(Fnext, q[h], old[h], foot, st);
 #pragma unroll
             for (int h = 0; h < 2; ++h) push_finish(q[h], cg, cs, nq, lq);
         }
@@ -493,10 +539,10 @@ __device__ inline void expand_entries(const GraphDev& G, const u32* list, u32 cn
 
 // The heavy list's arcs, 64 at a time, piece c to warp c mod nw (warp wid
 // of nw); run by every warp after all of them have left expand_entries.
-template <int W>
+template <int W, int R>
 __device__ __noinline__ void expand_heavy(const GraphDev& G, const HeavyEntry* H, u32 hn, u64* vis, u64* Fnext,
                                     u32* cg, u32* cs, u32 foot, WarpQueue& nq, WarpQueue& lq, u32 wid, u32 nw,
-                                    LocalStats& st, u32* bmn) {
+                                    LocalStats& st) {
     const u32 lane = threadIdx.x & 31;
     u32 base = 0;   // pieces in the batches before this one
     for (u32 h0 = 0; h0 < hn; h0 += 32) {
@@ -546,12 +592,12 @@ __device__ __noinline__ void expand_heavy(const GraphDev& G, const HeavyEntry* H
             lq.reserve(64);
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh)
-                if (v[hh]) push_check<W>(G.rp, vis, q[hh]);
+                if (v[hh]) push_check<W, R>(G.rp, vis, q[hh]);
             u64 old[2];
 #pragma unroll
-            for (int hh = 0; hh < 2; ++hh) push_vis(vis, q[hh], old[hh]);
+            for (int hh = 0; hh < 2; ++hh) push_vis<R>(vis, q[hh], old[hh]);
 #pragma unroll
-            for (int hh = 0; hh < 2; ++hh) push_next(Fnext, q[hh], old[hh], foot, st, bmn);
+            for (int hh = 0; hh < 2; ++hh) push_next<R>(Fnext, q[hh], old[hh], foot, st);
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh) push_finish(q[hh], cg, cs, nq, lq);
         }
@@ -582,21 +628,64 @@ constexpr int kPullUnroll = BCM_PULL_UNROLL;   // in-neighbours per step of a th
 #endif
 constexpr int kPullCoop = BCM_PULL_COOP;   // in-neighbours per thread and step of a warp's scan
 
+// The W words of one vertex in a plane (R = 1 layout), as 16-byte loads and stores.
+template <int W>
+__device__ __forceinline__ void load_words_cg(const u64* p, u64 (&w)[W]) {
+    if (W == 1) {
+        w[0] = __ldcg(p);
+    } else {
+#pragma unroll
+        for (int i = 0; i < W; i += 2) {
+            const ulonglong2 t = __ldcg((const ulonglong2*)(p + i));
+            w[i] = t.x;
+            w[i + 1] = t.y;
+        }
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void store_words(u64* p, const u64 (&w)[W]) {
+    if (W == 1) {
+        p[0] = w[0];
+    } else {
+#pragma unroll
+        for (int i = 0; i < W; i += 2) *(ulonglong2*)(p + i) = make_ulonglong2(w[i], w[i + 1]);
+    }
+}
+
+// Grid-wide waves only (planar layout).  An in-neighbour outside the
+// frontier has zero frontier words, so its words are loaded without first
+// asking whether it is in the frontier: one sector either way, and a
+// one-bit-per-vertex frontier map in front of it was a second dependent
+// load that measured slower on every workload.
 template <int W>
 __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32* s_alive32, u64* vis, u64* Fnext,
                                   u32* cg, u32* cs, u32 foot, WarpQueue& nq, WarpQueue& lq, u32* chunk_ctr,
-                                  LocalStats& st, const u32* bmc, u32* bmn) {
+                                  u32 wid, u32 nw, LocalStats& st) {
     const u32 lane = threadIdx.x & 31;
+    constexpr u32 NONE = 0xffffffffu;
     u64 alive[W];
 #pragma unroll
     for (int g = 0; g < W; ++g) alive[g] = ((u64)s_alive32[2 * g + 1] << 32) | s_alive32[2 * g];
-    // 32 consecutive vertices at a time from a shared counter (a warp held
-    // up by a large in-list takes fewer chunks)
+    // batches of 32 consecutive vertices: about three quarters of them dealt
+    // out in turn (warp wid takes wid, wid + nw, ...), the rest from a shared
+    // counter (a warp held up by a large in-list takes fewer of those), so
+    // that most batches cost no atomic on the one counter
+    const u32 nb = (G.n + 31) / 32;
+    const u32 dealt = ((nb / 4) * 3 / nw) * nw;
+    u32 next = wid;
     for (;;) {
-        u32 x0 = 0;
-        if (lane == 0) x0 = atomicAdd(chunk_ctr, 32u);
-        x0 = __shfl_sync(0xffffffffu, x0, 0);
-        if (x0 >= G.n) break;
+        u32 bi;
+        if (next < dealt) {
+            bi = next;
+            next += nw;
+        } else {
+            u32 c = 0;
+            if (lane == 0) c = atomicAdd(chunk_ctr, 1u);
+            bi = dealt + __shfl_sync(0xffffffffu, c, 0);
+        }
+        if (bi >= nb) break;
+        const u32 x0 = bi * 32;
         const u32 x = x0 + lane;
         u64 pend[W], acc[W], v0[W];
         bool any = false;
@@ -610,9 +699,9 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
             b = __ldg(&G.rrp[x]);
             e = __ldg(&G.rrp[x + 1]);
             dx = __ldg(&G.rp[x + 1]) - __ldg(&G.rp[x]);
+            load_words_cg<W>(&vis[(size_t)x * W], v0);
 #pragma unroll
             for (int g = 0; g < W; ++g) {
-                v0[g] = __ldcg(&vis[ri(x * W + g)]);
                 pend[g] = alive[g] & ~v0[g];
                 any = any || pend[g] != 0;
             }
@@ -626,23 +715,18 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
             while (i < e) {
                 u32 u[kPullUnroll];
 #pragma unroll
-                for (int j = 0; j < kPullUnroll; ++j) u[j] = i + j < e ? __ldg(&G.rcol[i + j]) : 0xffffffffu;
-                // in-neighbours outside the current frontier have no frontier words
+                for (int j = 0; j < kPullUnroll; ++j) u[j] = i + j < e ? __ldg(&G.rcol[i + j]) : NONE;
 #pragma unroll
-                for (int j = 0; j < kPullUnroll; ++j)
-                    if (u[j] != 0xffffffffu && !((__ldcg(&bmc[u[j] >> 5]) >> (u[j] & 31)) & 1u)) u[j] = 0xffffffffu;
+                for (int j = 0; j < kPullUnroll; ++j) {
+                    if (u[j] == NONE) continue;
+                    u64 w[W];
+                    load_words_cg<W>(&Fcur[(size_t)u[j] * W], w);
+#pragma unroll
+                    for (int g = 0; g < W; ++g) acc[g] |= w[g];
+                }
                 bool done = true;
 #pragma unroll
-                for (int g = 0; g < W; ++g) {
-                    if (pend[g] & ~acc[g]) {
-                        u64 f = 0;
-#pragma unroll
-                        for (int j = 0; j < kPullUnroll; ++j)
-                            if (u[j] != 0xffffffffu) f |= __ldcg(&Fcur[ri(u[j] * W + g)]);
-                        acc[g] |= f;
-                    }
-                    done = done && !(pend[g] & ~acc[g]);
-                }
+                for (int g = 0; g < W; ++g) done = done && !(pend[g] & ~acc[g]);
                 i = i + kPullUnroll < e ? i + kPullUnroll : e;
                 if (done) break;
             }
@@ -664,32 +748,30 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
             }
             // kPullCoop arcs per thread and step: a hub's in-list is the
             // level's longest chain of dependent loads, so each step puts
-            // kPullCoop independent col / bitmap / frontier loads in flight
+            // kPullCoop independent col / frontier-word loads in flight
             u32 i = cb;
             for (; i < ce; i += 32 * kPullCoop) {
                 u32 u[kPullCoop];
 #pragma unroll
                 for (int j = 0; j < kPullCoop; ++j) {
                     const u32 a = i + 32 * j + lane;
-                    u[j] = a < ce ? __ldg(&G.rcol[a]) : 0xffffffffu;
+                    u[j] = a < ce ? __ldg(&G.rcol[a]) : NONE;
                 }
-#pragma unroll
-                for (int j = 0; j < kPullCoop; ++j)
-                    if (u[j] != 0xffffffffu && !((__ldcg(&bmc[u[j] >> 5]) >> (u[j] & 31)) & 1u)) u[j] = 0xffffffffu;
                 u64 f[W];
 #pragma unroll
-                for (int g = 0; g < W; ++g) {
-                    f[g] = 0;
-                    if (cp[g] & ~ca[g]) {
+                for (int g = 0; g < W; ++g) f[g] = 0;
 #pragma unroll
-                        for (int j = 0; j < kPullCoop; ++j)
-                            if (u[j] != 0xffffffffu) f[g] |= __ldcg(&Fcur[ri(u[j] * W + g)]);
-                        f[g] &= cp[g];
-                    }
+                for (int j = 0; j < kPullCoop; ++j) {
+                    if (u[j] == NONE) continue;
+                    u64 w[W];
+                    load_words_cg<W>(&Fcur[(size_t)u[j] * W], w);
+#pragma unroll
+                    for (int g = 0; g < W; ++g) f[g] |= w[g];
                 }
                 bool done = true;
 #pragma unroll
                 for (int g = 0; g < W; ++g) {
+                    f[g] &= cp[g];
                     const u32 lo = __reduce_or_sync(0xffffffffu, (u32)f[g]);
                     const u32 hi = __reduce_or_sync(0xffffffffu, (u32)(f[g] >> 32));
                     ca[g] |= ((u64)hi << 32) | lo;
@@ -706,6 +788,7 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
         }
         u64 nb[W];
         u32 degp = 0;
+        bool found = false;
 #pragma unroll
         for (int g = 0; g < W; ++g) nb[g] = 0;
         if (any) {
@@ -714,20 +797,19 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
             for (int g = 0; g < W; ++g) {
                 nb[g] = acc[g] & pend[g];
                 if (nb[g]) {
-                    vis[ri(x * W + g)] = v0[g] | nb[g];
-                    Fnext[ri(x * W + g)] = nb[g];
                     st.disc += __popcll(nb[g]);
                     st.discwords++;
                     st.fwarcs += degp + foot;
+                    found = true;
                 }
             }
-        }
-        {   // the warp's 32 vertices share one bitmap word (x0 is a multiple of 32)
-            bool found = false;
+            if (found) {   // x's own words: no other thread touches them in a pulled level
+                u64 nv[W];
 #pragma unroll
-            for (int g = 0; g < W; ++g) found = found || nb[g] != 0;
-            const u32 word = __ballot_sync(0xffffffffu, found);
-            if (lane == 0 && word) bmn[x0 >> 5] = word;
+                for (int g = 0; g < W; ++g) nv[g] = v0[g] | nb[g];
+                store_words<W>(&vis[(size_t)x * W], nv);
+                store_words<W>(&Fnext[(size_t)x * W], nb);   // zero where nothing was found: they were zero
+            }
         }
 #pragma unroll
         for (int g = 0; g < W; ++g) {
@@ -744,6 +826,7 @@ __device__ inline void pull_level(const GraphDev& G, const u64* Fcur, const u32*
 // entries per thread are loaded before any of their stores, so the loads
 // are in flight together (the stores could alias the list as far as the
 // compiler knows).
+template <int R>
 __device__ inline void pull_clear(const u32* list, u32 cnt, u64* Fcur, u32 gtid, u32 gthreads) {
     u64 i = gtid;
     for (; i + 3ull * gthreads < cnt; i += 4ull * gthreads) {
@@ -751,9 +834,9 @@ __device__ inline void pull_clear(const u32* list, u32 cnt, u64* Fcur, u32 gtid,
 #pragma unroll
         for (int j = 0; j < 4; ++j) w[j] = __ldcg(&list[i + (u64)j * gthreads]);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) Fcur[ri(w[j])] = 0;
+        for (int j = 0; j < 4; ++j) Fcur[ri<R>(w[j])] = 0;
     }
-    for (; i < cnt; i += gthreads) Fcur[ri(__ldcg(&list[i]))] = 0;
+    for (; i < cnt; i += gthreads) Fcur[ri<R>(__ldcg(&list[i]))] = 0;
 }
 
 // Completed lanes: exhaustive runs write (f, r) by vertex id; top-k runs
@@ -874,7 +957,7 @@ __global__ void __launch_bounds__(256) k_prefilter(WaveParams p, u32* out, u32* 
     const GraphDev& G = p.g;
     if (threadIdx.x == 0) {
         s_thr.valid = 0; s_thr.N = 0; s_thr.F = 1; s_thr.id = 0;
-        read_threshold(p.topk.thr, s_thr);
+        read_thresholds(p.topk, s_thr);
         s_begin = vload(p.head);
     }
     bstat_init(s_bst);
@@ -898,6 +981,7 @@ __global__ void __launch_bounds__(256) k_prefilter(WaveParams p, u32* out, u32* 
             b = __ldg(&G.rp[v]);
             deg = __ldg(&G.rp[v + 1]) - b;
         }
+        if (!done && p.trace_lanes) lane_level(p, v, 0, 0, 1, deg);
         if (!done && deg == 0) {
             // R(v) = {v}: complete with key (0, 1); it only goes on (to be
             // merged by a wave) if it ranks before the k-th
@@ -905,6 +989,7 @@ __global__ void __launch_bounds__(256) k_prefilter(WaveParams p, u32* out, u32* 
             if (!ranks_before(0, 1, v, s_thr.N, s_thr.F, s_thr.id)) {
                 cut = true;
                 bstat_add(s_bst, ST_COMPLETED, 1);
+                if (p.trace_lanes) lane_end(p, v, 0, 0, 1, false);
             }
         }
         if (!done) {
@@ -913,6 +998,7 @@ __global__ void __launch_bounds__(256) k_prefilter(WaveParams p, u32* out, u32* 
             if (bfscut_stops(0, deg, 0, 1, xlo, xhi, v, s_thr)) {
                 cut = done = true;
                 bstat_add(s_bst, ST_CUT, 1);
+                if (p.trace_lanes) lane_end(p, v, 0, 0, 1, true);
             }
         }
         // level 1: gamma~_2 = sum over N(v) of deg(u) - footnote
@@ -942,11 +1028,13 @@ __global__ void __launch_bounds__(256) k_prefilter(WaveParams p, u32* out, u32* 
             if (lane == (u32)l0) g2 = part;
         }
         if (!done) {
+            if (p.trace_lanes) lane_level(p, v, 1, deg, 1 + deg, (u32)g2);
             if (bfscut_stops(deg, g2, 1, 1 + deg, xlo, xhi, v, s_thr)) {
                 cut = true;
                 bstat_add(s_bst, ST_CUT, 1);
                 st.mvis += deg;       // level 0 was expanded
                 st.arcwords += deg;
+                if (p.trace_lanes) lane_end(p, v, 1, deg, 1 + deg, true);
             }
         }
         const bool keep = have && !cut;
@@ -996,7 +1084,7 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
     const u32 tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const GraphDev& G = p.g;
     const u32 n_end = p.n_end_dev ? vload(p.n_end_dev) : p.n_end;
-    SlotPtrs S = slot_ptrs(p.slot_base + (size_t)blockIdx.x * p.slot_stride, G.n, W);
+    SlotPtrs S = slot_ptrs<REC>(p.slot_base + (size_t)blockIdx.x * p.slot_stride, G.n, W);
     LocalStats st;
     if (tid == 0) {
         s_thr.valid = 0; s_thr.N = 0; s_thr.F = 1; s_thr.id = 0;
@@ -1033,6 +1121,7 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
                     u32 c = atomicAdd(&s_nc, 1u);
                     s_cid[c] = v; s_cf[c] = 0; s_cr[c] = 1;
                     bstat_add(s_bst, ST_COMPLETED, 1);
+                    if (p.trace_lanes) { lane_level(p, v, 0, 0, 1, 0); lane_end(p, v, 0, 0, 1, false); }
                 } else {
                     alive = true;
                 }
@@ -1043,7 +1132,7 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
         // the current k-th key before the wave's first completions are
         // merged: sources of degree 0 rarely beat it, and a stale (empty)
         // key would send every CTA through the top-k lock
-        if (tid == 0 && !p.exhaustive) read_threshold(p.topk.thr, s_thr);
+        if (tid == 0 && !p.exhaustive) read_thresholds(p.topk, s_thr);
         __syncthreads();
         flush_completions(p, s_cid, s_cf, s_cr, s_nc, s_thr, THREADS, s_stage, &s_go);
         __syncthreads();
@@ -1052,16 +1141,18 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
         u32 d = 0, cur = 0;
         for (;;) {
             if (tid == 0) {
-                if (!p.exhaustive) read_threshold(p.topk.thr, s_thr);
+                if (!p.exhaustive) read_thresholds(p.topk, s_thr);
                 s_chunk = 0;
             }
             __syncthreads();
             if (tid < L) {   // stopping rule at level d, before Gamma_d is expanded
                 bool a = (s_alive32[tid >> 5] >> lane) & 1u;
-                if (a && !p.exhaustive &&
+                if (a && p.trace_lanes) lane_level(p, s_src[tid], d, s_f[tid], s_nd[tid], s_gt[tid]);
+                if (a && !p.exhaustive && !p.nocut &&
                     bfscut_stops(s_f[tid], s_gt[tid], d, s_nd[tid], s_xlo[tid], s_xhi[tid], s_src[tid], s_thr)) {
                     a = false;
                     bstat_add(s_bst, ST_CUT, 1);
+                    if (p.trace_lanes) lane_end(p, s_src[tid], d, s_f[tid], s_nd[tid], true);
                 }
                 u32 m = __ballot_sync(0xffffffffu, a);
                 if (lane == 0) s_alive32[tid >> 5] = m;
@@ -1097,17 +1188,17 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
                 WarpQueue nq{&s_stage[(2 * wid) * QCAP], S.list[cur ^ 1], &s_ln[cur ^ 1], QCAP, 0};
                 WarpQueue lq{&s_stage[(2 * wid + 1) * QCAP], S.clog, &s_logn, QCAP, 0};
                 if (d == 0)
-                    expand_sources<W>(G, s_src, s_alive32, s_pre, s_beg, L, S.vis, Fnext, s_cg, s_cs, p.footnote,
-                                      nq, lq, wid, NWARP, tid, THREADS, st, nullptr);
+                    expand_sources<W, REC>(G, s_src, s_alive32, s_pre, s_beg, L, S.vis, Fnext, s_cg, s_cs,
+                                           p.footnote, nq, lq, wid, NWARP, tid, THREADS, st);
                 else
-                    expand_entries<W>(G, S.list[cur], s_ln[cur], S.F[cur], s_alive32, S.vis, Fnext, s_cg, s_cs,
-                                      p.footnote, nq, lq, &s_chunk, NWARP, Hc, st, nullptr);
+                    expand_entries<W, REC>(G, S.list[cur], s_ln[cur], S.F[cur], s_alive32, S.vis, Fnext, s_cg,
+                                           s_cs, p.footnote, nq, lq, &s_chunk, wid, NWARP, Hc, st);
                 if (d > 0) {
                     __syncthreads();   // the heavy list is complete
                     const u32 hn = s_hn < kHeavyCapCta ? s_hn : kHeavyCapCta;
                     if (hn)
-                        expand_heavy<W>(G, s_heavy, hn, S.vis, Fnext, s_cg, s_cs, p.footnote, nq, lq, wid, NWARP,
-                                        st, nullptr);
+                        expand_heavy<W, REC>(G, s_heavy, hn, S.vis, Fnext, s_cg, s_cs, p.footnote, nq, lq, wid,
+                                             NWARP, st);
                 }
                 nq.flush();
                 lq.flush();
@@ -1123,6 +1214,7 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
                         s_cid[c] = s_src[tid]; s_cf[c] = s_f[tid]; s_cr[c] = s_nd[tid];
                         a = false;
                         bstat_add(s_bst, ST_COMPLETED, 1);
+                        if (p.trace_lanes) lane_end(p, s_src[tid], d, s_f[tid], s_nd[tid], false);
                     } else {
                         s_nd[tid] += gam;
                         s_f[tid] += (u64)(d + 1) * gam;
@@ -1148,10 +1240,7 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
         }
         // the wave's footprint: every word whose vis became non-zero
         const u32 nlog = s_logn;
-        for (u32 i = tid; i < nlog; i += THREADS) {
-            u32 w = S.clog[i];
-            clear_record(S.vis, w);
-        }
+        for (u32 i = tid; i < nlog; i += THREADS) clear_word<REC>(S, S.clog[i]);
         if (tid == 0) {
             bstat_add(s_bst, ST_CLEARED, nlog);
             trace_record(p, TR_CTA_WAVE, blockIdx.x, d, nlog, s_twave, global_ns());
@@ -1174,6 +1263,24 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
 // high-diameter graph) is better left to one CTA.  On the first narrow wave
 // the kernel returns and leaves *head where the per-CTA kernel continues;
 // exhaustive runs stay until the queue is empty.
+// Push or pull for a level whose frontier words have `farcs` out-arcs.
+// Push pays per frontier arc.  Pull pays a scan of every vertex's vis words
+// plus the in-lists of the vertices some live lane has not reached, and in a
+// multi-source BFS those rarely end early (every pending lane must be found),
+// so its cost is estimated as n/4 + (n - min n_d) * m/n, with min n_d the
+// fewest vertices any live lane has reached: a lattice's thin frontiers stay
+// push while most of the graph is unreached, a power-law graph's wide ones
+// pull.  A level also needs at least n*W/pull_div frontier arcs to be pulled.
+constexpr u64 kPullAlpha = 4;   // push arcs worth one unit of the pull estimate
+
+__device__ __forceinline__ bool pull_wanted(const WaveParams& p, int W, u64 farcs, u32 min_nd) {
+    const GraphDev& G = p.g;
+    if (p.all_pull) return true;
+    if (!p.pull_div || farcs < ((u64)G.n * W + p.pull_div - 1) / p.pull_div) return false;
+    const u64 pending = (u64)(G.n - (min_nd < G.n ? min_nd : G.n));
+    return kPullAlpha * farcs >= G.n / 4 + pending * G.m / (G.n ? G.n : 1);
+}
+
 // CTAs per SM the grid kernel is compiled for (its register budget is
 // 65536 / (this * THREADS) per thread)
 #ifndef BCM_GRID_MIN_BLOCKS
@@ -1190,6 +1297,8 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
     __shared__ u32 s_cg[L], s_cs[L];
     __shared__ u32 s_alive32[2 * W];
     __shared__ u32 s_nc, s_base;
+    __shared__ u32 s_minnd;   // fewest vertices a live lane has reached (push or pull)
+    __shared__ u32 s_pgam[L]; // each lane's gamma of the frontier being expanded (m_vis of a pulled level)
     __shared__ ThrCache s_thr;
     __shared__ BlockStats s_bst;
     constexpr u32 QCAP = 4096 / NWARP;
@@ -1203,15 +1312,18 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
     const u32 tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const bool leader = blockIdx.x == 0;
     const GraphDev& G = p.g;
-    // arrays placed at their 4-word offsets whatever W is, so runs of
-    // different widths never put bit arrays where another left lists or logs
-    SlotPtrs S = slot_ptrs(p.seed_base, G.n, 4);
+    // planes of 4 words per vertex whatever W is, so runs of different
+    // widths never put bit arrays where another left lists or logs
+    SlotPtrs S = slot_ptrs<1>(p.seed_base, G.n, 4);
+
     LocalStats st;
-    const u32 gw = blockIdx.x * NWARP + wid, gnw = gridDim.x * NWARP;
+    const u32 gnw = gridDim.x * NWARP;
+    // the same warps numbered across blocks first: work dealt by warp number
+    // (first chunks, pulled batches, heavy pieces) then spreads over every
+    // block and SM before a second warp of any block gets some
+    const u32 pw = wid * gridDim.x + blockIdx.x;
     const u32 n_end = p.n_end_dev ? vload(p.n_end_dev) : p.n_end;
     const HeavyList Hg{p.gheavy, p.gheavy_n, p.gheavy_cap};
-    // frontier bitmaps, one bit per vertex, by level parity
-    u32* const bm[2] = {p.gbm, p.gbm + p.nbw};
     if (tid == 0) { s_nc = 0; s_thr.valid = 0; s_thr.N = 0; s_thr.F = 1; s_thr.id = 0; }
     bstat_init(s_bst);
     bool ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err);
@@ -1235,6 +1347,7 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
                         u32 c = atomicAdd(&s_nc, 1u);
                         s_cid[c] = v; s_cf[c] = 0; s_cr[c] = 1;
                         bstat_add(s_bst, ST_COMPLETED, 1);
+                        if (p.trace_lanes) { lane_level(p, v, 0, 0, 1, 0); lane_end(p, v, 0, 0, 1, false); }
                     }
                 } else {
                     alive = true;
@@ -1254,15 +1367,21 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
         bool pulled = false;
         u32 level_cnt = 0;   // entries of the level's frontier list, read before it can be reset
         for (;;) {
-            if (!p.exhaustive && tid == 0) read_threshold(p.topk.thr, s_thr);
+            if (tid == 0) {
+                if (!p.exhaustive) read_thresholds(p.topk, s_thr);
+                s_minnd = 0xffffffffu;
+            }
             __syncthreads();
             if (tid < L) {
                 bool a = (s_alive32[tid >> 5] >> lane) & 1u;
-                if (a && !p.exhaustive &&
+                if (a && leader && p.trace_lanes) lane_level(p, s_src[tid], d, s_f[tid], s_nd[tid], s_gt[tid]);
+                if (a && !p.exhaustive && !p.nocut &&
                     bfscut_stops(s_f[tid], s_gt[tid], d, s_nd[tid], s_xlo[tid], s_xhi[tid], s_src[tid], s_thr)) {
                     a = false;
                     if (leader) bstat_add(s_bst, ST_CUT, 1);
+                    if (leader && p.trace_lanes) lane_end(p, s_src[tid], d, s_f[tid], s_nd[tid], true);
                 }
+                if (a) atomicMin(&s_minnd, s_nd[tid]);
                 u32 m = __ballot_sync(0xffffffffu, a);
                 if (lane == 0) s_alive32[tid >> 5] = m;
             }
@@ -1277,34 +1396,33 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
                 for (int i = 0; i < 2 * W; ++i) alive += __popc(s_alive32[i]);
                 const u32 cnt = d ? vload(&p.glist_n[cur]) : 0u;
                 const u64 arcs = d ? vload(&p.garc[cur]) : 0ull;
-                const bool pull = d && p.pull_div && arcs >= ((u64)G.n * W + p.pull_div - 1) / p.pull_div;
+                const bool pull = d && pull_wanted(p, W, arcs, s_minnd);
                 trace_record(p, TR_GRID_LEVEL, wave, d, cnt, alive | ((u64)pull << 16) | (arcs << 20), global_ns());
             }
             if (d == 0) source_prefix<THREADS>(G, s_src, s_alive32, L, s_pre, s_beg, s_wsum);
             const u32 par = d & 1;
-            u32* gcg = p.gcnt + par * 512;
+            u32* const gcpar = p.gcnt + par * kCntParity;                   // this level's counters
+            u32* gcg = gcpar + (blockIdx.x % kCntCopies) * 512;             // this block's copy
             u32* gcs = gcg + 256;
             {
                 WarpQueue nq{&s_stage[(2 * wid) * QCAP], S.list[cur ^ 1], &p.glist_n[cur ^ 1], QCAP, 0};
                 WarpQueue lq{&s_stage[(2 * wid + 1) * QCAP], S.clog, p.glog_n, QCAP, 0};
                 if (d == 0) {
-                    expand_sources<W>(G, s_src, s_alive32, s_pre, s_beg, L, S.vis, S.F[cur ^ 1], s_cg, s_cs,
-                                      p.footnote, nq, lq, gw, gnw, blockIdx.x * THREADS + tid, gridDim.x * THREADS,
-                                      st, bm[cur ^ 1]);
+                    expand_sources<W, 1>(G, s_src, s_alive32, s_pre, s_beg, L, S.vis, S.F[cur ^ 1], s_cg, s_cs,
+                                         p.footnote, nq, lq, pw, gnw, blockIdx.x * THREADS + tid,
+                                         gridDim.x * THREADS, st);
                 } else {
                     const u32 cnt = vload(&p.glist_n[cur]);
                     level_cnt = cnt;
                     wave_entries += cnt;
-                    // by pull once the frontier's out-arcs reach n*W/pull_div:
-                    // push pays per arc (and a hub's arcs fall to one warp),
-                    // pull pays a fixed scan of every vertex's vis words
-                    pulled = p.pull_div && vload(&p.garc[cur]) >= ((u64)G.n * W + p.pull_div - 1) / p.pull_div;
-                    if (pulled)
+                    pulled = pull_wanted(p, W, vload(&p.garc[cur]), s_minnd);
+                    if (pulled) {
                         pull_level<W>(G, S.F[cur], s_alive32, S.vis, S.F[cur ^ 1], s_cg, s_cs, p.footnote, nq, lq,
-                                      &p.gchunk[cur], st, bm[cur], bm[cur ^ 1]);
-                    else
-                        expand_entries<W>(G, S.list[cur], cnt, S.F[cur], s_alive32, S.vis, S.F[cur ^ 1], s_cg,
-                                          s_cs, p.footnote, nq, lq, &p.gchunk[cur], gnw, Hg, st, bm[cur ^ 1]);
+                                      &p.gchunk[cur], pw, gnw, st);
+                    } else {
+                        expand_entries<W, 1>(G, S.list[cur], cnt, S.F[cur], s_alive32, S.vis, S.F[cur ^ 1], s_cg,
+                                             s_cs, p.footnote, nq, lq, &p.gchunk[cur], pw, gnw, Hg, st);
+                    }
                 }
                 nq.flush();
                 lq.flush();
@@ -1326,8 +1444,8 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
                     {
                         WarpQueue nq{&s_stage[(2 * wid) * QCAP], S.list[cur ^ 1], &p.glist_n[cur ^ 1], QCAP, 0};
                         WarpQueue lq{&s_stage[(2 * wid + 1) * QCAP], S.clog, p.glog_n, QCAP, 0};
-                        expand_heavy<W>(G, p.gheavy, hn, S.vis, S.F[cur ^ 1], s_cg, s_cs, p.footnote, nq, lq, gw,
-                                        gnw, st, bm[cur ^ 1]);
+                        expand_heavy<W, 1>(G, p.gheavy, hn, S.vis, S.F[cur ^ 1], s_cg, s_cs, p.footnote, nq, lq,
+                                           pw, gnw, st);
                         nq.flush();
                         lq.flush();
                         flush_fwarcs(st, &p.garc[cur ^ 1]);
@@ -1344,7 +1462,7 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
             if (pulled) {   // every block is past the pull: retire the frontier words
                 // (the count read at the level's start: the leader resets
                 // glist_n[cur] below while slower blocks may still be here)
-                pull_clear(S.list[cur], level_cnt, S.F[cur], blockIdx.x * THREADS + tid, gridDim.x * THREADS);
+                pull_clear<1>(S.list[cur], level_cnt, S.F[cur], blockIdx.x * THREADS + tid, gridDim.x * THREADS);
                 // the arcs a push would have scanned (m_vis counts those
                 // whichever direction ran): a live lane's frontier out-arcs
                 // are its gamma-tilde sum plus the footnote's 1 per vertex,
@@ -1352,7 +1470,7 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
                 // counters (cleared at this level's end)
                 if (leader) {
                     if (tid < L && ((s_alive32[tid >> 5] >> lane) & 1u))
-                        st.mvis += (u64)s_gt[tid] + (u64)p.footnote * vload(&p.gcnt[(par ^ 1) * 512 + tid]);
+                        st.mvis += (u64)s_gt[tid] + (u64)p.footnote * s_pgam[tid];
                     if (tid == 0) {
                         bstat_add(s_bst, ST_ENTRIES, level_cnt);
                         bstat_add(s_bst, ST_PULLENTRIES, level_cnt);
@@ -1361,31 +1479,36 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
                 pulled = false;
                 __syncthreads();
             }
-            // the consumed level's bitmap, for reuse two levels on
-            for (u32 i = blockIdx.x * THREADS + tid; i < p.nbw; i += gridDim.x * THREADS) bm[cur][i] = 0;
             if (tid < L) {
                 bool a = (s_alive32[tid >> 5] >> lane) & 1u;
                 if (a) {
-                    u32 gam = vload(&gcg[tid]);
+                    u32 gam = 0, dsum = 0;
+#pragma unroll
+                    for (u32 c = 0; c < kCntCopies; ++c) {
+                        gam += vload(&gcpar[c * 512 + tid]);
+                        dsum += vload(&gcpar[c * 512 + 256 + tid]);
+                    }
+                    s_pgam[tid] = gam;
                     if (gam == 0) {
                         if (leader) {
                             u32 c = atomicAdd(&s_nc, 1u);
                             s_cid[c] = s_src[tid]; s_cf[c] = s_f[tid]; s_cr[c] = s_nd[tid];
                             bstat_add(s_bst, ST_COMPLETED, 1);
+                            if (p.trace_lanes) lane_end(p, s_src[tid], d, s_f[tid], s_nd[tid], false);
                         }
                         a = false;
                     } else {
                         s_nd[tid] += gam;
                         s_f[tid] += (u64)(d + 1) * gam;
-                        s_gt[tid] = vload(&gcs[tid]);
+                        s_gt[tid] = dsum;
                     }
                 }
                 u32 m = __ballot_sync(0xffffffffu, a);
                 if (lane == 0) s_alive32[tid >> 5] = m;
             }
             if (leader) {   // buffers of the next level: counters par^1, list count and chunk counter
-                u32* nx = p.gcnt + (par ^ 1) * 512;
-                for (u32 i = tid; i < 512; i += THREADS) nx[i] = 0;
+                u32* nx = p.gcnt + (par ^ 1) * kCntParity;
+                for (u32 i = tid; i < kCntParity; i += THREADS) nx[i] = 0;
                 if (tid == 0) {
                     p.glist_n[cur] = 0;
                     p.garc[cur] = 0;
@@ -1411,16 +1534,12 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
         // (the level loop ends at a barrier or on a decision all blocks share)
         if (!(ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err))) break;
         const u32 nlog = vload(p.glog_n);
-        for (u32 i = blockIdx.x * THREADS + tid; i < nlog; i += gridDim.x * THREADS) {
-            u32 w = __ldcg(&S.clog[i]);
-            clear_record(S.vis, w);
-        }
-        for (u32 i = blockIdx.x * THREADS + tid; i < 2 * p.nbw; i += gridDim.x * THREADS) p.gbm[i] = 0;
+        for (u32 i = blockIdx.x * THREADS + tid; i < nlog; i += gridDim.x * THREADS) clear_word<1>(S, __ldcg(&S.clog[i]));
         if (leader && tid == 0) bstat_add(s_bst, ST_CLEARED, nlog);
         if (!(ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err))) break;
         if (leader && tid == 0) trace_record(p, TR_GRID_WAVE, wave, d, nlog, wave_entries, global_ns());
         if (leader) {   // reset per-wave counters and advance the queue
-            for (u32 i = tid; i < 1024; i += THREADS) p.gcnt[i] = 0;
+            for (u32 i = tid; i < 2 * kCntParity; i += THREADS) p.gcnt[i] = 0;
             if (tid == 0) {
                 p.glist_n[0] = 0;
                 p.glist_n[1] = 0;
@@ -1461,7 +1580,7 @@ __global__ void __launch_bounds__(THREADS) k_plain(WaveParams p, u32 it, u32* st
     if (tid == 0) {
         s_cg = 0; s_cs = 0;
         s_thr.valid = 0; s_thr.N = 0; s_thr.F = 1; s_thr.id = 0;
-        read_threshold(p.topk.thr, s_thr);   // fixed for this launch: only its end inserts
+        read_thresholds(p.topk, s_thr);   // fixed for this launch: only its end inserts
     }
     bstat_init(s_bst);
     __syncthreads();
@@ -1472,9 +1591,10 @@ __global__ void __launch_bounds__(THREADS) k_plain(WaveParams p, u32 it, u32* st
     bool done = false, cut = false, ok = true;
     const u32 gw = blockIdx.x * NWARP + wid, gnw = gridDim.x * NWARP;
     while (ok) {
-        if (bfscut_stops(f, gt, d, nd, xlo, xhi, v, s_thr)) { cut = true; break; }
+        if (leader && tid == 0 && p.trace_lanes) lane_level(p, v, d, f, nd, gt);
+        if (!p.nocut && bfscut_stops(f, gt, d, nd, xlo, xhi, v, s_thr)) { cut = true; break; }
         const u32 par = d & 1;
-        u32* gcg = p.gcnt + par * 512;
+        u32* gcg = p.gcnt + par * kCntParity;
         u32* gcs = gcg + 256;
         u32* nlist = lists + (size_t)(cur ^ 1) * n;
         u32* nn = &p.glist_n[cur ^ 1];
@@ -1545,7 +1665,7 @@ __global__ void __launch_bounds__(THREADS) k_plain(WaveParams p, u32 it, u32* st
         if (!grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err)) { ok = false; break; }
         u32 gam = vload(&gcg[0]);
         if (leader && tid == 0) {
-            u32* nx = p.gcnt + (par ^ 1) * 512;
+            u32* nx = p.gcnt + (par ^ 1) * kCntParity;
             nx[0] = 0; nx[256] = 0;
             p.glist_n[cur] = 0;
         }
@@ -1558,12 +1678,13 @@ __global__ void __launch_bounds__(THREADS) k_plain(WaveParams p, u32 it, u32* st
     // leave the shared buffers zeroed for the next launch, then insert
     if (ok) ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err);
     if (leader && tid == 0) {
-        p.gcnt[0] = 0; p.gcnt[256] = 0; p.gcnt[512] = 0; p.gcnt[768] = 0;
+        p.gcnt[0] = 0; p.gcnt[256] = 0; p.gcnt[kCntParity] = 0; p.gcnt[kCntParity + 256] = 0;
         p.glist_n[0] = 0; p.glist_n[1] = 0;
         bstat_add(s_bst, ST_LEVELS, d);
         bstat_max(s_bst, ST_MAXLEVEL, d);
         bstat_add(s_bst, ST_WAVES, 1);
         if (cut) bstat_add(s_bst, ST_CUT, 1);
+        if (p.trace_lanes && ((done && ok) || cut)) lane_end(p, v, d, f, nd, cut);
         if (done && ok) {
             bstat_add(s_bst, ST_COMPLETED, 1);
             if (lock_acquire(p.topk.lock, p.lock_limit_ns, p.err)) {

@@ -289,6 +289,8 @@ def workload(name: str) -> Graph:
         return chung_lu(1 << 18, 10.0, 2.3, seed=2)
     if name == "rmat20":
         return rmat(20, 16, seed=3)
+    if name == "rmat18":           # the same recipe at scale 18 (profiling-size case)
+        return rmat(18, 16, seed=3)
     if name == "grid2048":
         return grid_lcc(2048, 2048, 0.05, seed=4)
     raise KeyError(name)

@@ -73,11 +73,11 @@ def test_topk_and_farness_directed(B, gen, orc, lanes):
             assert np.array_equal(gf, f) and np.array_equal(gr, r), g.name
             gf, gr, _ = h.farness_all(lanes=lanes, flags=B.BCM_CTA_ONLY)
             assert np.array_equal(gf, f) and np.array_equal(gr, r), g.name
-            gf, gr, _ = h.farness_all(grid_lanes=lanes, pull_div=1 << 30)
+            gf, gr, _ = h.farness_all(grid_lanes=lanes, flags=B.BCM_ALL_PULL)
             assert np.array_equal(gf, f) and np.array_equal(gr, r), (g.name, "pull")
             for k in sorted({1, 2, 5, 10, 100, min(g.n, 1024), min(g.n + 3, 1024)} - {0}):
                 exp = orc.topk(f, r, k)
-                for flags, pd in ((0, 0), (B.BCM_CTA_ONLY, 0), (B.BCM_GRID_ONLY, 0), (B.BCM_GRID_ONLY, 1 << 30),
+                for flags, pd in ((0, 0), (B.BCM_CTA_ONLY, 0), (B.BCM_GRID_ONLY, 0), (B.BCM_GRID_ONLY | B.BCM_ALL_PULL, 0),
                                   (B.BCM_GRID_ONLY | B.BCM_NO_PULL, 0)):
                     ids, tf, tr, st = h.topk(k, lanes=lanes, grid_lanes=lanes, flags=flags, pull_div=pd)
                     assert np.array_equal(ids, exp), (g.name, k, flags)

@@ -32,7 +32,10 @@ def undirected_graphs(gen):
           gen.relabel(gen.cycle(12), seed=3), gen.relabel(gen.grid(4, 4), seed=5),
           gen.ba(200, 2, seed=11), gen.grid_lcc(12, 12, 0.1, seed=2),
           gen.with_self_loops_and_repeats(gen.grid(4, 5), seed=1),
-          gen.star(300), gen.grid(17, 19)]
+          gen.star(300), gen.grid(17, 19),
+          # in-hubs (more than 128 in-arcs) scanned in pieces by pulled levels: every vertex of
+          # K_260, a centre with 4 pieces, the hubs of a denser BA graph
+          gen.complete(260), gen.star(1000), gen.ba(3000, 8, seed=12)]
     for s in range(6):
         gs.append(gen.gnp(60 + 37 * s, 0.02 + 0.01 * (s % 4), seed=100 + s, directed=False))
     gs.append(gen.chung_lu(3000, 6.0, 2.3, seed=4))
@@ -73,7 +76,7 @@ def test_farness_all_small(B, gen, orc, lanes):
             assert np.array_equal(gf, f) and np.array_equal(gr, r), (g.name, lanes)
             gf, gr, st = h.farness_all(lanes=lanes, flags=B.BCM_CTA_ONLY)
             assert np.array_equal(gf, f) and np.array_equal(gr, r), (g.name, lanes, "cta")
-            gf, gr, st = h.farness_all(grid_lanes=lanes, pull_div=1 << 30)
+            gf, gr, st = h.farness_all(grid_lanes=lanes, flags=B.BCM_ALL_PULL)
             assert np.array_equal(gf, f) and np.array_equal(gr, r), (g.name, lanes, "pull")
             gf, gr, st = h.farness_all(grid_lanes=lanes, flags=B.BCM_NO_PULL)
             assert np.array_equal(gf, f) and np.array_equal(gr, r), (g.name, lanes, "push")
@@ -109,7 +112,8 @@ def test_topk_kernel_choices_and_footnote(B, gen, orc):
                         ids, gf, gr, st = h.topk(k, grid_lanes=gl, heavy_words=hw)
                         assert np.array_equal(ids, exp) and np.array_equal(gf, f[exp]), (g.name, k, gl, hw)
                     # every grid level by pull, then every one by push
-                    for flags, pd in ((B.BCM_GRID_ONLY, 1 << 30), (B.BCM_GRID_ONLY | B.BCM_NO_PULL, 0)):
+                    for flags, pd in ((B.BCM_GRID_ONLY | B.BCM_ALL_PULL, 0), (B.BCM_GRID_ONLY | B.BCM_NO_PULL, 0),
+                                      (B.BCM_GRID_ONLY, 1 << 30)):
                         ids, gf, gr, st = h.topk(k, grid_lanes=gl, flags=flags, pull_div=pd)
                         assert np.array_equal(ids, exp) and np.array_equal(gf, f[exp]), (g.name, k, gl, pd)
 
@@ -131,7 +135,8 @@ def test_exhaustive_m_vis_is_the_push_count_either_way(B, gen):
                   for v in range(g.n))
         with B.BcmGraph.from_graph(g) as h:
             for gl in (64, 128, 256):
-                for pd, flags in ((1 << 30, 0), (1 << 30, B.BCM_NO_FOOTNOTE), (0, B.BCM_NO_PULL), (0, 0)):
+                for pd, flags in ((0, B.BCM_ALL_PULL), (0, B.BCM_ALL_PULL | B.BCM_NO_FOOTNOTE), (0, B.BCM_NO_PULL), (0, 0),
+                                  (1 << 30, 0)):
                     _, _, st = h.farness_all(grid_lanes=gl, pull_div=pd, flags=flags)
                     assert st["m_vis"] == exp, (g.name, gl, pd, flags, st["m_vis"], exp)
 

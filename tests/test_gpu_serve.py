@@ -1,13 +1,32 @@
 """Serving with continuous batching on the GPU: every request's result is the
-same alone and in the mix (bit-exact: ids, farness, reach), runs on
-different graphs overlap on the device, and admission keeps the workspace
-inside the HBM budget."""
+oracle's exact top-k (the sequential Algorithm 1, pinned against the textbook
+top-k) and the same alone and in the mix (bit-exact: ids, farness, reach),
+runs on different graphs overlap on the device, and admission keeps the
+workspace inside the HBM budget."""
 import math
 
 import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
+
+
+def _oracle_topk(args):
+    g, k = args
+    import oracle
+    ids, far, reach, _ = oracle.bcm(g, k, refined=g.directed)
+    return ids, far, reach
+
+
+def _oracle_answers(graphs, keys):
+    """The oracle's top-k for each (graph, k), in processes of their own (spawned:
+    this process already holds a CUDA context)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    keys = sorted(keys)
+    with ProcessPoolExecutor(max_workers=min(16, len(keys)), mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_oracle_topk, [(graphs[gi], k) for gi, k in keys]))
+    return dict(zip(keys, res))
 
 
 @pytest.fixture(scope="module")
@@ -22,6 +41,7 @@ def backend():
     specs = serve.mix_specs(16, n_hi=2e5)
     graphs = [serve.build_graph(s) for s in specs]
     be = serve.GpuBackend(graphs, trace=True)
+    be.test_graphs = graphs
     yield be
     be.close()
 
@@ -32,6 +52,7 @@ def test_results_identical_alone_and_in_the_mix(backend):
     sched = serve.Scheduler(backend, max_inflight=8)
     res = sched.run(reqs)
     assert sched.peak_inflight > 1
+    exact = _oracle_answers(backend.test_graphs, {(r.graph, r.k) for r in res})
     alone = {}
     for r in res:
         key = (r.graph, r.k)
@@ -41,6 +62,8 @@ def test_results_identical_alone_and_in_the_mix(backend):
         assert np.array_equal(r.ids, ids), key
         assert np.array_equal(r.farness, far), key
         assert np.array_equal(r.reach, reach), key
+        oi, of, orr = exact[key]
+        assert np.array_equal(r.ids, oi) and np.array_equal(r.farness, of) and np.array_equal(r.reach, orr), key
     # device time of runs on different graphs overlapped
     spans = [(r.stats["device_span_ns"], r.graph) for r in res if "device_span_ns" in r.stats]
     spans.sort()

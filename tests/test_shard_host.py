@@ -1,8 +1,10 @@
 """Source sharding across GPUs (one graph, N ranks), on the CPU: the shard
 rule partitions the degree order, bcm_topk_merge is the exact ranking, and
 the N>1 host path -- each rank's shard top-k, one all-gather, the merge --
-gives the graph's top-k, run as two gloo ranks.  The per-rank top-k comes
-from the oracle here (no GPU); the GPU side is test_gpu_shard.py."""
+gives the graph's top-k, run as two gloo ranks, also with the ranks sharing
+their k-th keys while they run (paper_1507_01490_gb300.exchange).  The
+per-rank top-k comes from the oracle here (no GPU); the GPU side is
+test_gpu_shard.py."""
 import os
 import socket
 
@@ -68,6 +70,9 @@ def test_merge_arguments(lib):
     assert ei.value.status == B.BCM_ERR_INVALID
     oi, of, orr = B.bcm_topk_merge([], [], [], 5)
     assert len(oi) == 0
+    # padding of a shard list that holds fewer than k entries is skipped
+    oi, of, orr = B.bcm_topk_merge([5, B.PAD_ID, 2, B.PAD_ID], [10, 0, 4, 0], [3, 0, 3, 0], 3)
+    assert oi.tolist() == [2, 5] and of.tolist() == [4, 10] and orr.tolist() == [3, 3]
 
 
 def _free_port():
@@ -116,3 +121,75 @@ def test_two_gloo_ranks_merge_to_the_global_topk(lib, orc, tmp_path, k):
     for rank in range(2):
         for gi in range(3):
             assert (tmp_path / ("rank%d_graph%d" % (rank, gi))).read_text() == "ok", (rank, gi)
+
+
+def test_key_order():
+    from paper_1507_01490_gb300.exchange import NO_KEY, best_key, key_before
+    a = (1, 16, 40, 7)       # (r-1)^2 / f = 0.4
+    b = (1, 9, 30, 3)        # 0.3
+    tie = (1, 32, 80, 5)     # 0.4, smaller id than a
+    assert key_before(a, b) and not key_before(b, a)
+    assert key_before(tie, a) and not key_before(a, tie)
+    assert key_before(b, NO_KEY) and not key_before(NO_KEY, b) and not key_before(NO_KEY, NO_KEY)
+    assert best_key([b, NO_KEY, a, tie]) == tie and best_key([]) == NO_KEY
+
+
+def _exchange_rank_main(rank, world, port, k, chunk, out_dir):
+    import torch.distributed as dist
+
+    import oracle
+    from paper_1507_01490_gb300 import graphgen
+    from paper_1507_01490_gb300.exchange import ThresholdExchange
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        graphs = [graphgen.ba(2000, 3, seed=1), graphgen.chung_lu(3000, 8.0, 2.3, seed=5),
+                  graphgen.gnp(700, 0.006, seed=3, directed=True), graphgen.rmat(11, 8, seed=6)]
+        offers = 0
+        for gi, g in enumerate(graphs):
+            order = oracle.order(g)
+            src = order[B.shard_positions(g.n, rank, world)]
+            if g.directed:
+                _, al, om, _ = oracle.alpha_omega(g)
+                bounds = (al, om)
+            else:
+                _, rr = oracle.farness_all(g)
+                bounds = (rr, rr)
+            alone = oracle.ShardRun(g, k, src, bounds)
+            alone.step(len(src) + 1)
+            run = oracle.ShardRun(g, k, src, bounds)
+            ex = ThresholdExchange(period_s=0)
+            ex.run(run.key, run.offer, lambda: run.step(chunk))
+            offers += ex.offers
+            ids, f, r, st = run.result()
+            lists = [None] * world
+            dist.all_gather_object(lists, (ids, f, r))
+            mi, mf, mr = B.bcm_topk_merge(np.concatenate([x[0] for x in lists]),
+                                          np.concatenate([x[1] for x in lists]),
+                                          np.concatenate([x[2] for x in lists]), k)
+            fa, ra = oracle.farness_all(g)
+            exp = oracle.topk(fa, ra, k)
+            ok = np.array_equal(mi, exp) and np.array_equal(mf, fa[exp]) and np.array_equal(mr, ra[exp])
+            fewer = st["m_vis"] <= alone.result()[3]["m_vis"]
+            with open(os.path.join(out_dir, "x_rank%d_graph%d" % (rank, gi)), "w") as fh:
+                fh.write("ok" if ok and fewer else "mismatch %s %s" % (ok, fewer))
+        with open(os.path.join(out_dir, "x_rank%d_offers" % rank), "w") as fh:
+            fh.write(str(offers))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("k", [1, 10])
+def test_two_gloo_ranks_exchange_thresholds(lib, orc, tmp_path, k):
+    """Two ranks, each running Algorithm 1 over its shard (the oracle, a few
+    sources at a time), share their k-th keys every round: the merged top-k
+    is the graph's, no rank scans more arcs than it would alone, and keys
+    were actually offered."""
+    import torch.multiprocessing as mp
+    orc.build()
+    mp.spawn(_exchange_rank_main, args=(2, _free_port(), k, 16, str(tmp_path)), nprocs=2, join=True)
+    for rank in range(2):
+        for gi in range(4):
+            assert (tmp_path / ("x_rank%d_graph%d" % (rank, gi))).read_text() == "ok", (rank, gi)
+    assert sum(int((tmp_path / ("x_rank%d_offers" % r)).read_text()) for r in range(2)) > 0
