@@ -461,6 +461,7 @@ def main():
     ap.add_argument("--workload", default="chunglu1m", choices=sorted(WORKLOADS))
     ap.add_argument("--k", type=int, default=10)
     ap.add_argument("--lanes", type=int, default=0, help="0: library default")
+    ap.add_argument("--grid-lanes", type=int, default=0, help="sources per grid-wide wave; 0: library default")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--blocks", type=int, default=0)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain one-source baseline")
@@ -477,7 +478,7 @@ def main():
     ap.add_argument("--serve-rates", default="0.5,0.8,1.0", help="fractions of the measured capacity")
     ap.add_argument("--serve-inflight", type=int, default=16)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
-    ap.add_argument("--serve-ws-cap-gb", type=float, default=0.0,
+    ap.add_argument("--serve-ws-cap-gb", type=float, default=-1.0,
                     help="per-run workspace cap (fewer per-CTA blocks on large graphs); <0: budget/inflight, 0: none")
     ap.add_argument("--serve-check", type=int, default=300, help="results compared with the request alone")
     ap.add_argument("--serve-blocks", type=int, default=0, help="per-CTA blocks of a served run (0: library default)")
@@ -527,7 +528,7 @@ def main():
     # launch parameters: the autotuner's choice for this graph (rank 0 tunes,
     # the others take its choice), unless fixed on the command line
     tuned, tuning_s = None, 0.0
-    if not args.no_autotune and not (args.lanes or args.threads):
+    if not args.no_autotune and not (args.lanes or args.threads or args.grid_lanes):
         from paper_1507_01490_gb300 import autotune
         if rank == 0:
             with B.BcmGraph(rp_d, col_d, g.n, g.directed, on_device=True, stream=stream.cuda_stream) as th:
@@ -536,14 +537,16 @@ def main():
             box = [tuned]
             dist.broadcast_object_list(box, src=0)
             tuned = box[0]
-    par = dict(lanes=args.lanes, threads=args.threads, grid_lanes=0, pull_div=0)
+    par = dict(lanes=args.lanes, threads=args.threads, grid_lanes=args.grid_lanes, pull_div=0, kflags=0)
     if tuned:
+        from paper_1507_01490_gb300 import autotune
         par.update(lanes=tuned["lanes"], threads=tuned["threads"], grid_lanes=tuned["grid_lanes"],
-                   pull_div=tuned["pull_div"])
+                   pull_div=tuned["pull_div"], kflags=autotune.PER_CTA[tuned.get("per_cta", "auto")])
 
     def mkopt(flags, **extra):
-        return B.make_options(lanes=par["lanes"], threads=par["threads"], blocks=args.blocks, flags=flags,
-                              grid_lanes=par["grid_lanes"], pull_div=par["pull_div"], **extra)
+        return B.make_options(lanes=par["lanes"], threads=par["threads"], blocks=args.blocks,
+                              flags=flags | par["kflags"], grid_lanes=par["grid_lanes"], pull_div=par["pull_div"],
+                              **extra)
 
     opts = mkopt(B.BCM_OUT_DEVICE)
 
@@ -593,16 +596,20 @@ def main():
                 merged["ids"], merged["far"], merged["reach"] = B.bcm_topk_merge(
                     sel[0].view(np.uint32), sel[1].view(np.uint64), sel[2].view(np.uint32), k)
 
-    def timed(fn, reps):
-        """per-step device time (CUDA events on the library's stream), L2 flushed before each"""
+    def timed(fn, reps, last_stats=None):
+        """per-step device time (CUDA events on the library's stream), L2 flushed before each;
+        the last step also fills last_stats (the counters are copied with the results either way)"""
         ts = []
-        for _ in range(reps):
+        for i in range(reps):
             with torch.cuda.stream(stream):
                 flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            fn()
+            if last_stats is not None and i == reps - 1:
+                fn(stats=last_stats)
+            else:
+                fn()
             e1.record(stream)
             e1.synchronize()
             ts.append(e0.elapsed_time(e1) / 1e3)
@@ -619,7 +626,8 @@ def main():
     l0 = B.bcm_launch_count()
     torch.cuda.synchronize()
     t_wall = time.perf_counter()
-    step_times = timed(run_step, args.steps)
+    st = B.bcm_stats()
+    step_times = timed(run_step, args.steps, last_stats=st)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
     launches = B.bcm_launch_count() - l0
@@ -632,9 +640,7 @@ def main():
     # N ranks finish one graph per step together
     s_per_graph = total / args.steps
 
-    # one more step with stats (outside the timed region)
-    st = B.bcm_stats()
-    run_step(stats=st)
+    # counters of the last timed step
     st = st.as_dict()
     if world > 1:
         shard_stats = st
@@ -671,8 +677,6 @@ def main():
                 ids_d[:nq].cpu().numpy().view(np.uint32).tolist() == gk["ids"] and
                 far_d[:nq].cpu().numpy().view(np.uint64).tolist() == gk["farness"] and
                 reach_d[:nq].cpu().numpy().view(np.uint32).tolist() == gk["reach"])
-    # restore k's outputs for verification
-    step()
     plain = None
     if not args.no_plain:
         popts = B.make_options(flags=B.BCM_OUT_DEVICE | B.BCM_PLAIN)
@@ -681,7 +685,6 @@ def main():
         p_ids = ids_d[:kk].cpu().numpy().view(np.uint32).copy()
         plain = {"s_per_graph": tp, "m_vis": sp.m_vis, "gteps": sp.m_vis / tp / 1e9,
                  "launches": sp.launches, "same_result": bool(np.array_equal(p_ids, got_ids))}
-        step()
 
     # e2e: through the C-ABI from pinned host memory, results back to host
     rp_h = torch.from_numpy(g.row_ptr.view(np.int64)).pin_memory()
@@ -719,7 +722,7 @@ def main():
     if st["seed_ms"] >= st["wave_ms"]:
         kname, kms, kbytes = "k_wave_grid", st["seed_ms"], st["grid_bytes"]
     else:
-        kname, kms, kbytes = "k_wave_cta", st["wave_ms"], st["wave_bytes"]
+        kname, kms, kbytes = ("k_sparse" if st["sparse"] else "k_wave_cta"), st["wave_ms"], st["wave_bytes"]
     achieved = kbytes / (kms / 1e3) / 1e9 if kms > 0 else None
     src_hash = kernel_source_hash()
     traffic = profile_traffic(kname, src_hash)
@@ -795,7 +798,8 @@ def main():
                    "k": k, "lanes": par["lanes"] or 64, "grid_lanes": par["grid_lanes"] or 128,
                    "pull_div": par["pull_div"] or 32, "threads": par["threads"] or 512,
                    "launch_parameters": ("autotuned for this graph (%.2f s, outside the timed region)" % tuning_s)
-                   if tuned else "library defaults" if not (args.lanes or args.threads) else "command line",
+                   if tuned else "library defaults" if not (args.lanes or args.threads or args.grid_lanes)
+                   else "command line",
                    "l2": "256 MiB buffer written before every timed step",
                    "step": "graph handle from device CSR + preprocessing + top-k + release" +
                            (" (each rank its shard of the sources), all-gather of the k-entry lists, "

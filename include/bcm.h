@@ -85,6 +85,12 @@ typedef enum {
                                      it ended (record kinds 3 and 4 of bcm_trace); meant for small graphs */
 #define BCM_ALL_PULL      0x2000u /* grid-wide waves expand every level after the first by pull (a check of
                                      the pull path; results are the same) */
+#define BCM_SPARSE        0x4000u /* one source per CTA instead of bit-lane waves: a visited bitmap and
+                                     vertex queues (for graphs whose sources' searches share no frontier).
+                                     The default on undirected graphs of n >= 4096 and largest degree <= 8
+                                     (lattices, meshes); with it there are no grid-wide waves unless
+                                     BCM_GRID_ONLY.  Results are the same */
+#define BCM_NO_SPARSE     0x8000u /* bit-lane waves whatever the graph */
 
 /* Sources are taken from the degree order in waves.  Waves run first on a
  * grid-wide kernel (all CTAs on one wave) while they are heavy, then on a
@@ -105,9 +111,10 @@ typedef struct {
     uint32_t grid_lanes;      /* sources per grid-wide wave: 64, 128 or 256; 0 = 128 */
     uint32_t flags;           /* BCM_* flags above */
     uint32_t blocks;          /* CTAs of the per-CTA kernel; 0 = all that fit on the GPU, at most
-                                 one per wave of sources (ceil(n / lanes)), and at most as many as
-                                 keep their slots (44 n lanes/64 bytes each) within 2 GiB */
-    uint32_t threads;         /* threads per CTA of the per-CTA kernel: 256, 512 or 1024; 0 = 512 */
+                                 one per wave of sources (ceil(n / lanes)).  Each holds a slot of
+                                 44 E lanes/64 bytes, E its table's entries (cta_table) */
+    uint32_t threads;         /* threads per CTA of the per-CTA kernel: 256, 512 or 1024; 0 = 512
+                                 (the one-source kernel, BCM_SPARSE: also 128; 0 = 256) */
     uint32_t heavy_words;     /* see above; 0 = default (4 per warp of the grid) */
     uint32_t pull_div;        /* a grid-wave level is expanded by pull when the out-arcs of its
                                  frontier's (vertex, word) entries number at least n*W/pull_div
@@ -124,6 +131,14 @@ typedef struct {
                                  shard_index; the result is that shard's own top-k, min(k, shard
                                  size) entries, and bcm_topk_merge of every shard's lists is the
                                  graph's top-k.  shard_count 0 or 1 = every source */
+    uint32_t cta_table;       /* entries of a per-CTA wave's vertex table.  Where the per-CTA
+                                 waves can defer (top-k runs, no BCM_CTA_ONLY / BCM_GRID_ONLY /
+                                 BCM_NO_DEFER) and n is larger, the table is hashed with this many
+                                 entries (a power of two >= 1024; 0 = default, n/16 rounded up to a
+                                 power of two within [65536, 2^20]), and a wave
+                                 that makes more than half as many entries is deferred like a wide
+                                 one; otherwise (or with a value >= n) it is dense, n entries.
+                                 Results are the same either way */
 } bcm_options;
 
 typedef struct {
@@ -144,14 +159,17 @@ typedef struct {
     double   preprocess_ms;   /* device time of preprocessing done by this call */
     double   total_ms;        /* wall time of the call */
     double   seed_ms;         /* device time of the grid-wide waves (or of the plain launches) */
-    double   wave_ms;         /* device time of the per-CTA wave kernel */
+    double   wave_ms;         /* device time of the per-CTA wave kernel (or of the one-source kernel) */
     uint64_t wave_bytes;      /* algorithmic bytes the per-CTA wave kernel moved: 20 per source
                                  started, 28 per frontier word, 12 per (arc, frontier word), 32 per
-                                 new frontier word, 28 per cleared word */
+                                 new frontier word, 28 per cleared word; the one-source kernel: 20 per
+                                 source, 12 per frontier vertex, 8 per arc, 16 per discovered vertex,
+                                 12 per cleared bitmap word */
     uint64_t grid_waves;      /* waves run by the grid-wide kernel */
     uint64_t grid_levels;     /* levels those waves expanded */
     uint64_t grid_bytes;      /* algorithmic bytes of the grid-wide kernel (same unit costs) */
     uint64_t deferred;        /* sources per-CTA waves handed to the grid-wide pass */
+    uint64_t sparse;          /* sources the one-source-per-CTA kernel ran (BCM_SPARSE), else 0 */
 } bcm_stats;
 
 /*

@@ -10,6 +10,10 @@ fastest on it:
   pull_div     the push/pull switch: a grid level is pulled once its
                frontier's out-arcs reach n*W/pull_div
   threads      the per-CTA kernel's block shape (256, 512, 1024 threads)
+  per_cta      which per-CTA kernel runs after the grid-wide waves: the
+               library's choice, bit-lane waves (BCM_NO_SPARSE) or one
+               source per CTA (BCM_SPARSE); tried on graphs whose largest
+               degree is at most 64, where the two are close
 
 Search: coordinate descent from the library defaults -- one parameter at a
 time over its candidates with the others held, kept if it beats the best
@@ -35,6 +39,9 @@ SPACE = {
     "threads": (512, 256, 1024),
 }
 DEFAULTS = {"grid_lanes": 128, "pull_div": 32, "lanes": 64, "threads": 512}
+PER_CTA = {"auto": 0, "bitlanes": bcm.BCM_NO_SPARSE, "sparse": bcm.BCM_SPARSE}
+KERNEL_MAX_DEG = 64   # graphs with a larger degree keep the library's choice
+KERNEL_TRIAL_MS = 200.0   # ... and so do graphs whose default run takes longer
 
 
 def _device_name() -> str:
@@ -49,9 +56,17 @@ def _valid(cfg) -> bool:
     return cfg["threads"] >= cfg["lanes"]
 
 
+def options_of(cfg):
+    """bcm_topk keyword arguments of a tuned setting."""
+    kw = dict(cfg)
+    per = kw.pop("per_cta", "auto")
+    return kw, PER_CTA[per]
+
+
 def measure(h, k, cfg, reps=3, flags=0):
     """Median kernel time (ms) of bcm_topk with cfg, and its result."""
-    kw = dict(cfg)
+    kw, extra = options_of(cfg)
+    flags = flags | extra
     h.topk(k, flags=flags, **kw)
     ts = []
     res = None
@@ -62,15 +77,24 @@ def measure(h, k, cfg, reps=3, flags=0):
     return float(np.median(ts)), res
 
 
-def tune(h, k=10, rounds=2, reps=3, margin=0.02, flags=0, log=None):
-    """Coordinate descent over SPACE on the handle `h` (a BcmGraph).
-    Returns (best config, its time in ms, trials)."""
+def tune(h, k=10, rounds=2, reps=3, margin=0.02, flags=0, log=None, kernels=False):
+    """Coordinate descent over SPACE (and, with kernels, the per-CTA kernel)
+    on the handle `h` (a BcmGraph).  Returns (best config, its time in ms,
+    trials)."""
     best = dict(DEFAULTS)
+    space = dict(SPACE)
+    if kernels:
+        best["per_cta"] = "auto"
     best_t, ref = measure(h, k, best, reps, flags)
+    # the other kernel can be far slower on a graph that suits the default
+    # (bit lanes on a large lattice: a hundred times), so it is tried only
+    # where a trial is cheap
+    if kernels and best_t <= KERNEL_TRIAL_MS:
+        space["per_cta"] = tuple(PER_CTA)
     trials = [(dict(best), best_t)]
     for _ in range(rounds):
         changed = False
-        for name, values in SPACE.items():
+        for name, values in space.items():
             for v in values:
                 if v == best[name]:
                     continue
@@ -129,6 +153,7 @@ def tuned_options(h, graph, k=10, cache_path=None, **kw):
         if hit:
             return hit["config"], 0.0, True
     t0 = time.perf_counter()
+    kw.setdefault("kernels", bool(graph.n) and int(graph.degrees().max()) <= KERNEL_MAX_DEG)
     cfg, ms, _ = tune(h, k, **kw)
     spent = time.perf_counter() - t0
     if cache:

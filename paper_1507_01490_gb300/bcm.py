@@ -37,6 +37,8 @@ BCM_NO_PREFILTER = 0x400
 BCM_NO_CUT = 0x800
 BCM_TRACE_LANES = 0x1000
 BCM_ALL_PULL = 0x2000
+BCM_SPARSE = 0x4000
+BCM_NO_SPARSE = 0x8000
 
 # trace record kinds (bits 60..63 of a record's second word)
 TRACE_GRID_LEVEL, TRACE_GRID_WAVE, TRACE_CTA_WAVE, TRACE_LANE_LEVEL, TRACE_LANE_END = 0, 1, 2, 3, 4
@@ -56,7 +58,7 @@ class bcm_options(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_uint32), ("grid_lanes", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("blocks", ctypes.c_uint32), ("threads", ctypes.c_uint32), ("heavy_words", ctypes.c_uint32),
                 ("pull_div", ctypes.c_uint32), ("defer_words", ctypes.c_uint32), ("wait_limit_ns", ctypes.c_uint64),
-                ("shard_index", ctypes.c_uint32), ("shard_count", ctypes.c_uint32)]
+                ("shard_index", ctypes.c_uint32), ("shard_count", ctypes.c_uint32), ("cta_table", ctypes.c_uint32)]
 
 
 class bcm_key(ctypes.Structure):
@@ -76,7 +78,8 @@ class bcm_stats(ctypes.Structure):
                 ("kernel_ms", ctypes.c_double), ("preprocess_ms", ctypes.c_double),
                 ("total_ms", ctypes.c_double), ("seed_ms", ctypes.c_double), ("wave_ms", ctypes.c_double),
                 ("wave_bytes", ctypes.c_uint64), ("grid_waves", ctypes.c_uint64),
-                ("grid_levels", ctypes.c_uint64), ("grid_bytes", ctypes.c_uint64), ("deferred", ctypes.c_uint64)]
+                ("grid_levels", ctypes.c_uint64), ("grid_bytes", ctypes.c_uint64), ("deferred", ctypes.c_uint64),
+                ("sparse", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -184,9 +187,9 @@ def bcm_launch_count() -> int:
 
 
 def make_options(lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0, grid_lanes=0,
-                 heavy_words=0, pull_div=0, defer_words=0, shard_index=0, shard_count=0) -> bcm_options:
+                 heavy_words=0, pull_div=0, defer_words=0, shard_index=0, shard_count=0, cta_table=0) -> bcm_options:
     return bcm_options(lanes, grid_lanes, flags, blocks, threads, heavy_words, pull_div, defer_words, wait_limit_ns,
-                       shard_index, shard_count)
+                       shard_index, shard_count, cta_table)
 
 
 def bcm_graph_create(row_ptr, col, n, m, directed, ptr_on_device=False, stream=None, flags=0):
@@ -381,14 +384,15 @@ class BcmGraph:
         return comp[:self.n], al[:self.n], om[:self.n], nc
 
     def topk(self, k, lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0, grid_lanes=0, heavy_words=0,
-             pull_div=0, defer_words=0, shard_index=0, shard_count=0):
+             pull_div=0, defer_words=0, shard_index=0, shard_count=0, cta_table=0):
         kk = max(min(k, self.n), 1)
         ids = np.zeros(kk, np.uint32)
         far = np.zeros(kk, np.uint64)
         reach = np.zeros(kk, np.uint32)
         st = bcm_stats()
         bcm_topk(self.h, k, make_options(lanes, flags, blocks, threads, wait_limit_ns, grid_lanes, heavy_words,
-                                         pull_div, defer_words, shard_index, shard_count), ids, far, reach, st)
+                                         pull_div, defer_words, shard_index, shard_count, cta_table),
+                 ids, far, reach, st)
         n_src = shard_size(self.n, shard_index, shard_count) if shard_count > 1 else self.n
         kk = min(k, n_src)
         return ids[:kk], far[:kk], reach[:kk], st.as_dict()

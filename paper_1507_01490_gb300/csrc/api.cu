@@ -57,8 +57,11 @@ static bcm_status cuda_fail(cudaError_t e, const char* what) {
 // with (vertex count, words per vertex, CTA count): frontier lists and logs
 // of one layout overlap the bit arrays of another.
 struct Layout {
-    uint32_t n = 0, W = 0, blocks = 0;
-    bool operator==(const Layout& o) const { return n == o.n && W == o.W && blocks == o.blocks; }
+    uint32_t n = 0, W = 0, blocks = 0, entries = 0;   // entries: the vertex tables', or the sparse queues'
+    bool sparse = false;
+    bool operator==(const Layout& o) const {
+        return n == o.n && W == o.W && blocks == o.blocks && entries == o.entries && sparse == o.sparse;
+    }
 };
 struct Region { int dev; void* ptr; size_t bytes; Layout layout; };
 static std::mutex g_region_mu;
@@ -269,6 +272,7 @@ struct Aux {
     int err;
     Threshold thr;
     Threshold ext;        // key offered by bcm_topk_offer (written by the host while the run goes on)
+    Threshold snap;       // the threshold all blocks of a grid-wide or plain launch cut with
     unsigned long long stats[ST_COUNT];        // per-CTA wave kernel
     unsigned long long seed_stats[ST_COUNT];   // seed wave / plain kernel
     GridBarrier bar;
@@ -328,6 +332,7 @@ struct bcm_graph {
     bool simple = false;           // rows strictly increasing, no self-loops (found by preprocessing):
                                    // level 1 of every BFS is then known from degrees alone (the prefilter)
     bool preprocessed = false;
+    uint32_t max_deg = 0;          // largest row length (found by preprocessing)
     Aux* d_aux = nullptr;
     uint32_t* d_plain = nullptr;   // stamps [n], two vertex queues [2n]
     unsigned long long* d_far = nullptr;   // exhaustive outputs [n]
@@ -339,6 +344,7 @@ struct bcm_graph {
         bool active = false;
         bool exhaustive = false;
         bool plain = false;
+        bool sparse = false;      // the per-CTA phase ran k_sparse
         uint32_t kk = 0;          // entries the top-k must hold
         uint32_t flags = 0;
         uint64_t l0 = 0;          // launch counter at the start
@@ -367,7 +373,6 @@ struct bcm_graph {
 namespace {
 
 constexpr uint64_t kDefaultLimitNs = 20ull * 1000 * 1000 * 1000;
-constexpr uint64_t kCtaRegionCap = 2ull << 30;   // default bound on the per-CTA slots of a run
 
 struct Cfg {
     int W, threads, blocks, grid_W, grid_blocks;
@@ -377,35 +382,73 @@ struct Cfg {
     uint32_t shard_index, shard_count;
     uint64_t limit_ns;
     uint32_t flags;
+    uint32_t cta_entries, tab_shift;   // per-CTA vertex tables (WaveParams)
+    bool sparse;                       // per-CTA phase: one source per CTA (k_sparse)
+    uint32_t sparse_qcap;
 };
+
+// Entries of a hashed per-CTA vertex table by default: n/16 rounded up to a
+// power of two, within [2^16, 2^20].  A per-CTA wave runs after the
+// grid-wide waves and the prefilter and reaches a small part of the graph
+// before it completes, is cut, or turns wide enough to be deferred anyway
+// (Chung-Lu n = 2^20 leaves no source to the per-CTA waves at all), so a
+// table of n/16 entries stands in for n records per CTA.  Measured on
+// Barabasi-Albert n = 2^21 (k = 10): 2^16 entries deferred 258,176 sources
+// (611 ms against 75 ms dense), 2^17 none (88 ms, 2.0 GB of slots against
+// 26.5 GB).
+constexpr uint32_t kCtaTableMin = 1u << 16, kCtaTableMax = 1u << 20;
+uint32_t default_cta_table(uint32_t n) {
+    uint32_t t = kCtaTableMin;
+    while (t < kCtaTableMax && (uint64_t)t * 16 < n) t <<= 1;
+    return t;
+}
+
+// One source per CTA (k_sparse) by default on undirected graphs whose
+// largest degree is at most this: lattices, meshes, road-like graphs, where
+// the sources of a wave (consecutive in the degree order) have BFS spheres
+// that share almost no vertex at any level, and bit lanes would carry one
+// live bit per word.  A hub is reached by every source's search and makes
+// lanes share frontiers, so graphs with hubs keep the bit-lane waves.
+constexpr uint32_t kSparseMaxDeg = 8;
+// Entries of each of its vertex queues where a longer frontier can be
+// deferred to the grid-wide pass (else n).
+constexpr uint32_t kSparseQcap = 1u << 18;
 
 bcm_status resolve(bcm_graph* g, const bcm_options* opt, Cfg* c) {
     bcm_options o{};
     if (opt) o = *opt;
     c->flags = o.flags;
+    if ((o.flags & BCM_SPARSE) && (o.flags & BCM_NO_SPARSE))
+        return fail(BCM_ERR_INVALID, "BCM_SPARSE and BCM_NO_SPARSE exclude each other");
     uint32_t lanes = o.lanes ? o.lanes : 64;
     if (lanes != 64 && lanes != 128 && lanes != 256)
         return fail(BCM_ERR_UNSUPPORTED, "lanes must be 64, 128 or 256 (got %u)", lanes);
     c->W = (int)(lanes / 64);
-    c->threads = o.threads ? (int)o.threads : 512;
-    if (c->threads != 256 && c->threads != 512 && c->threads != 1024)
-        return fail(BCM_ERR_UNSUPPORTED, "threads must be 256, 512 or 1024 (got %u)", o.threads);
-    if (c->threads < 64 * c->W)
-        return fail(BCM_ERR_UNSUPPORTED, "threads (%d) must be >= lanes (%u)", c->threads, lanes);
-    int per = cta_blocks_per_sm(c->W, c->threads);
+    // one source per CTA: asked for, or by default on undirected graphs
+    // without hubs (kSparseMaxDeg)
+    c->sparse = !(o.flags & BCM_GRID_ONLY) &&
+                ((o.flags & BCM_SPARSE) || (!(o.flags & BCM_NO_SPARSE) && !g->directed && g->n >= 4096 &&
+                                            g->max_deg <= kSparseMaxDeg));
+    // its default block is 256 threads (more sources at once: 2.5 s against
+    // 3.4 s for 512 on a 512^2 damaged grid); it also runs 128
+    c->threads = o.threads ? (int)o.threads : (c->sparse ? 256 : 512);
+    if (c->sparse) {
+        if (c->threads != 128 && c->threads != 256 && c->threads != 512 && c->threads != 1024)
+            return fail(BCM_ERR_UNSUPPORTED, "threads must be 128, 256, 512 or 1024 (got %u)", o.threads);
+    } else {
+        if (c->threads != 256 && c->threads != 512 && c->threads != 1024)
+            return fail(BCM_ERR_UNSUPPORTED, "threads must be 256, 512 or 1024 (got %u)", o.threads);
+        if (c->threads < 64 * c->W)
+            return fail(BCM_ERR_UNSUPPORTED, "threads (%d) must be >= lanes (%u)", c->threads, lanes);
+    }
+    const int per_threads = c->threads < 256 ? 256 : c->threads;   // the wave kernel's shape (not run)
+    int per = cta_blocks_per_sm(c->W, per_threads < 64 * c->W ? 64 * c->W : per_threads);
     if (per < 1) return fail(BCM_ERR_CUDA, "wave kernel does not fit on an SM");
     int maxb = per * g->sms;
     // default: every CTA that fits, but no more than there are waves of
-    // sources (a small graph then holds a small workspace), and no more than
-    // keep the per-CTA slots (dense in n) within kCtaRegionCap: on large
-    // graphs the grid-wide waves and the prefilter leave the per-CTA waves
-    // little to do, and a slot per resident CTA would hold tens of GB
+    // sources (a small graph then holds a small workspace)
     uint64_t waves = ((uint64_t)g->n + 64 * c->W - 1) / (64 * c->W);
     c->blocks = o.blocks ? (int)o.blocks : (waves < (uint64_t)maxb ? (int)(waves ? waves : 1) : maxb);
-    if (!o.blocks) {
-        const uint64_t fit = kCtaRegionCap / slot_bytes(g->n, c->W);
-        if ((uint64_t)c->blocks > fit) c->blocks = fit > 0 ? (int)fit : 1;
-    }
     if (c->blocks > maxb) c->blocks = maxb;
     c->limit_ns = o.wait_limit_ns ? o.wait_limit_ns : kDefaultLimitNs;
     uint32_t glanes = o.grid_lanes ? o.grid_lanes : 128;
@@ -418,6 +461,32 @@ bcm_status resolve(bcm_graph* g, const bcm_options* opt, Cfg* c) {
     c->heavy_words = o.heavy_words ? o.heavy_words : (uint64_t)gb * 16 * 4;   // 4 words per warp and level
     c->pull_div = (c->flags & BCM_NO_PULL) ? 0u : o.pull_div;   // 0: per-mode default below
     c->defer_words = (c->flags & BCM_NO_DEFER) ? 0 : (o.defer_words ? o.defer_words : c->heavy_words);
+    // per-CTA vertex tables: hashed where a wave that fills its table can be
+    // handed to the grid-wide pass (deferral on, and a graph larger than the
+    // table), else dense
+    if (o.cta_table && o.cta_table < g->n && (o.cta_table < 1024 || (o.cta_table & (o.cta_table - 1))))
+        return fail(BCM_ERR_UNSUPPORTED, "cta_table must be a power of two >= 1024, or >= n (got %u)", o.cta_table);
+    const uint32_t tab = o.cta_table ? o.cta_table : default_cta_table(g->n);
+    const bool can_defer = !(c->flags & (BCM_CTA_ONLY | BCM_GRID_ONLY)) && c->defer_words &&
+                           (uint64_t)g->n * c->W >= c->defer_words;
+    if (can_defer && tab < g->n) {
+        c->cta_entries = tab;
+        c->tab_shift = 1 + (uint32_t)__builtin_clz(tab);   // 32 - log2(tab)
+    } else {
+        c->cta_entries = g->n;
+        c->tab_shift = 0;
+    }
+    // one source per CTA: its queues are bounded only where an overflowing
+    // source can be deferred
+    const bool sparse_defer = !(c->flags & (BCM_CTA_ONLY | BCM_GRID_ONLY)) && c->defer_words;
+    c->sparse_qcap = (sparse_defer && g->n > kSparseQcap) ? kSparseQcap : g->n;
+    if (c->sparse) {
+        const int sper = sparse_blocks_per_sm(c->threads);
+        if (sper < 1) return fail(BCM_ERR_CUDA, "one-source kernel does not fit on an SM");
+        const int smax = sper * g->sms;
+        c->blocks = o.blocks ? (int)o.blocks : (g->n < (uint32_t)smax ? (int)(g->n ? g->n : 1) : smax);
+        if (c->blocks > smax) c->blocks = smax;
+    }
     c->shard_count = o.shard_count > 1 ? o.shard_count : 1;
     c->shard_index = o.shard_count > 1 ? o.shard_index : 0;
     if (c->shard_index >= c->shard_count)
@@ -428,7 +497,10 @@ bcm_status resolve(bcm_graph* g, const bcm_options* opt, Cfg* c) {
 }
 
 // CTA slots first, then one slot (4 words per vertex) for the grid-wide waves.
-size_t cta_region_bytes(bcm_graph* g, const Cfg& c) { return (size_t)c.blocks * slot_bytes(g->n, c.W); }
+size_t cta_slot_stride(bcm_graph* g, const Cfg& c) {
+    return c.sparse ? sparse_slot_bytes(g->n, c.sparse_qcap) : slot_bytes(c.cta_entries, c.W);
+}
+size_t cta_region_bytes(bcm_graph* g, const Cfg& c) { return (size_t)c.blocks * cta_slot_stride(g, c); }
 size_t region_bytes(bcm_graph* g, const Cfg& c) {
     return cta_region_bytes(g, c) + slot_bytes(g->n, 4);
 }
@@ -437,6 +509,8 @@ Layout region_layout(bcm_graph* g, const Cfg& c) {
     l.n = g->n;
     l.W = (uint32_t)c.W;
     l.blocks = (uint32_t)c.blocks;
+    l.entries = c.sparse ? c.sparse_qcap : c.cta_entries;
+    l.sparse = c.sparse;
     return l;
 }
 
@@ -465,6 +539,9 @@ bcm_status check_dev_err(int err) {
     if (err & (DEV_ERR_BARRIER_TIMEOUT | DEV_ERR_LOCK_TIMEOUT))
         return fail(BCM_ERR_TIMEOUT, "an in-kernel wait ran past its limit (device error bits 0x%x)", err);
     if (err & DEV_ERR_INVALID_CSR) return fail(BCM_ERR_INVALID, "malformed CSR (device check 0x%x)", err);
+    if (err & DEV_ERR_TABLE_FULL)
+        return fail(BCM_ERR_CUDA, "a per-CTA wave filled its vertex table with no grid-wide pass to take it "
+                                  "(device error bits 0x%x)", err);
     return fail(BCM_ERR_CUDA, "device error bits 0x%x", err);
 }
 
@@ -522,7 +599,7 @@ bcm_status preprocess(bcm_graph* g, double* ms) {
         }
         forked = true;
         if (cudaMemsetAsync(d_simple, 0, sizeof(int), g->aux) != cudaSuccess ||
-            launch_degree_order(g->d_rp, n, g->d_order, d_scr2, dos, g->aux) ||
+            launch_degree_order(g->d_rp, n, g->d_order, d_scr2, dos, g->aux, &g->max_deg) ||
             launch_simple_check(g->d_rp, g->d_col, n, g->m, d_simple, d_scr2 + dos, g->aux) ||
             cudaMemcpyAsync(&g->h->not_simple, d_simple, sizeof(int), cudaMemcpyDeviceToHost, g->aux) != cudaSuccess) {
             st = fail(BCM_ERR_CUDA, "degree order: %s", cudaGetErrorString(cudaGetLastError()));
@@ -636,8 +713,13 @@ WaveParams base_params(bcm_graph* g, const Cfg& c) {
     p.topk.lock = &a->lock;
     p.topk.thr = &a->thr;
     p.topk.ext = &a->ext;
+    p.snap = &a->snap;
     p.slot_base = (char*)g->slots.ptr;
-    p.slot_stride = slot_bytes(g->n, c.W);
+    p.slot_stride = cta_slot_stride(g, c);
+    p.sparse_qcap = c.sparse_qcap;
+    p.cta_entries = c.cta_entries;
+    p.tab_shift = c.tab_shift;
+    p.tab_limit = c.cta_entries / 2;
     p.seed_base = (char*)g->slots.ptr + cta_region_bytes(g, c);
     p.stats = a->stats;
     p.err = &a->err;
@@ -666,6 +748,17 @@ WaveParams base_params(bcm_graph* g, const Cfg& c) {
 uint64_t wave_alg_bytes(const unsigned long long* w, uint64_t sources) {
     return 20ull * sources + 28ull * (w[ST_ENTRIES] - w[ST_PULLENTRIES]) + 12ull * w[ST_PULLENTRIES] +
            12ull * w[ST_ARCWORDS] + 32ull * w[ST_DISCWORDS] + 28ull * w[ST_CLEARED];
+}
+
+// The one-source kernel's (its counters count vertices, arcs and bitmap words):
+//   source started            20 B  order entry, row_ptr pair, x_lo/x_hi
+//   frontier vertex expanded  12 B  queue entry, row_ptr pair
+//   arc scanned                8 B  col entry, the target's bitmap word
+//   vertex discovered         16 B  bitmap atomicOr, row_ptr pair, queue entry
+//   cleared bitmap word       12 B  log entry written and read, the word cleared
+uint64_t sparse_alg_bytes(const unsigned long long* w, uint64_t sources) {
+    return 20ull * sources + 12ull * w[ST_ENTRIES] + 8ull * w[ST_ARCWORDS] + 16ull * w[ST_DISCWORDS] +
+           12ull * w[ST_CLEARED];
 }
 
 void fill_stats(bcm_stats* s, const unsigned long long* st, uint64_t launches, double kms, double pms, double tms) {
@@ -815,12 +908,17 @@ bcm_status start_run(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, vo
         // A top-k run on a graph with fewer (vertex, word) pairs than the
         // heavy threshold cannot have a heavy wave and skips the grid kernel.
         const bool grid = !(c.flags & BCM_CTA_ONLY) &&
-                          (exhaustive || (c.flags & BCM_GRID_ONLY) || (uint64_t)g->n * c.grid_W >= c.heavy_words);
+                          ((c.flags & BCM_GRID_ONLY) ||
+                           (!c.sparse && (exhaustive || (uint64_t)g->n * c.grid_W >= c.heavy_words)));
         // a per-CTA wave whose frontier grows to defer_words words hands its
         // sources to a second grid-wide pass (only where one can follow, and
         // only if a frontier that wide is possible)
-        const bool defer = !exhaustive && !(c.flags & (BCM_CTA_ONLY | BCM_GRID_ONLY)) && c.defer_words &&
-                           (uint64_t)g->n * c.W >= c.defer_words;
+        // (one source per CTA: a source whose frontier outgrows its queue,
+        // in exhaustive runs too)
+        const bool defer = c.sparse ? (!(c.flags & (BCM_CTA_ONLY | BCM_GRID_ONLY)) && c.defer_words &&
+                                       c.sparse_qcap < g->n)
+                                    : (!exhaustive && !(c.flags & (BCM_CTA_ONLY | BCM_GRID_ONLY)) && c.defer_words &&
+                                       (uint64_t)g->n * c.W >= c.defer_words);
         if (defer) {
             if (!g->d_defer) CU(buf_get_t(&g->d_defer, (size_t)g->n * sizeof(uint32_t)), "defer list allocation");
             p.defer_words = (uint32_t)(c.defer_words < 0xffffffffull ? c.defer_words : 0xffffffffull);
@@ -840,7 +938,8 @@ bcm_status start_run(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, vo
         // first wave alone (the highest-degree sources), so the threshold
         // exists before the other waves start (otherwise they all start at
         // once, and none of them can be stopped)
-        const bool seed = !grid && rc == 0 && !exhaustive && !(c.flags & (BCM_CTA_ONLY | BCM_NO_PREFILTER));
+        const bool seed = !grid && rc == 0 && !exhaustive && !c.sparse &&
+                          !(c.flags & (BCM_CTA_ONLY | BCM_NO_PREFILTER));
         if (seed) {
             WaveParams ps = p;
             ps.max_cta_waves = 1;
@@ -864,7 +963,8 @@ bcm_status start_run(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, vo
             pc.n_end = 0;
             pc.n_end_dev = &g->d_aux->surv_n;
         }
-        if (rc == 0) rc = launch_cta_waves(pc, c.W, c.blocks, c.threads, s);
+        if (rc == 0)
+            rc = c.sparse ? launch_sparse(pc, c.blocks, c.threads, s) : launch_cta_waves(pc, c.W, c.blocks, c.threads, s);
         cudaEventRecord(g->ev[2], s);
         if (defer && rc == 0) {
             // the deferred sources, on the grid kernel, every wave
@@ -908,6 +1008,7 @@ bcm_status start_run(bcm_graph* g, const Cfg& c, uint32_t k, bool exhaustive, vo
     g->pend.active = true;
     g->pend.exhaustive = exhaustive;
     g->pend.plain = plain;
+    g->pend.sparse = !plain && c.sparse;
     g->pend.kk = k < n_src ? k : n_src;
     g->pend.flags = c.flags;
     return BCM_OK;
@@ -970,7 +1071,10 @@ void fill_run_stats(bcm_stats* stats, bcm_graph* g, const unsigned long long* sv
     const bool plain = g->pend.plain;
     stats->seed_ms = rt.seed_ms;
     stats->wave_ms = rt.wave_ms;
-    stats->wave_bytes = plain ? 0 : wave_alg_bytes(wv, wv[ST_COMPLETED] + wv[ST_CUT]);
+    stats->wave_bytes = plain ? 0
+                      : g->pend.sparse ? sparse_alg_bytes(wv, wv[ST_WAVES])
+                                       : wave_alg_bytes(wv, wv[ST_COMPLETED] + wv[ST_CUT]);
+    stats->sparse = g->pend.sparse ? wv[ST_WAVES] : 0;
     stats->grid_waves = rt.grid[ST_WAVES];
     stats->grid_levels = rt.grid[ST_LEVELS];
     stats->grid_bytes = plain ? 0 : wave_alg_bytes(rt.grid, rt.grid[ST_COMPLETED] + rt.grid[ST_CUT]);
@@ -1187,6 +1291,7 @@ bcm_status bcm_topk_start(bcm_graph_t g, uint32_t k, const bcm_options* opt, uin
         g->pend.active = true;
         g->pend.exhaustive = false;
         g->pend.plain = false;
+        g->pend.sparse = false;
         g->pend.kk = 0;
         g->pend.flags = 0;
     }
@@ -1540,6 +1645,7 @@ bcm_status bcm_batch_destroy(bcm_batch_t b) {
 
 uint64_t bcm_workspace_bytes(bcm_graph_t g, const bcm_options* opt) {
     if (!g) return 0;
+    if (!g->preprocessed && preprocess(g, nullptr) != BCM_OK) return 0;   // the default kernels depend on it
     Cfg c;
     if (resolve(g, opt, &c)) return 0;
     return (uint64_t)region_bytes(g, c) + sizeof(Aux) + (uint64_t)g->n * 12;

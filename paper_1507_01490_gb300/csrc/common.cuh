@@ -20,6 +20,7 @@ enum DevErr : int {
     DEV_ERR_LOCK_TIMEOUT = 2,      // the top-k lock wait ran past its limit
     DEV_ERR_INVALID_CSR = 4,       // input validation failed
     DEV_ERR_RETRY_LIMIT = 8,       // a lock-free retry loop exceeded its cap
+    DEV_ERR_TABLE_FULL = 16,       // a per-CTA wave's vertex table filled where no grid pass could take it
 };
 
 __device__ __forceinline__ u64 global_ns() {
@@ -80,6 +81,23 @@ __device__ __forceinline__ void read_threshold(const Threshold* t, ThrCache& c) 
         __threadfence();
         if (vload(&t->seq) == s1) { c.N = N; c.F = F; c.id = id; c.valid = valid; return; }
     }
+}
+
+// The threshold every block of a grid-wide launch cuts with at one level:
+// taken by the leader block's thread 0 before a grid barrier and read by all
+// blocks after it, so that they agree on which lanes live (a key offered by
+// the host may arrive between two blocks' own reads of the published ones).
+__device__ __forceinline__ void store_snapshot(Threshold* snap, const ThrCache& c) {
+    vstore(&snap->N, c.N);
+    vstore(&snap->F, c.F);
+    vstore(&snap->id, c.id);
+    vstore(&snap->valid, c.valid);
+}
+__device__ __forceinline__ void load_snapshot(const Threshold* snap, ThrCache& c) {
+    c.N = vload(&snap->N);
+    c.F = vload(&snap->F);
+    c.id = vload(&snap->id);
+    c.valid = vload(&snap->valid);
 }
 
 // ------------------------------------------------- stopping rule (BFSCut)

@@ -41,13 +41,22 @@ struct GraphDev {
 };
 
 // Per-slot working memory of one MS-BFS wave with W words (64W sources) per
-// vertex.  Word index of (vertex v, word g) is v*W + g; each word has a
-// 32-byte record (vis, F[0], F[1], padding), then two frontier lists and a
-// clear log of 4-byte word indices.
+// vertex, for n vertices (or table entries).  Word index of (entry v, word g)
+// is v*W + g; each word has a 32-byte record (vis, key, F[0], F[1]), then two
+// frontier lists and a clear log of 4-byte word indices.
 constexpr size_t slot_bytes(uint32_t n, int W) {
     size_t nw = (size_t)n * W;
     size_t b = nw * (4 * sizeof(uint64_t) + 3 * sizeof(uint32_t));
     return (b + 255) & ~(size_t)255;
+}
+
+// One-source-per-CTA slot (k_sparse): a visited bitmap of one bit per vertex,
+// the log of its words that became non-zero, then two queues of qcap
+// entries each (a frontier vertex's first arc and degree, 8 bytes).
+__host__ __device__ constexpr size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+__host__ __device__ constexpr size_t sparse_bitmap_bytes(uint32_t n) { return al256(((size_t)n + 31) / 32 * sizeof(uint32_t)); }
+__host__ __device__ constexpr size_t sparse_slot_bytes(uint32_t n, uint32_t qcap) {
+    return 2 * sparse_bitmap_bytes(n) + 2 * al256((size_t)qcap * 2 * sizeof(uint32_t));
 }
 
 // The grid kernel's per-lane level counters are summed in kCntCopies copies
@@ -77,6 +86,16 @@ struct WaveParams {
     uint32_t* out_reach;
     char* slot_base;         // CTA i: slot_base + i * slot_stride
     size_t slot_stride;
+    // per-CTA slots: vertex tables of cta_entries entries (cta_entries = n
+    // and tab_shift = 0: dense, vertex x is entry x; else hashed, cta_entries
+    // = 2^(32 - tab_shift), and a wave making more than tab_limit entries is
+    // given up and deferred)
+    uint32_t cta_entries;
+    uint32_t tab_shift;
+    uint32_t tab_limit;
+    // one-source-per-CTA kernel: entries of each vertex queue (a longer
+    // frontier defers the source)
+    uint32_t sparse_qcap;
     char* seed_base;         // the grid kernel's own slot (4 words per vertex)
     unsigned long long* stats;   // [ST_COUNT]
     int* err;
@@ -113,6 +132,7 @@ struct WaveParams {
     uint32_t* trace_n;       // records written (may exceed trace_cap; the excess is dropped)
     uint32_t trace_lanes;    // also record every lane's level state and end (needs trace)
     uint32_t nocut;          // top-k runs: never stop a source (every BFS runs to its end)
+    Threshold* snap;         // grid-wide and plain kernels: the threshold all blocks cut with (see store_snapshot)
 };
 
 // Trace record kinds (bits 60..63 of a record's second word).
@@ -130,7 +150,7 @@ int launch_simple_check(const uint32_t* rp32, const uint32_t* col, uint32_t n, u
 int launch_cc_reach(const uint32_t* rp, const uint32_t* col, uint32_t n, uint32_t* parent,
                     uint32_t* size, uint32_t* xlo, uint32_t* xhi, int* err, cudaStream_t s);
 int launch_degree_order(const uint32_t* rp, uint32_t n, uint32_t* order, void* scratch,
-                        size_t scratch_bytes, cudaStream_t s);
+                        size_t scratch_bytes, cudaStream_t s, uint32_t* max_degree = nullptr);
 size_t degree_order_scratch_bytes(uint32_t n);
 // stable LSD radix sort of (key, value) pairs on the low `bits` of the key
 size_t radix_scratch_bytes(size_t count);
@@ -167,6 +187,9 @@ int launch_plain_source(const WaveParams& p, uint32_t it, uint32_t* stamp, uint3
 
 int max_coop_blocks(int kind, int W, int threads);   // kind 0 grid waves, 1 plain
 int cta_blocks_per_sm(int W, int threads);
+// one source per CTA (high-diameter graphs): sources p.sources[*p.head .. n_end)
+int launch_sparse(const WaveParams& p, int blocks, int threads, cudaStream_t s);
+int sparse_blocks_per_sm(int threads);
 
 // launch bookkeeping (api.cu)
 void note_launch(int count = 1);

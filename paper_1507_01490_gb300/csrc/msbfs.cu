@@ -34,9 +34,10 @@ namespace bcm {
 // Two layouts of the bit words of a (vertex, 64-lane word) pair -- vis,
 // F[0], F[1] -- chosen per kernel by the template parameter R, the stride
 // between consecutive words of one array:
-//   R = 4  records: the three words sit in one 32-byte record (the fourth
-//          u64 is padding), so a push's check and atomics and the wave-end
-//          clear touch a single sector (per-CTA waves: push only);
+//   R = 4  records: the three words sit in one 32-byte record (vis, a key
+//          word, F[0], F[1]), so a push's check and atomics and the wave-end
+//          clear touch a single sector (per-CTA waves: push only).  The
+//          records of a per-CTA slot are a vertex table (CtaTab below);
 //   R = 1  planes: each array is its own plane, and the W words of a vertex
 //          are consecutive in it, so a pulled level reads the vis words of 32
 //          consecutive vertices in one coalesced sweep and an in-neighbour's
@@ -66,8 +67,8 @@ __device__ __forceinline__ SlotPtrs slot_ptrs(char* base, u32 n, int W) {
         s.F[1] = s.vis + 2 * nw;
         s.list[0] = (u32*)(s.vis + 3 * nw);
     } else {
-        s.F[0] = s.vis + 1;
-        s.F[1] = s.vis + 2;
+        s.F[0] = s.vis + 2;   // vis + 1: the key word
+        s.F[1] = s.vis + 3;
         s.list[0] = (u32*)(s.vis + REC * nw);
     }
     s.list[1] = s.list[0] + nw;
@@ -86,6 +87,58 @@ __device__ __forceinline__ void clear_word(const SlotPtrs& S, u32 word) {
         r[0] = make_ulonglong2(0, 0);
         r[1] = make_ulonglong2(0, 0);
     }
+}
+
+// A per-CTA wave's vertex table: which records hold vertex x.
+//   dense  (shift 0): x owns entry x (n entries; the key word is unused);
+//   hashed (shift > 0): x's entry is found from h(x) = (x * kTabMul) >> shift
+//          by linear probing over 2^(32 - shift) entries; the record of the
+//          entry's word 0 keeps x + 1 in its key word, 0 marking a free entry.
+// A wave touches few vertices once the grid-wide waves and the prefilter
+// have run, so a table of 2^16 entries replaces n records per CTA.  Inserts
+// are counted; once `limit` is passed no new entry is made, and the wave is
+// given up at the end of the level: its live sources go to the grid-wide
+// pass, which runs them again from the start (the counts of a level with a
+// dropped arc are incomplete and never used).  The limit (half the table)
+// keeps the table from filling: past it, only the inserts already in
+// flight (two per thread) land.
+struct CtaTab {
+    u32 shift, mask, limit;
+    u32* ins;              // shared: entries this wave inserted
+    volatile u32* full;    // shared: set once an insert passed the limit
+};
+constexpr u32 kTabMul = 0x9E3779B1u;   // 2^32 / golden ratio: Fibonacci hashing
+__device__ constexpr CtaTab kDenseTab{0, 0, 0, nullptr, nullptr};   // the grid kernel's planes
+
+// Entry e of vertex x in a hashed table, inserted if x has none (fl |= 2:
+// the clear log then takes the entry); seen = vis word 0 of the entry as
+// read.  False when x has no entry and the table is past its limit.  Kept
+// out of line: inlined at its call sites it pushed the dense path's
+// registers into spills (out of line, the dense path has none at 64 lanes).
+template <int W>
+__device__ __noinline__ bool tab_find(const CtaTab& T, u64* rec, u32 x, u32& e, u64& seen, u32& fl) {
+    const u32 key = x + 1;
+    e = (x * kTabMul) >> T.shift;
+    for (u32 probe = 0; probe <= T.mask; ++probe) {
+        u64* r = rec + (size_t)e * W * REC;
+        const ulonglong2 kv = __ldcg((const ulonglong2*)r);   // vis word 0, key
+        u32 k = (u32)kv.y;
+        if (k == key) { seen = kv.x; return true; }
+        if (k == 0) {
+            if (*T.full) return false;
+            k = atomicCAS((u32*)(r + 1), 0u, key);
+            if (k == 0) {
+                fl |= 2u;
+                if (atomicAdd(T.ins, 1u) >= T.limit) *T.full = 1;
+                seen = 0;
+                return true;
+            }
+            if (k == key) { seen = __ldcg(r); return true; }
+        }
+        e = (e + 1) & T.mask;
+    }
+    *T.full = 1;   // every entry taken: cannot happen below the limit, and the wave is given up
+    return false;
 }
 
 // Counters of the expansion loops, per thread (kept small: they live in
@@ -201,8 +254,10 @@ struct WarpQueue {
 // memory operations in flight at once.
 struct Push {
     u32 x, g, word, r0, r1;
+    u32 lw;          // hashed table: the entry's word 0, which the clear log takes (dense: the word)
     u64 F, nb;
-    u32 fl;          // bit 0: word enters the next frontier; bit 1: vis word was empty (log it)
+    u32 fl;          // bit 0: word enters the next frontier; bit 1: log lw (a vis word was empty,
+                     // or a table entry was made)
     u32 degp;
 };
 
@@ -214,11 +269,26 @@ __device__ __forceinline__ void push_load(const u32* __restrict__ col, u32 e, u6
 }
 
 template <int W, int R>
-__device__ __forceinline__ void push_check(const u32* __restrict__ rp, const u64* vis, Push& q) {
-    q.word = q.x * W + q.g;
-    q.nb = q.F & ~__ldcg(&vis[ri<R>(q.word)]);
+__device__ __forceinline__ void push_check(const u32* __restrict__ rp, u64* vis, Push& q, const CtaTab& T) {
     q.fl = 0;
     q.degp = 0;
+    u64 seen;
+    if (R == REC && T.shift) {
+        u32 e;
+        if (!tab_find<W>(T, vis, q.x, e, seen, q.fl)) {   // table past its limit: the wave is given up
+            q.nb = 0;
+            q.word = 0;
+            q.lw = 0;
+            return;
+        }
+        q.word = e * W + q.g;
+        q.lw = e * W;
+        if (W > 1 && q.g) seen = __ldcg(&vis[ri<R>(q.word)]);
+    } else {
+        q.word = q.x * W + q.g;
+        seen = __ldcg(&vis[ri<R>(q.word)]);
+    }
+    q.nb = q.F & ~seen;
     if (q.nb) {
         q.r0 = __ldg(&rp[q.x]);
         q.r1 = __ldg(&rp[q.x + 1]);
@@ -231,9 +301,10 @@ __device__ __forceinline__ void push_vis(u64* vis, Push& q, u64& old) {
 }
 
 template <int R>
-__device__ __forceinline__ void push_next(u64* Fnext, Push& q, u64 old, u32 foot, LocalStats& st) {
+__device__ __forceinline__ void push_next(u64* Fnext, Push& q, u64 old, u32 foot, LocalStats& st,
+                                          const CtaTab& T) {
     if (!q.nb) return;
-    q.fl = (old == 0) ? 2u : 0u;
+    if (!(R == REC && T.shift)) q.fl = (old == 0) ? 2u : 0u;   // hashed: logged when the entry was made
     q.nb &= ~old;
     if (!q.nb) return;
     u64 oldF = atomicOr(&Fnext[ri<R>(q.word)], q.nb);
@@ -319,10 +390,12 @@ __device__ __forceinline__ void warp_count_word(u64 nb, u32 degp, u32 g, u32* cg
     if (c_hi) { atomicAdd(&cg[g * 64 + 32 + lane], c_hi); atomicAdd(&cs[g * 64 + 32 + lane], s_hi); }
 }
 
-__device__ __forceinline__ void push_finish(const Push& q, u32* cg, u32* cs, WarpQueue& nq, WarpQueue& lq) {
+template <int R>
+__device__ __forceinline__ void push_finish(const Push& q, u32* cg, u32* cs, WarpQueue& nq, WarpQueue& lq,
+                                            const CtaTab& T) {
     warp_count(q.nb, q.degp, q.g, cg, cs);
     nq.push(q.fl & 1u, q.word);
-    lq.push(q.fl & 2u, q.word);
+    lq.push(q.fl & 2u, (R == REC && T.shift) ? q.lw : q.word);
 }
 
 // Prefix sums of the live sources' degrees (s_pre[0..L]) and their first
@@ -370,29 +443,44 @@ template <int W, int R>
 __device__ inline void expand_sources(const GraphDev& G, const u32* s_src, const u32* s_alive32, const u32* s_pre,
                                       const u32* s_beg, int L, u64* vis, u64* Fnext, u32* cg, u32* cs, u32 foot,
                                       WarpQueue& nq, WarpQueue& lq, u32 wid, u32 nw, u32 tid, u32 nthreads,
-                                      LocalStats& st) {
+                                      const CtaTab& T, LocalStats& st) {
     const u32 lane = threadIdx.x & 31;
     lq.reserve(32);
     for (u32 j0 = tid - lane; j0 < (u32)L; j0 += nthreads) {
         const u32 j = j0 + lane;
         bool first = false;
-        u32 word = 0;
+        u32 lw = 0;
         if (j < (u32)L && ((s_alive32[j >> 5] >> (j & 31)) & 1u)) {
             const u32 deg = s_pre[j + 1] - s_pre[j];
-            word = s_src[j] * W + (j >> 6);
-            first = atomicOr(&vis[ri<R>(word)], 1ull << (j & 63)) == 0;
+            u32 e = s_src[j];
+            bool have = true;
+            if (R == REC && T.shift) {
+                u64 seen;
+                u32 fl = 0;
+                have = tab_find<W>(T, vis, s_src[j], e, seen, fl);
+                first = fl != 0;
+                lw = e * W;
+            }
+            if (have) {
+                const u32 word = e * W + (j >> 6);
+                const bool empty = atomicOr(&vis[ri<R>(word)], 1ull << (j & 63)) == 0;
+                if (!(R == REC && T.shift)) {
+                    first = empty;
+                    lw = word;
+                }
+            }
             st.mvis += deg;
             st.arcwords += deg;
         }
         lq.reserve(32);
-        lq.push(first, word);
+        lq.push(first, lw);
     }
     const u32 total = s_pre[L];
     for (u32 t0 = wid * 32; t0 < total; t0 += nw * 32) {
         const u32 idx = t0 + lane;
         bool v = idx < total;
         Push q;
-        q.nb = 0; q.fl = 0; q.degp = 0; q.g = 0; q.word = 0;
+        q.nb = 0; q.fl = 0; q.degp = 0; q.g = 0; q.word = 0; q.lw = 0;
         if (v) {
             // the lane owning arc idx: the last j with s_pre[j] <= idx
             u32 lo = 0, hi = (u32)L;
@@ -406,14 +494,14 @@ __device__ inline void expand_sources(const GraphDev& G, const u32* s_src, const
         nq.reserve(32);
         lq.reserve(32);
         if (v) {
-            push_check<W, R>(G.rp, vis, q);
+            push_check<W, R>(G.rp, vis, q, T);
             u64 old;
             push_vis<R>(vis, q, old);
-            push_next<R>(Fnext, q, old, foot, st);
+            push_next<R>(Fnext, q, old, foot, st, T);
         } else {
             q.nb = 0;
         }
-        push_finish(q, cg, cs, nq, lq);
+        push_finish<R>(q, cg, cs, nq, lq, T);
     }
 }
 
@@ -437,7 +525,7 @@ template <int W, int R>
 __device__ inline void expand_entries(const GraphDev& G, const u32* list, u32 cnt, u64* Fcur,
                                       const u32* s_alive32, u64* vis, u64* Fnext, u32* cg, u32* cs,
                                       u32 foot, WarpQueue& nq, WarpQueue& lq, u32* chunk_ctr, u32 wid, u32 nw,
-                                      const HeavyList& H, LocalStats& st) {
+                                      const HeavyList& H, const CtaTab& T, LocalStats& st) {
     const u32 lane = threadIdx.x & 31;
     // entries taken per chunk: 32 when the frontier is small, up to 256 when
     // it is large enough to keep every warp busy anyway.  Warp wid's first
@@ -472,6 +560,7 @@ __device__ inline void expand_entries(const GraphDev& G, const u32* list, u32 cn
             u32 word = __ldcg(&list[e]);
             u32 u = word / W;
             g = word - u * W;
+            if (R == REC && T.shift) u = (u32)__ldcg(&vis[ri<R>(u * W) + 1]) - 1;   // the entry's vertex
             F = __ldcg(&Fcur[ri<R>(word)]);
             Fcur[ri<R>(word)] = 0;
             F &= ((u64)s_alive32[2 * g + 1] << 32) | s_alive32[2 * g];
@@ -518,21 +607,21 @@ __device__ inline void expand_entries(const GraphDev& G, const u32* list, u32 cn
                 const u64 o_F = __shfl_sync(0xffffffffu, F, owner);
                 const u32 o_g = __shfl_sync(0xffffffffu, g, owner);
                 v[h] = idx < total;
-                q[h].nb = 0; q[h].fl = 0; q[h].degp = 0; q[h].g = o_g; q[h].word = 0;
+                q[h].nb = 0; q[h].fl = 0; q[h].degp = 0; q[h].g = o_g; q[h].word = 0; q[h].lw = 0;
                 if (v[h]) push_load<W>(G.col, o_beg + idx - o_excl, o_F, o_g, q[h]);
             }
             nq.reserve(64);
             lq.reserve(64);
 #pragma unroll
             for (int h = 0; h < 2; ++h)
-                if (v[h]) push_check<W, R>(G.rp, vis, q[h]);
+                if (v[h]) push_check<W, R>(G.rp, vis, q[h], T);
             u64 old[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) push_vis<R>(vis, q[h], old[h]);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) push_next<R>(Fnext, q[h], old[h], foot, st);
+            for (int h = 0; h < 2; ++h) push_next<R>(Fnext, q[h], old[h], foot, st, T);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) push_finish(q[h], cg, cs, nq, lq);
+            for (int h = 0; h < 2; ++h) push_finish<R>(q[h], cg, cs, nq, lq, T);
         }
     }
 }
@@ -542,7 +631,7 @@ __device__ inline void expand_entries(const GraphDev& G, const u32* list, u32 cn
 template <int W, int R>
 __device__ __noinline__ void expand_heavy(const GraphDev& G, const HeavyEntry* H, u32 hn, u64* vis, u64* Fnext,
                                     u32* cg, u32* cs, u32 foot, WarpQueue& nq, WarpQueue& lq, u32 wid, u32 nw,
-                                    LocalStats& st) {
+                                    const CtaTab& T, LocalStats& st) {
     const u32 lane = threadIdx.x & 31;
     u32 base = 0;   // pieces in the batches before this one
     for (u32 h0 = 0; h0 < hn; h0 += 32) {
@@ -585,21 +674,21 @@ __device__ __noinline__ void expand_heavy(const GraphDev& G, const HeavyEntry* H
             for (int hh = 0; hh < 2; ++hh) {
                 const u32 a = off + 32 * hh + lane;
                 v[hh] = a < o_deg;
-                q[hh].nb = 0; q[hh].fl = 0; q[hh].degp = 0; q[hh].g = o_g; q[hh].word = 0;
+                q[hh].nb = 0; q[hh].fl = 0; q[hh].degp = 0; q[hh].g = o_g; q[hh].word = 0; q[hh].lw = 0;
                 if (v[hh]) push_load<W>(G.col, o_beg + a, o_F, o_g, q[hh]);
             }
             nq.reserve(64);
             lq.reserve(64);
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh)
-                if (v[hh]) push_check<W, R>(G.rp, vis, q[hh]);
+                if (v[hh]) push_check<W, R>(G.rp, vis, q[hh], T);
             u64 old[2];
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh) push_vis<R>(vis, q[hh], old[hh]);
 #pragma unroll
-            for (int hh = 0; hh < 2; ++hh) push_next<R>(Fnext, q[hh], old[hh], foot, st);
+            for (int hh = 0; hh < 2; ++hh) push_next<R>(Fnext, q[hh], old[hh], foot, st, T);
 #pragma unroll
-            for (int hh = 0; hh < 2; ++hh) push_finish(q[hh], cg, cs, nq, lq);
+            for (int hh = 0; hh < 2; ++hh) push_finish<R>(q[hh], cg, cs, nq, lq, T);
         }
         base += total;
     }
@@ -1067,6 +1156,7 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
     __shared__ u32 s_cg[L], s_cs[L];
     __shared__ u32 s_alive32[2 * W];
     __shared__ u32 s_ln[2], s_logn, s_base, s_nc, s_stop, s_chunk;
+    __shared__ u32 s_ins, s_full;   // the wave's table entries; set once past the table's limit
     __shared__ u64 s_twave;
     __shared__ unsigned long long s_arcs[2];   // out-arcs of each frontier list's words
     __shared__ HeavyEntry s_heavy[kHeavyCapCta];
@@ -1084,7 +1174,10 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
     const u32 tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const GraphDev& G = p.g;
     const u32 n_end = p.n_end_dev ? vload(p.n_end_dev) : p.n_end;
-    SlotPtrs S = slot_ptrs<REC>(p.slot_base + (size_t)blockIdx.x * p.slot_stride, G.n, W);
+    // dense tables hold n entries whatever cta_entries says
+    const u32 entries = p.tab_shift ? p.cta_entries : G.n;
+    SlotPtrs S = slot_ptrs<REC>(p.slot_base + (size_t)blockIdx.x * p.slot_stride, entries, W);
+    const CtaTab T{p.tab_shift, entries - 1, p.tab_limit, &s_ins, &s_full};
     LocalStats st;
     if (tid == 0) {
         s_thr.valid = 0; s_thr.N = 0; s_thr.F = 1; s_thr.id = 0;
@@ -1102,6 +1195,8 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
                 s_base = atomicAdd(p.head, (u32)L);
                 s_stop = (s_base >= n_end) || (vload(p.err) != 0);
             }
+            s_ins = 0;
+            s_full = 0;
         }
         __syncthreads();
         if (s_stop) break;
@@ -1189,22 +1284,48 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
                 WarpQueue lq{&s_stage[(2 * wid + 1) * QCAP], S.clog, &s_logn, QCAP, 0};
                 if (d == 0)
                     expand_sources<W, REC>(G, s_src, s_alive32, s_pre, s_beg, L, S.vis, Fnext, s_cg, s_cs,
-                                           p.footnote, nq, lq, wid, NWARP, tid, THREADS, st);
+                                           p.footnote, nq, lq, wid, NWARP, tid, THREADS, T, st);
                 else
                     expand_entries<W, REC>(G, S.list[cur], s_ln[cur], S.F[cur], s_alive32, S.vis, Fnext, s_cg,
-                                           s_cs, p.footnote, nq, lq, &s_chunk, wid, NWARP, Hc, st);
+                                           s_cs, p.footnote, nq, lq, &s_chunk, wid, NWARP, Hc, T, st);
                 if (d > 0) {
                     __syncthreads();   // the heavy list is complete
                     const u32 hn = s_hn < kHeavyCapCta ? s_hn : kHeavyCapCta;
                     if (hn)
                         expand_heavy<W, REC>(G, s_heavy, hn, S.vis, Fnext, s_cg, s_cs, p.footnote, nq, lq, wid,
-                                             NWARP, st);
+                                             NWARP, T, st);
                 }
                 nq.flush();
                 lq.flush();
                 flush_fwarcs(st, &s_arcs[cur ^ 1]);
             }
             __syncthreads();
+            if (s_full) {
+                // the table passed its limit during this level, so some arcs
+                // were dropped and the level's counts are incomplete: the
+                // lanes live in it go to the grid-wide pass (where no such
+                // pass follows, the run fails rather than use the counts)
+                if (tid < L) {
+                    const bool a = (s_alive32[tid >> 5] >> lane) & 1u;
+                    const u32 m = __ballot_sync(0xffffffffu, a);
+                    if (p.defer_src) {
+                        u32 at = 0;
+                        if (lane == 0 && m) {
+                            at = atomicAdd(p.defer_n, (u32)__popc(m));
+                            bstat_add(s_bst, ST_DEFERRED, __popc(m));
+                        }
+                        at = __shfl_sync(0xffffffffu, at, 0);
+                        if (a) p.defer_src[at + __popc(m & lanemask_lt())] = s_src[tid];
+                    }
+                    s_cg[tid] = 0;
+                    s_cs[tid] = 0;
+                }
+                if (tid == 0) {
+                    s_hn = 0;
+                    if (!p.defer_src) atomicOr(p.err, DEV_ERR_TABLE_FULL);
+                }
+                break;
+            }
             if (tid < L) {   // level d+1 is known: gamma_{d+1} and its degree sum
                 bool a = (s_alive32[tid >> 5] >> lane) & 1u;
                 if (a) {
@@ -1238,15 +1359,308 @@ __global__ void __launch_bounds__(THREADS, (1024 / THREADS) > 0 ? (1024 / THREAD
             bstat_add(s_bst, ST_LEVELS, d);
             bstat_max(s_bst, ST_MAXLEVEL, d);
         }
-        // the wave's footprint: every word whose vis became non-zero
+        // the wave's footprint: every word whose vis became non-zero (dense),
+        // or every table entry it made, with its W words (hashed)
         const u32 nlog = s_logn;
-        for (u32 i = tid; i < nlog; i += THREADS) clear_word<REC>(S, S.clog[i]);
+        if (p.tab_shift) {
+            for (u32 i = tid; i < nlog * W; i += THREADS) clear_word<REC>(S, __ldcg(&S.clog[i / W]) + i % W);
+        } else {
+            for (u32 i = tid; i < nlog; i += THREADS) clear_word<REC>(S, S.clog[i]);
+        }
         if (tid == 0) {
-            bstat_add(s_bst, ST_CLEARED, nlog);
+            bstat_add(s_bst, ST_CLEARED, p.tab_shift ? nlog * W : nlog);
             trace_record(p, TR_CTA_WAVE, blockIdx.x, d, nlog, s_twave, global_ns());
         }
         __syncthreads();
         if (tid == 0) { s_logn = 0; s_ln[0] = 0; s_ln[1] = 0; s_arcs[0] = 0; s_arcs[1] = 0; }
+    }
+    __syncthreads();
+    flush_stats(st, s_bst, p.stats);
+}
+
+// ------------------------------------------------------ one source per CTA
+// BFSCut of one source at a time per CTA (Algorithm 2 as written: one BFS,
+// the same stopping rule on the same per-level state as the wave kernels),
+// on a visited bitmap of one bit per vertex and two queues.  For graphs
+// whose sources' searches share almost no frontier: on a lattice the
+// sources of a wave are consecutive vertices, and two BFS spheres cross only
+// at points, so a bit lane per source fills one bit of each 64-bit word it
+// touches and every arc costs a 32-byte record; here an arc costs a bit of a
+// bitmap that stays in L2.
+//
+// The kernel is bound by the latency of each level's chain of dependent
+// loads, so the chain is kept short.  A queue entry is the frontier
+// vertex's arc range (first arc, degree), loaded with the vertex's degree by
+// the thread that discovered it; each warp takes 32 entries at a time (its
+// first chunk fixed, the rest from a counter), lays their arcs end to end
+// and walks them 128 per step, four independent arcs per thread: the
+// target's id, then its bitmap word and its own arc range (read for every
+// arc, so that a discovery needs no further load), then atomicOr where the
+// bit was clear; the thread whose atomicOr set the bit has discovered the
+// vertex, appends its arc range to the next queue and counts it (gamma_{d+1})
+// with its degree (for gamma~_{d+2}).  The threshold for the next level is
+// read by one thread while the others expand; the stopping rule for level
+// d+1 is evaluated with the level's update, so a level costs two block
+// barriers.  Bitmap words that were zero are logged and cleared when the
+// source ends.  A frontier longer than the queue gives the source up to the
+// grid-wide pass (deferral), which runs it again from the start.
+struct SQueue {   // WarpQueue of 8-byte entries with a capacity: entries past it are dropped and flagged
+    uint2* sbuf;
+    uint2* dst;
+    u32* counter;
+    u32 cap;
+    u32 n;
+    u32 lim;
+    volatile u32* ovf;
+    __device__ __forceinline__ void push(bool want, uint2 item) {
+        const u32 m = __ballot_sync(0xffffffffu, want);
+        if (want) sbuf[n + __popc(m & lanemask_lt())] = item;
+        n += __popc(m);
+    }
+    __device__ __forceinline__ void flush() {
+        if (n == 0) return;
+        __syncwarp();
+        u32 base = 0;
+        if ((threadIdx.x & 31) == 0) base = atomicAdd(counter, n);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (u32 i = threadIdx.x & 31; i < n; i += 32)
+            if (base + i < lim) dst[base + i] = sbuf[i];
+        if ((threadIdx.x & 31) == 0 && base + n > lim) *ovf = 1;
+        __syncwarp();
+        n = 0;
+    }
+    __device__ __forceinline__ void reserve(u32 need) {
+        if (n + need > cap) flush();
+    }
+};
+
+constexpr int kSparseArcs = 4;   // independent arcs per thread and step
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k_sparse(WaveParams p) {
+    constexpr int NWARP = THREADS / 32;
+    constexpr u32 QCAP = 1024 / NWARP;   // staged entries per warp: next queue (8 B each) and log (4 B)
+    static_assert(QCAP >= 32, "a warp stages up to 32 entries per push");
+    constexpr u32 SCR = NWARP * QCAP * 3 > 4608 ? NWARP * QCAP * 3 : 4608;
+    __shared__ __align__(16) u32 s_stage[SCR];   // staging, and flush_completions' scratch
+    __shared__ u32 s_qn[2], s_logn, s_base, s_stop, s_cut, s_gam, s_dsum, s_ovf, s_chunk, s_nc;
+    __shared__ u32 s_src, s_nd, s_gt, s_xlo, s_xhi;
+    __shared__ u64 s_f;
+    __shared__ u32 s_cid[1], s_cr[1];
+    __shared__ u64 s_cf[1];
+    __shared__ int s_go;
+    __shared__ ThrCache s_thr, s_thr_next;
+    __shared__ BlockStats s_bst;
+
+    const u32 tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const GraphDev& G = p.g;
+    const u32 n_end = p.n_end_dev ? vload(p.n_end_dev) : p.n_end;
+    char* slot = p.slot_base + (size_t)blockIdx.x * p.slot_stride;
+    u32* const vis = (u32*)slot;
+    u32* const wlog = (u32*)(slot + sparse_bitmap_bytes(G.n));
+    uint2* const q0 = (uint2*)(slot + 2 * sparse_bitmap_bytes(G.n));
+    uint2* const q1 = q0 + al256((size_t)p.sparse_qcap * sizeof(uint2)) / sizeof(uint2);
+    uint2* const stq = (uint2*)&s_stage[wid * QCAP * 3];   // QCAP entries of 8 bytes
+    u32* const stl = &s_stage[wid * QCAP * 3 + 2 * QCAP];  // QCAP entries of 4 bytes
+    LocalStats st;
+    if (tid == 0) {
+        s_thr.valid = 0; s_thr.N = 0; s_thr.F = 1; s_thr.id = 0;
+        s_thr_next = s_thr;
+        s_qn[0] = 0; s_qn[1] = 0; s_logn = 0; s_nc = 0;
+    }
+    bstat_init(s_bst);
+    __syncthreads();
+
+    for (;;) {
+        if (tid == 0) {
+            s_base = atomicAdd(p.head, 1u);
+            s_stop = (s_base >= n_end) || (vload(p.err) != 0);
+        }
+        __syncthreads();
+        if (s_stop) break;
+        if (tid == 0) {
+            const u32 v = __ldg(&p.sources[s_base]);
+            const u32 beg = __ldg(&G.rp[v]);
+            const u32 deg = __ldg(&G.rp[v + 1]) - beg;
+            s_src = v; s_nd = 1; s_f = 0; s_gt = deg;
+            s_xlo = __ldg(&G.xlo[v]); s_xhi = __ldg(&G.xhi[v]);
+            s_ovf = 0; s_cut = 0; s_gam = 0; s_dsum = 0; s_chunk = 0;
+            bstat_add(s_bst, ST_WAVES, 1);
+            if (!p.exhaustive) read_thresholds(p.topk, s_thr);
+            if (deg == 0) {   // R(v) = {v}: r = 1, f = 0
+                s_cid[0] = v; s_cf[0] = 0; s_cr[0] = 1; s_nc = 1;
+                bstat_add(s_bst, ST_COMPLETED, 1);
+                if (p.trace_lanes) { lane_level(p, v, 0, 0, 1, 0); lane_end(p, v, 0, 0, 1, false); }
+            } else {
+                vis[v >> 5] = 1u << (v & 31);   // the bitmap is clean: no other bit of this word is set
+                wlog[0] = v >> 5;
+                s_logn = 1;
+                q0[0] = make_uint2(beg, deg);
+                s_qn[0] = 1;
+                // stopping rule at level 0
+                if (p.trace_lanes) lane_level(p, v, 0, 0, 1, deg);
+                if (!p.exhaustive && !p.nocut && bfscut_stops(0, deg, 0, 1, s_xlo, s_xhi, v, s_thr)) {
+                    s_cut = 1;
+                    bstat_add(s_bst, ST_CUT, 1);
+                    if (p.trace_lanes) lane_end(p, v, 0, 0, 1, true);
+                }
+            }
+        }
+        __syncthreads();
+        u32 d = 0, cur = 0;
+        while (!s_nc && !s_cut) {
+            {
+                if (wid == NWARP - 1 && lane == 0 && !p.exhaustive) read_thresholds(p.topk, s_thr_next);
+                const u32 cnt = s_qn[cur];
+                const uint2* qc = cur ? q1 : q0;
+                SQueue nq{stq, cur ? q0 : q1, &s_qn[cur ^ 1], QCAP, 0, p.sparse_qcap, &s_ovf};
+                WarpQueue lq{stl, wlog, &s_logn, QCAP, 0};
+                u32 gam = 0, dsum = 0;
+                bool first = true;
+                for (;;) {
+                    u32 b = wid * 32;
+                    if (!first) {
+                        u32 c = 0;
+                        if (lane == 0) c = atomicAdd(&s_chunk, 32u);
+                        b = NWARP * 32 + __shfl_sync(0xffffffffu, c, 0);
+                    }
+                    first = false;
+                    if (b >= cnt) break;
+                    const u32 e = b + lane;
+                    uint2 ent = make_uint2(0, 0);
+                    if (e < cnt) {
+                        ent = __ldcg(&qc[e]);
+                        st.mvis += ent.y;
+                        st.arcwords += ent.y;
+                        st.entries++;
+                    }
+                    const u32 beg = ent.x, deg = ent.y;
+                    u32 incl = deg;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const u32 t = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= (u32)o) incl += t;
+                    }
+                    const u32 total = __shfl_sync(0xffffffffu, incl, 31);
+                    const u32 excl = incl - deg;
+                    for (u32 t0 = 0; t0 < total; t0 += 32 * kSparseArcs) {
+                        u32 x[kSparseArcs], w[kSparseArcs], r0[kSparseArcs], r1[kSparseArcs];
+                        bool v[kSparseArcs];
+#pragma unroll
+                        for (int j = 0; j < kSparseArcs; ++j) {
+                            const u32 idx = t0 + 32 * j + lane;
+                            int owner = 0;
+#pragma unroll
+                            for (int step = 16; step; step >>= 1) {
+                                const u32 ex = __shfl_sync(0xffffffffu, excl, owner + step);
+                                if (ex <= idx) owner += step;
+                            }
+                            const u32 o_beg = __shfl_sync(0xffffffffu, beg, owner);
+                            const u32 o_excl = __shfl_sync(0xffffffffu, excl, owner);
+                            v[j] = idx < total;
+                            x[j] = v[j] ? __ldg(&G.col[o_beg + idx - o_excl]) : 0u;
+                        }
+#pragma unroll
+                        for (int j = 0; j < kSparseArcs; ++j) {
+                            w[j] = v[j] ? __ldcg(&vis[x[j] >> 5]) : ~0u;
+                            r0[j] = v[j] ? __ldg(&G.rp[x[j]]) : 0u;
+                            r1[j] = v[j] ? __ldg(&G.rp[x[j] + 1]) : 0u;
+                        }
+                        bool found[kSparseArcs], fresh[kSparseArcs];
+#pragma unroll
+                        for (int j = 0; j < kSparseArcs; ++j) {
+                            const u32 bit = 1u << (x[j] & 31);
+                            found[j] = false;
+                            fresh[j] = false;
+                            if (v[j] && !(w[j] & bit)) {
+                                const u32 old = atomicOr(&vis[x[j] >> 5], bit);
+                                found[j] = !(old & bit);
+                                fresh[j] = old == 0;
+                            }
+                        }
+#pragma unroll
+                        for (int j = 0; j < kSparseArcs; ++j) {
+                            if (found[j]) {
+                                gam++;
+                                dsum += r1[j] - r0[j] - p.footnote;
+                            }
+                            nq.reserve(32);
+                            lq.reserve(32);
+                            nq.push(found[j], make_uint2(r0[j], r1[j] - r0[j]));
+                            lq.push(fresh[j], x[j] >> 5);
+                        }
+                    }
+                }
+                nq.flush();
+                lq.flush();
+                st.disc += gam;
+                st.discwords += gam;
+                for (int o = 16; o; o >>= 1) {
+                    gam += __shfl_xor_sync(0xffffffffu, gam, o);
+                    dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+                }
+                if (lane == 0 && gam) {
+                    atomicAdd(&s_gam, gam);
+                    atomicAdd(&s_dsum, dsum);
+                }
+            }
+            __syncthreads();
+            if (s_ovf) {
+                // the next frontier did not fit its queue: the source goes to
+                // the grid-wide pass (where none follows, the run fails
+                // rather than use the level's counts)
+                if (tid == 0) {
+                    if (p.defer_src) {
+                        p.defer_src[atomicAdd(p.defer_n, 1u)] = s_src;
+                        bstat_add(s_bst, ST_DEFERRED, 1);
+                    } else {
+                        atomicOr(p.err, DEV_ERR_TABLE_FULL);
+                    }
+                }
+                break;
+            }
+            if (tid == 0) {   // level d+1 is known: gamma_{d+1} and its degree sum; its stopping rule
+                const u32 gam = s_gam;
+                if (gam == 0) {
+                    s_cid[0] = s_src; s_cf[0] = s_f; s_cr[0] = s_nd; s_nc = 1;
+                    bstat_add(s_bst, ST_COMPLETED, 1);
+                    if (p.trace_lanes) lane_end(p, s_src, d, s_f, s_nd, false);
+                } else {
+                    s_nd += gam;
+                    s_f += (u64)(d + 1) * gam;
+                    s_gt = s_dsum;
+                    if (!p.exhaustive) s_thr = s_thr_next;
+                    if (p.trace_lanes) lane_level(p, s_src, d + 1, s_f, s_nd, s_gt);
+                    if (!p.exhaustive && !p.nocut &&
+                        bfscut_stops(s_f, s_gt, d + 1, s_nd, s_xlo, s_xhi, s_src, s_thr)) {
+                        s_cut = 1;
+                        bstat_add(s_bst, ST_CUT, 1);
+                        if (p.trace_lanes) lane_end(p, s_src, d + 1, s_f, s_nd, true);
+                    }
+                }
+                s_qn[cur] = 0;
+                s_gam = 0;
+                s_dsum = 0;
+                s_chunk = 0;
+            }
+            __syncthreads();
+            cur ^= 1;
+            ++d;
+        }
+        if (tid == 0) {
+            bstat_add(s_bst, ST_LEVELS, d);
+            bstat_max(s_bst, ST_MAXLEVEL, d);
+        }
+        // the source's footprint: every bitmap word it made non-zero
+        const u32 nlog = s_logn;
+        for (u32 i = tid; i < nlog; i += THREADS) vis[__ldcg(&wlog[i])] = 0;
+        flush_completions(p, s_cid, s_cf, s_cr, s_nc, s_thr, THREADS, s_stage, &s_go);
+        __syncthreads();
+        if (tid == 0) {
+            bstat_add(s_bst, ST_CLEARED, nlog);
+            s_logn = 0; s_qn[0] = 0; s_qn[1] = 0; s_nc = 0;
+        }
+        __syncthreads();
     }
     __syncthreads();
     flush_stats(st, s_bst, p.stats);
@@ -1325,6 +1739,12 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
     const u32 n_end = p.n_end_dev ? vload(p.n_end_dev) : p.n_end;
     const HeavyList Hg{p.gheavy, p.gheavy_n, p.gheavy_cap};
     if (tid == 0) { s_nc = 0; s_thr.valid = 0; s_thr.N = 0; s_thr.F = 1; s_thr.id = 0; }
+    // every block cuts with the leader's snapshot of the threshold, taken
+    // before a barrier and read after it
+    if (leader && tid == 0) {
+        if (!p.exhaustive) read_thresholds(p.topk, s_thr);
+        store_snapshot(p.snap, s_thr);
+    }
     bstat_init(s_bst);
     bool ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err);
 
@@ -1360,6 +1780,10 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
         if (leader) flush_completions(p, s_cid, s_cf, s_cr, s_nc, s_thr, THREADS, s_stage, &s_go);
         __syncthreads();
         if (tid == 0) s_nc = 0;
+        if (leader && tid == 0 && !p.exhaustive) {
+            read_thresholds(p.topk, s_thr);
+            store_snapshot(p.snap, s_thr);
+        }
         if (!(ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err))) break;
 
         u32 d = 0, cur = 0;
@@ -1368,7 +1792,7 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
         u32 level_cnt = 0;   // entries of the level's frontier list, read before it can be reset
         for (;;) {
             if (tid == 0) {
-                if (!p.exhaustive) read_thresholds(p.topk, s_thr);
+                if (!p.exhaustive) load_snapshot(p.snap, s_thr);
                 s_minnd = 0xffffffffu;
             }
             __syncthreads();
@@ -1410,7 +1834,7 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
                 if (d == 0) {
                     expand_sources<W, 1>(G, s_src, s_alive32, s_pre, s_beg, L, S.vis, S.F[cur ^ 1], s_cg, s_cs,
                                          p.footnote, nq, lq, pw, gnw, blockIdx.x * THREADS + tid,
-                                         gridDim.x * THREADS, st);
+                                         gridDim.x * THREADS, kDenseTab, st);
                 } else {
                     const u32 cnt = vload(&p.glist_n[cur]);
                     level_cnt = cnt;
@@ -1421,7 +1845,7 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
                                       &p.gchunk[cur], pw, gnw, st);
                     } else {
                         expand_entries<W, 1>(G, S.list[cur], cnt, S.F[cur], s_alive32, S.vis, S.F[cur ^ 1], s_cg,
-                                             s_cs, p.footnote, nq, lq, &p.gchunk[cur], pw, gnw, Hg, st);
+                                             s_cs, p.footnote, nq, lq, &p.gchunk[cur], pw, gnw, Hg, kDenseTab, st);
                     }
                 }
                 nq.flush();
@@ -1445,7 +1869,7 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
                         WarpQueue nq{&s_stage[(2 * wid) * QCAP], S.list[cur ^ 1], &p.glist_n[cur ^ 1], QCAP, 0};
                         WarpQueue lq{&s_stage[(2 * wid + 1) * QCAP], S.clog, p.glog_n, QCAP, 0};
                         expand_heavy<W, 1>(G, p.gheavy, hn, S.vis, S.F[cur ^ 1], s_cg, s_cs, p.footnote, nq, lq,
-                                           pw, gnw, st);
+                                           pw, gnw, kDenseTab, st);
                         nq.flush();
                         lq.flush();
                         flush_fwarcs(st, &p.garc[cur ^ 1]);
@@ -1520,6 +1944,10 @@ __global__ void __launch_bounds__(THREADS, BCM_GRID_MIN_BLOCKS) k_wave_grid(Wave
             if (leader) flush_completions(p, s_cid, s_cf, s_cr, s_nc, s_thr, THREADS, s_stage, &s_go);
             __syncthreads();
             if (tid == 0) s_nc = 0;
+            if (leader && tid == 0 && !p.exhaustive) {
+                read_thresholds(p.topk, s_thr);
+                store_snapshot(p.snap, s_thr);
+            }
             if (!(ok = grid_sync(p.bar, gridDim.x, p.barrier_limit_ns, p.err))) break;
             cur ^= 1;
             ++d;
@@ -1580,7 +2008,7 @@ __global__ void __launch_bounds__(THREADS) k_plain(WaveParams p, u32 it, u32* st
     if (tid == 0) {
         s_cg = 0; s_cs = 0;
         s_thr.valid = 0; s_thr.N = 0; s_thr.F = 1; s_thr.id = 0;
-        read_thresholds(p.topk, s_thr);   // fixed for this launch: only its end inserts
+        load_snapshot(p.snap, s_thr);   // fixed for this launch: the previous launch's end took it
     }
     bstat_init(s_bst);
     __syncthreads();
@@ -1693,6 +2121,10 @@ __global__ void __launch_bounds__(THREADS) k_plain(WaveParams p, u32 it, u32* st
                 lock_release(p.topk.lock);
             }
         }
+        // the next launch's threshold, the same for all its blocks
+        ThrCache c = s_thr;
+        read_thresholds(p.topk, c);
+        store_snapshot(p.snap, c);
     }
     (void)s_go;
     __syncthreads();
@@ -1752,6 +2184,32 @@ int max_coop_blocks(int kind, int W, int threads) {
     else f = (const void*)k_wave_grid<4, 512>;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, f, threads, 0) != cudaSuccess) return 0;
     return per * sms;
+}
+
+template <int T>
+static int launch_sparse_t(const WaveParams& p, int blocks, cudaStream_t s) {
+    k_sparse<T><<<blocks, T, 0, s>>>(p);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_sparse(const WaveParams& p, int blocks, int threads, cudaStream_t s) {
+    if (threads == 128) return launch_sparse_t<128>(p, blocks, s);
+    if (threads == 256) return launch_sparse_t<256>(p, blocks, s);
+    if (threads == 512) return launch_sparse_t<512>(p, blocks, s);
+    if (threads == 1024) return launch_sparse_t<1024>(p, blocks, s);
+    return -2;
+}
+
+int sparse_blocks_per_sm(int threads) {
+    const void* f = threads == 128 ? (const void*)k_sparse<128>
+                  : threads == 256 ? (const void*)k_sparse<256>
+                  : threads == 512 ? (const void*)k_sparse<512>
+                  : threads == 1024 ? (const void*)k_sparse<1024> : nullptr;
+    if (!f) return 0;
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, f, threads, 0) != cudaSuccess) return 0;
+    return per;
 }
 
 int cta_blocks_per_sm(int W, int threads) {

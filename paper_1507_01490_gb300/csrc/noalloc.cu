@@ -41,8 +41,6 @@ struct NoAllocHeader {
     unsigned long long stats[ST_COUNT];
 };
 
-constexpr size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
-
 // Layout: header (256 bytes) | offsets u32[n+1] | order u32[n] | CTA slots.
 constexpr size_t kHeaderBytes = 256;
 static_assert(sizeof(NoAllocHeader) <= kHeaderBytes, "the header must fit before the offsets");
@@ -169,6 +167,7 @@ extern "C" bcm_status bcm_farness_all_noalloc(const uint64_t* row_ptr, const uin
     w.out_reach = reach;
     w.slot_base = slots;
     w.slot_stride = sb;
+    w.cta_entries = n;        // dense per-CTA slots (no hashed table: exhaustive runs never defer)
     w.stats = hdr->stats;
     w.err = &hdr->err;
     w.lock_limit_ns = 20ull * 1000 * 1000 * 1000;

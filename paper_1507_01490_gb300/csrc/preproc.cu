@@ -517,7 +517,7 @@ size_t degree_order_scratch_bytes(uint32_t n) {
 
 // order[] = vertices by (degree desc, id asc); degree = CSR row length.
 int launch_degree_order(const uint32_t* rp, uint32_t n, uint32_t* order, void* scratch,
-                        size_t scratch_bytes, cudaStream_t s) {
+                        size_t scratch_bytes, cudaStream_t s, uint32_t* max_degree) {
     if (n == 0) return 0;
     if (scratch_bytes < degree_order_scratch_bytes(n)) return -1;
     size_t a = ((size_t)n * sizeof(uint32_t) + 255) & ~(size_t)255;
@@ -534,6 +534,7 @@ int launch_degree_order(const uint32_t* rp, uint32_t n, uint32_t* order, void* s
     uint32_t maxdeg = 0;
     if (cudaMemcpyAsync(&maxdeg, d_max, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return -1;
     if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+    if (max_degree) *max_degree = maxdeg;
     int bits = 0;
     while (bits < 32 && (maxdeg >> bits)) ++bits;
     bool in_tmp = false;

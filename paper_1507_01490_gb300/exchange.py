@@ -20,6 +20,7 @@ stay below 2^62, so they travel as int64.
 """
 from __future__ import annotations
 
+import threading
 import time
 
 NO_KEY = (0, 0, 1, 0)
@@ -46,15 +47,47 @@ def best_key(keys):
     return best
 
 
+class ThreadGather:
+    """All-gather among `world` threads of one process: shards of one graph
+    run from threads that share one GPU context (and its streams), as the
+    serving loop runs several graphs.  for_rank(r) is rank r's gather."""
+
+    def __init__(self, world: int, timeout_s: float = 60.0):
+        self.rows = [None] * world
+        self.bar = threading.Barrier(world, timeout=timeout_s)
+
+    def for_rank(self, rank: int):
+        def gather(row):
+            self.rows[rank] = tuple(int(x) for x in row)
+            self.bar.wait()
+            out = list(self.rows)
+            self.bar.wait()           # every rank has read the round's rows
+            return out
+        return gather
+
+
 class ThresholdExchange:
     """Rounds of key exchange among the ranks of `group` (a gloo process
-    group; None = the default group).  period_s: pause between rounds."""
+    group; None = the default group), or through `gather` (row -> every
+    rank's row, e.g. ThreadGather.for_rank).  period_s: pause between rounds."""
 
-    def __init__(self, group=None, period_s: float = 2e-4):
+    def __init__(self, group=None, period_s: float = 2e-4, gather=None):
         self.group = group
         self.period_s = period_s
+        self.gather = gather
         self.rounds = 0
         self.offers = 0
+
+    def _all_gather(self, row):
+        if self.gather is not None:
+            return self.gather(row)
+        import torch
+        import torch.distributed as dist
+        world = dist.get_world_size(self.group)
+        t = torch.tensor(row, dtype=torch.int64)
+        out = [torch.zeros(len(row), dtype=torch.int64) for _ in range(world)]
+        dist.all_gather(out, t, group=self.group)
+        return [tuple(int(x) for x in o.tolist()) for o in out]
 
     def run(self, read_key, offer_key, poll):
         """Exchange until every rank's run has finished.
@@ -64,9 +97,6 @@ class ThresholdExchange:
         read_key()    -> this rank's current k-th key (valid, N, F, id);
         offer_key(k)  -> gives key k to this rank's run (only while it runs).
         Returns the best key seen."""
-        import torch
-        import torch.distributed as dist
-        world = dist.get_world_size(self.group)
         done = False
         offered = NO_KEY
         best = NO_KEY
@@ -74,11 +104,9 @@ class ThresholdExchange:
             if not done:
                 done = bool(poll())
             mine = tuple(int(x) for x in read_key())
-            t = torch.tensor([int(done), *mine], dtype=torch.int64)
-            out = [torch.zeros(5, dtype=torch.int64) for _ in range(world)]
-            dist.all_gather(out, t, group=self.group)
+            out = self._all_gather([int(done), *mine])
             self.rounds += 1
-            keys = [tuple(int(x) for x in o[1:].tolist()) for o in out]
+            keys = [tuple(o[1:]) for o in out]
             best = best_key(keys + [best])
             if not done and key_before(best, mine) and key_before(best, offered):
                 offer_key(best)

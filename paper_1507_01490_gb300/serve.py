@@ -289,7 +289,8 @@ class GpuBackend(Backend):
 
     def options(self, gid):
         """The run options of graph gid: the backend's, with the per-CTA
-        block count lowered (largest that fits) when the workspace cap asks."""
+        block count set to the largest whose workspace fits the cap when
+        there is one (the library's default, every resident CTA, may not)."""
         if gid not in self._gopts:
             o = self.opts
             h = self.handles[gid].h
@@ -366,4 +367,5 @@ class GpuBackend(Backend):
 
 def _opts_kw(o):
     return dict(lanes=o.lanes, flags=o.flags, blocks=o.blocks, threads=o.threads, wait_limit_ns=o.wait_limit_ns,
-                grid_lanes=o.grid_lanes, heavy_words=o.heavy_words, pull_div=o.pull_div, defer_words=o.defer_words)
+                grid_lanes=o.grid_lanes, heavy_words=o.heavy_words, pull_div=o.pull_div, defer_words=o.defer_words,
+                shard_index=o.shard_index, shard_count=o.shard_count, cta_table=o.cta_table)

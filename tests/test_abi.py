@@ -39,15 +39,15 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_layouts_match_header(lib, tmp_path):
     src = tmp_path / "sz.c"
     src.write_text('#include "bcm.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(bcm_options), sizeof(bcm_stats),'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(bcm_options), sizeof(bcm_stats),'
                    ' offsetof(bcm_options, wait_limit_ns), offsetof(bcm_stats, kernel_ms), sizeof(bcm_key),'
-                   ' offsetof(bcm_key, id));return 0;}\n')
+                   ' offsetof(bcm_key, id), offsetof(bcm_options, cta_table));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     assert got == [ctypes.sizeof(lib.bcm_options), ctypes.sizeof(lib.bcm_stats),
                    lib.bcm_options.wait_limit_ns.offset, lib.bcm_stats.kernel_ms.offset,
-                   ctypes.sizeof(lib.bcm_key), lib.bcm_key.id.offset]
+                   ctypes.sizeof(lib.bcm_key), lib.bcm_key.id.offset, lib.bcm_options.cta_table.offset]
 
 
 def test_host_argument_checks(lib):

@@ -19,6 +19,9 @@ class FakeHandle:
         for name, v in cfg.items():
             vals = autotune.SPACE[name]
             t += abs(vals.index(v) - vals.index(self.best[name])) * 0.3
+        if autotune.PER_CTA[self.best.get("per_cta", "auto")] != (flags & (autotune.PER_CTA["sparse"] |
+                                                                            autotune.PER_CTA["bitlanes"])):
+            t += 0.5
         ids = np.arange(k, dtype=np.uint32)
         if self.change and all(cfg.get(a) == b for a, b in self.change.items()):
             ids = ids[::-1].copy()
@@ -53,9 +56,22 @@ def test_cache_roundtrip(tmp_path, gen):
     h = FakeHandle(target)
     path = str(tmp_path / "sub" / "tune.json")
     cfg, spent, hit = autotune.tuned_options(h, g, k=3, cache_path=path, reps=1)
-    assert cfg == target and not hit
+    # a path's largest degree is 2: the per-CTA kernel is tuned too
+    assert cfg == dict(target, per_cta="auto") and not hit
     calls = h.calls
     cfg2, spent2, hit2 = autotune.tuned_options(h, g, k=3, cache_path=path, reps=1)
-    assert cfg2 == target and hit2 and spent2 == 0.0 and h.calls == calls
+    assert cfg2 == cfg and hit2 and spent2 == 0.0 and h.calls == calls
     cfg3, _, hit3 = autotune.tuned_options(h, g, k=4, cache_path=path, reps=1)   # another k: tuned again
     assert not hit3
+
+
+@pytest.mark.parametrize("kernel", ["sparse", "bitlanes"])
+def test_per_cta_kernel_is_searched(kernel):
+    """With kernels=True the per-CTA kernel is one more coordinate, passed as
+    its flag; without, it is never tried."""
+    target = dict(autotune.DEFAULTS, per_cta=kernel)
+    h = FakeHandle(target)
+    cfg, ms, trials = autotune.tune(h, k=10, rounds=2, reps=1, kernels=True)
+    assert cfg == target and abs(ms - 1.0) < 1e-9
+    cfg, ms, trials = autotune.tune(FakeHandle(target), k=10, rounds=2, reps=1)
+    assert "per_cta" not in cfg and abs(ms - 1.5) < 1e-9

@@ -142,13 +142,17 @@ def test_rmat20_topk(B, gen, orc, rmat, k):
 
 def test_grid512_topk10(B, gen, orc):
     """The damaged-grid recipe at 512 x 512: BCM scans about 56% of m*n on such
-    grids (the bound only bites late on a lattice) and lanes of one wave share
-    almost no frontier words, so the work grows with n^2; this size keeps the
-    run to seconds, and the 2048 x 2048 case is the opt-in test below."""
+    grids (the bound only bites late on a lattice), so the work grows with
+    n^2; the graph's largest degree is 4, so it runs on the one-source kernel
+    by default (and, checked too, on bit-lane waves).  The 2048 x 2048 case is
+    the opt-in test below."""
     g = gen.grid_lcc(512, 512, 0.05, seed=4)
     with B.BcmGraph.from_graph(g) as h:
         ids, far, reach, st = h.topk(10)
+        assert st["sparse"] == g.n and st["grid_waves"] == 0
+        lanes = h.topk(10, flags=B.BCM_NO_SPARSE)
     assert (reach == g.n).all()
+    assert all(np.array_equal(a, b) for a, b in zip((ids, far, reach), lanes[:3]))
     _check_topk(orc, gen, g, ids, far, reach, n_top=64, n_rand=192)
 
 
@@ -158,6 +162,7 @@ def test_grid2048_topk10(B, gen, orc):
     g = gen.workload("grid2048")
     assert g.n > 4_000_000 and g.meta["deleted_edges"] == 419226
     with B.BcmGraph.from_graph(g) as h:
-        ids, far, reach, st = h.topk(10, lanes=256, wait_limit_ns=600_000_000_000)
+        ids, far, reach, st = h.topk(10)
+    assert st["sparse"] == g.n
     assert (reach == g.n).all()
     _check_topk(orc, gen, g, ids, far, reach, n_top=64, n_rand=192)

@@ -17,7 +17,8 @@ undirected graphs).  The records are checked:
   entry, so the cut was allowed by the threshold it could have read.
 
 Each kernel is checked alone: per-CTA waves, grid-wide waves by push and by
-pull, the plain one-source kernel, and the default schedule (seed wave,
+pull, the plain one-source kernel, the one-source-per-CTA kernel (with and
+without a grid-wide pass behind it), and the default schedule (seed wave,
 prefilter, per-CTA waves).
 """
 import numpy as np
@@ -78,7 +79,8 @@ def _parse(recs):
 
 MODES = [("cta", dict(flags_extra="CTA_ONLY")), ("grid_push", dict(flags_extra="GRID_ONLY|NO_PULL")),
          ("grid_pull", dict(flags_extra="GRID_ONLY|ALL_PULL")), ("plain", dict(flags_extra="PLAIN")),
-         ("default", dict(flags_extra=""))]
+         ("default", dict(flags_extra="")), ("sparse", dict(flags_extra="SPARSE")),
+         ("sparse_cta", dict(flags_extra="SPARSE|CTA_ONLY"))]
 
 
 def _flags(B, names):

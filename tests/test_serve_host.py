@@ -177,7 +177,8 @@ class _FakeBcm:
     class Opt:
         def __init__(self, **kw):
             self.__dict__.update(dict(lanes=0, flags=0, blocks=0, threads=0, wait_limit_ns=0, grid_lanes=0,
-                                      heavy_words=0, pull_div=0, defer_words=0), **kw)
+                                      heavy_words=0, pull_div=0, defer_words=0, shard_index=0, shard_count=0,
+                                      cta_table=0), **kw)
 
     def make_options(self, **kw):
         return self.Opt(**kw)

@@ -193,3 +193,54 @@ def test_two_gloo_ranks_exchange_thresholds(lib, orc, tmp_path, k):
         for gi in range(4):
             assert (tmp_path / ("x_rank%d_graph%d" % (rank, gi))).read_text() == "ok", (rank, gi)
     assert sum(int((tmp_path / ("x_rank%d_offers" % r)).read_text()) for r in range(2)) > 0
+
+
+@pytest.mark.parametrize("k", [1, 10])
+def test_thread_ranks_exchange_thresholds(lib, orc, k):
+    """The same exchange with the ranks as threads of one process
+    (ThreadGather, the way shards sharing one GPU context are driven): the
+    merged top-k is the graph's and no shard scans more arcs than alone."""
+    import threading
+
+    import oracle
+    from paper_1507_01490_gb300 import graphgen
+    from paper_1507_01490_gb300.exchange import ThreadGather, ThresholdExchange
+    orc.build()
+    world = 2
+    for g in [graphgen.ba(2000, 3, seed=1), graphgen.gnp(700, 0.006, seed=3, directed=True)]:
+        order = oracle.order(g)
+        if g.directed:
+            _, al, om, _ = oracle.alpha_omega(g)
+            bounds = (al, om)
+        else:
+            _, rr = oracle.farness_all(g)
+            bounds = (rr, rr)
+        tg = ThreadGather(world)
+        res, errs, offers = [None] * world, [], [0] * world
+
+        def rank_main(rank):
+            try:
+                src = order[B.shard_positions(g.n, rank, world)]
+                alone = oracle.ShardRun(g, k, src, bounds)
+                alone.step(len(src) + 1)
+                run = oracle.ShardRun(g, k, src, bounds)
+                ex = ThresholdExchange(period_s=0, gather=tg.for_rank(rank))
+                ex.run(run.key, run.offer, lambda: run.step(16))
+                offers[rank] = ex.offers
+                res[rank] = run.result()
+                assert res[rank][3]["m_vis"] <= alone.result()[3]["m_vis"]
+            except BaseException as e:   # reported by the main thread
+                errs.append(e)
+                tg.bar.abort()
+
+        ts = [threading.Thread(target=rank_main, args=(r,)) for r in range(world)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        assert not errs, errs
+        mi, mf, mr = B.bcm_topk_merge(np.concatenate([x[0] for x in res]), np.concatenate([x[1] for x in res]),
+                                      np.concatenate([x[2] for x in res]), k)
+        fa, ra = oracle.farness_all(g)
+        exp = oracle.topk(fa, ra, k)
+        assert np.array_equal(mi, exp) and np.array_equal(mf, fa[exp]) and np.array_equal(mr, ra[exp]), g.name
