@@ -47,6 +47,10 @@ WORKLOADS = {
                  "self-loops and repeats removed, undirected",
     "rmat20": "R-MAT scale 20, edge factor 16, (0.57,0.19,0.19,0.05), seed 3, directed",
     "grid2048": "2048x2048 grid, 5% of edges deleted (seed 4), largest component",
+    "grid1024": "1024x1024 grid, 5% of edges deleted (seed 4), largest component (profiling-size case of the "
+                "same recipe)",
+    "grid256": "256x256 grid, 5% of edges deleted (seed 4), largest component (profiling-size case of the "
+               "same recipe)",
     "ba2000": "Barabasi-Albert n=2000, m=3, seed 1",
     "chunglu256k": "Chung-Lu power-law graph, n=2^18, mean degree 10, degree exponent 2.3, seed 2 "
                    "(profiling-size case of the same recipe)",
@@ -123,10 +127,10 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def profile_traffic(kernel, kernel_src_hash):
-    """dram bytes per launch of `kernel` from the committed ncu summary, if
-    it was taken on the current kernel source; else None."""
-    p = os.path.join(ROOT, "profiles", "%s_chunglu1m.md" % kernel)
+def profile_traffic(kernel, kernel_src_hash, workload="chunglu1m"):
+    """dram bytes per launch of `kernel` on `workload` from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload))
     if not os.path.exists(p):
         return None
     traffic, src = None, None
@@ -238,7 +242,16 @@ def run_serve(args, rank, world):
     # optional cap on each run's workspace (negative: the budget's share of
     # one run in flight; 0, the default: none)
     ws_cap = int(args.serve_ws_cap_gb * (1 << 30)) if args.serve_ws_cap_gb >= 0 else budget // args.serve_inflight
-    be = serve.GpuBackend(graphs, options=B.make_options(blocks=args.serve_blocks), workspace_cap=ws_cap)
+    # per-CTA blocks and vertex-table entries of a run (0: the library's
+    # defaults; blocks < 0: the resident per-CTA blocks, two 512-thread CTAs
+    # per SM, shared among the runs in flight; table < 0: dense).  Measured on
+    # this mix (1000-2000 requests per rate): the defaults served 41.7
+    # requests/s, 19 blocks with dense tables 24.8, 38 blocks 22.5 -- a run
+    # gains more from every SM than runs gain from overlapping.
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    blocks = args.serve_blocks if args.serve_blocks >= 0 else max(1, 2 * sms // args.serve_inflight)
+    table = args.serve_table if args.serve_table >= 0 else (1 << 30)
+    be = serve.GpuBackend(graphs, options=B.make_options(blocks=blocks, cta_table=table), workspace_cap=ws_cap)
     torch.cuda.synchronize()
     t_load = time.perf_counter() - t
     csr_bytes = int(sum(g.row_ptr.nbytes // 2 + g.col.nbytes for g in graphs))
@@ -257,6 +270,8 @@ def run_serve(args, rank, world):
     cap_res = s0.run(serve.request_stream(args.serve_requests, len(graphs), float("inf"), seed=5))
     cap_span = time.perf_counter() - t
     capacity = len(cap_res) / cap_span
+    print(json.dumps({"progress": "capacity", "rps": capacity, "requests": len(cap_res)}), file=sys.stderr,
+          flush=True)
     rates = []
     last = None
     for frac in [float(x) for x in args.serve_rates.split(",") if x]:
@@ -271,6 +286,7 @@ def run_serve(args, rank, world):
                      "trims": sc.trims})
         rates.append(summ)
         last = res
+        print(json.dumps({"progress": "rate", "summary": summ}), file=sys.stderr, flush=True)
     launches = __import__("paper_1507_01490_gb300.bcm", fromlist=["x"]).bcm_launch_count() - l0
     clk = clocks.stop()
     # the same requests alone (each graph's workspace given back first)
@@ -293,7 +309,8 @@ def run_serve(args, rank, world):
                                "graph uniform, k uniform in {1,10,100}, Poisson arrivals (seed 5)"
                                % (len(graphs), args.serve_requests),
                    "max_inflight": args.serve_inflight, "hbm_budget_gb": args.serve_budget_gb,
-                   "cta_blocks": args.serve_blocks or "library default",
+                   "cta_blocks": blocks or "library default",
+                   "cta_table": "dense" if table >= (1 << 30) else (table or "library default"),
                    "workspace_cap_gb": ws_cap / 2**30 if ws_cap else None,
                    "graphs_resident_bytes": csr_bytes, "vertices": int(sum(g.n for g in graphs)),
                    "arcs": int(sum(g.m for g in graphs))},
@@ -481,7 +498,10 @@ def main():
     ap.add_argument("--serve-ws-cap-gb", type=float, default=-1.0,
                     help="per-run workspace cap (fewer per-CTA blocks on large graphs); <0: budget/inflight, 0: none")
     ap.add_argument("--serve-check", type=int, default=300, help="results compared with the request alone")
-    ap.add_argument("--serve-blocks", type=int, default=0, help="per-CTA blocks of a served run (0: library default)")
+    ap.add_argument("--serve-blocks", type=int, default=0,
+                    help="per-CTA blocks of a served run (0: library default; <0: resident blocks / inflight)")
+    ap.add_argument("--serve-table", type=int, default=0,
+                    help="per-CTA vertex table entries of a served run (0: library default; <0: dense)")
     ap.add_argument("--batch", action="store_true", help="many small graphs as one CUDA graph")
     ap.add_argument("--batch-graphs", type=int, default=128)
     ap.add_argument("--batch-max-n", type=int, default=8000)
@@ -725,7 +745,7 @@ def main():
         kname, kms, kbytes = ("k_sparse" if st["sparse"] else "k_wave_cta"), st["wave_ms"], st["wave_bytes"]
     achieved = kbytes / (kms / 1e3) / 1e9 if kms > 0 else None
     src_hash = kernel_source_hash()
-    traffic = profile_traffic(kname, src_hash)
+    traffic = profile_traffic(kname, src_hash, args.workload)
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "peak_kind": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
@@ -796,7 +816,8 @@ def main():
         "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": "%s: %s" % (args.workload, WORKLOADS[args.workload]), "n": g.n, "m_arcs": g.m,
                    "k": k, "lanes": par["lanes"] or 64, "grid_lanes": par["grid_lanes"] or 128,
-                   "pull_div": par["pull_div"] or 32, "threads": par["threads"] or 512,
+                   "pull_div": par["pull_div"] or 32, "threads": par["threads"] or (256 if st["sparse"] else 512),
+                   "per_cta_kernel": "k_sparse (one source per CTA)" if st["sparse"] else "k_wave_cta (bit lanes)",
                    "launch_parameters": ("autotuned for this graph (%.2f s, outside the timed region)" % tuning_s)
                    if tuned else "library defaults" if not (args.lanes or args.threads or args.grid_lanes)
                    else "command line",

@@ -134,8 +134,8 @@ typedef struct {
     uint32_t cta_table;       /* entries of a per-CTA wave's vertex table.  Where the per-CTA
                                  waves can defer (top-k runs, no BCM_CTA_ONLY / BCM_GRID_ONLY /
                                  BCM_NO_DEFER) and n is larger, the table is hashed with this many
-                                 entries (a power of two >= 1024; 0 = default, n/16 rounded up to a
-                                 power of two within [65536, 2^20]), and a wave
+                                 entries (a power of two >= 1024; 0 = default, n/8 rounded up to a
+                                 power of two within [65536, 2^21]), and a wave
                                  that makes more than half as many entries is deferred like a wide
                                  one; otherwise (or with a value >= n) it is dense, n entries.
                                  Results are the same either way */

@@ -387,19 +387,20 @@ struct Cfg {
     uint32_t sparse_qcap;
 };
 
-// Entries of a hashed per-CTA vertex table by default: n/16 rounded up to a
-// power of two, within [2^16, 2^20].  A per-CTA wave runs after the
+// Entries of a hashed per-CTA vertex table by default: n/8 rounded up to a
+// power of two, within [2^16, 2^21].  A per-CTA wave runs after the
 // grid-wide waves and the prefilter and reaches a small part of the graph
 // before it completes, is cut, or turns wide enough to be deferred anyway
 // (Chung-Lu n = 2^20 leaves no source to the per-CTA waves at all), so a
-// table of n/16 entries stands in for n records per CTA.  Measured on
-// Barabasi-Albert n = 2^21 (k = 10): 2^16 entries deferred 258,176 sources
-// (611 ms against 75 ms dense), 2^17 none (88 ms, 2.0 GB of slots against
-// 26.5 GB).
-constexpr uint32_t kCtaTableMin = 1u << 16, kCtaTableMax = 1u << 20;
+// table of n/8 entries stands in for n records per CTA.  A table too small
+// defers waves by the hundred thousand, measured on Barabasi-Albert graphs
+// (k = 10): n = 2^21 with 2^16 entries deferred 258,176 sources (611 ms
+// against 75 ms dense), with 2^17 none (88 ms, 2.0 GB of slots against
+// 26.5 GB); n = 2^20 with 2^16 entries took 162 ms against 33 ms dense.
+constexpr uint32_t kCtaTableMin = 1u << 16, kCtaTableMax = 1u << 21;
 uint32_t default_cta_table(uint32_t n) {
     uint32_t t = kCtaTableMin;
-    while (t < kCtaTableMax && (uint64_t)t * 16 < n) t <<= 1;
+    while (t < kCtaTableMax && (uint64_t)t * 8 < n) t <<= 1;
     return t;
 }
 
