@@ -244,10 +244,12 @@ def run_serve(args, rank, world):
     ws_cap = int(args.serve_ws_cap_gb * (1 << 30)) if args.serve_ws_cap_gb >= 0 else budget // args.serve_inflight
     # per-CTA blocks and vertex-table entries of a run (0: the library's
     # defaults; blocks < 0: the resident per-CTA blocks, two 512-thread CTAs
-    # per SM, shared among the runs in flight; table < 0: dense).  Measured on
-    # this mix (1000-2000 requests per rate): the defaults served 41.7
-    # requests/s, 19 blocks with dense tables 24.8, 38 blocks 22.5 -- a run
-    # gains more from every SM than runs gain from overlapping.
+    # per SM, shared among the runs in flight; table < 0: dense, the default
+    # here).  Measured on this mix (1000-2000 requests per rate): dense tables
+    # with the library's block count (lowered by the workspace cap on the
+    # largest graphs) served 106.8 requests/s; the library's hashed tables
+    # 41.7 (likely: the mix's denser Barabasi-Albert graphs outgrow them and
+    # defer waves); 19 blocks with dense tables 24.8, 38 blocks 22.5.
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     blocks = args.serve_blocks if args.serve_blocks >= 0 else max(1, 2 * sms // args.serve_inflight)
     table = args.serve_table if args.serve_table >= 0 else (1 << 30)
@@ -500,7 +502,7 @@ def main():
     ap.add_argument("--serve-check", type=int, default=300, help="results compared with the request alone")
     ap.add_argument("--serve-blocks", type=int, default=0,
                     help="per-CTA blocks of a served run (0: library default; <0: resident blocks / inflight)")
-    ap.add_argument("--serve-table", type=int, default=0,
+    ap.add_argument("--serve-table", type=int, default=-1,
                     help="per-CTA vertex table entries of a served run (0: library default; <0: dense)")
     ap.add_argument("--batch", action="store_true", help="many small graphs as one CUDA graph")
     ap.add_argument("--batch-graphs", type=int, default=128)
