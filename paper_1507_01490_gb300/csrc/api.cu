@@ -430,8 +430,9 @@ bcm_status resolve(bcm_graph* g, const bcm_options* opt, Cfg* c) {
     c->sparse = !(o.flags & BCM_GRID_ONLY) &&
                 ((o.flags & BCM_SPARSE) || (!(o.flags & BCM_NO_SPARSE) && !g->directed && g->n >= 4096 &&
                                             g->max_deg <= kSparseMaxDeg));
-    // its default block is 256 threads (more sources at once: 2.5 s against
-    // 3.4 s for 512 on a 512^2 damaged grid); it also runs 128
+    // its default block is 256 threads: on damaged grids 512 threads took
+    // 3.4 s against 2.5 s at 512^2, 128 threads 25.7 s against 23.6 s at
+    // 1024^2 (it also runs 128)
     c->threads = o.threads ? (int)o.threads : (c->sparse ? 256 : 512);
     if (c->sparse) {
         if (c->threads != 128 && c->threads != 256 && c->threads != 512 && c->threads != 1024)
