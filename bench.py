@@ -49,6 +49,8 @@ WORKLOADS = {
     "grid2048": "2048x2048 grid, 5% of edges deleted (seed 4), largest component",
     "grid1024": "1024x1024 grid, 5% of edges deleted (seed 4), largest component (profiling-size case of the "
                 "same recipe)",
+    "grid512": "512x512 grid, 5% of edges deleted (seed 4), largest component (smaller case of the same "
+               "recipe)",
     "grid256": "256x256 grid, 5% of edges deleted (seed 4), largest component (profiling-size case of the "
                "same recipe)",
     "ba2000": "Barabasi-Albert n=2000, m=3, seed 1",

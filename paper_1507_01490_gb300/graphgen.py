@@ -293,8 +293,10 @@ def workload(name: str) -> Graph:
         return rmat(18, 16, seed=3)
     if name == "grid2048":
         return grid_lcc(2048, 2048, 0.05, seed=4)
-    if name == "grid1024":         # the same recipe at 1024 x 1024 and 256 x 256 (profiling-size cases)
+    if name == "grid1024":         # the same recipe at 1024 x 1024, 512 x 512 and 256 x 256 (smaller cases)
         return grid_lcc(1024, 1024, 0.05, seed=4)
+    if name == "grid512":
+        return grid_lcc(512, 512, 0.05, seed=4)
     if name == "grid256":
         return grid_lcc(256, 256, 0.05, seed=4)
     raise KeyError(name)

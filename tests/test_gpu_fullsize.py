@@ -2,9 +2,10 @@
 defaults).
 
 Complete check: tests/golden/fullsize_<workload>_k<k>.json hold the exact
-top-k of chunglu1m and rmat20 (k = 1, 10, 100) as the oracle's sequential
-Algorithm 1 computed it (tests/golden/make_fullsize.py, which calls only the
-oracle); the GPU's ids, farness and reach must equal them element by element.
+top-k of chunglu1m and rmat20 (k = 1, 10, 100) and of the damaged-grid recipe
+at 512 x 512 (k = 10) as the oracle's sequential Algorithm 1 computed it
+(tests/golden/make_fullsize.py, which calls only the oracle); the GPU's ids,
+farness and reach must equal them element by element.
 
 The oracle cannot run every BFS of a million-vertex graph inside a test, so
 the remaining checks are on sampled outputs it computes one by one:
@@ -141,18 +142,19 @@ def test_rmat20_topk(B, gen, orc, rmat, k):
 
 
 def test_grid512_topk10(B, gen, orc):
-    """The damaged-grid recipe at 512 x 512: BCM scans about 56% of m*n on such
-    grids (the bound only bites late on a lattice), so the work grows with
-    n^2; the graph's largest degree is 4, so it runs on the one-source kernel
-    by default (and, checked too, on bit-lane waves).  The 2048 x 2048 case is
-    the opt-in test below."""
-    g = gen.grid_lcc(512, 512, 0.05, seed=4)
+    """The damaged-grid recipe at 512 x 512, against the oracle's complete
+    answer (golden): BCM scans about 57% of m*n on such grids (the bound only
+    bites late on a lattice), so the work grows with n^2; the graph's largest
+    degree is 4, so it runs on the one-source kernel by default, and is also
+    checked on bit-lane waves.  The 2048 x 2048 case is the opt-in test below."""
+    g = gen.workload("grid512")
+    gold = _golden("grid512", 10)
     with B.BcmGraph.from_graph(g) as h:
         ids, far, reach, st = h.topk(10)
         assert st["sparse"] == g.n and st["grid_waves"] == 0
         lanes = h.topk(10, flags=B.BCM_NO_SPARSE)
-    assert (reach == g.n).all()
-    assert all(np.array_equal(a, b) for a, b in zip((ids, far, reach), lanes[:3]))
+    _check_golden(gold, g, ids, far, reach)
+    _check_golden(gold, g, *lanes[:3])
     _check_topk(orc, gen, g, ids, far, reach, n_top=64, n_rand=192)
 
 
