@@ -101,7 +101,8 @@ typedef enum {
  * runs skip the grid kernel).  A per-CTA wave that turns out wide after all
  * is stopped and its sources run again on the grid kernel after the
  * per-CTA phase (see defer_words).  Exhaustive runs stay on the grid
- * kernel.  Levels of grid waves run by push (each frontier vertex
+ * kernel (with BCM_SPARSE, on the one-source kernel).  Levels of grid waves
+ * run by push (each frontier vertex
  * sets its lanes' bits in its out-neighbours) or, when the frontier's arcs
  * are a large share of the graph's, by pull (each vertex with lanes still
  * to reach gathers them from its in-neighbours' frontier bits, with no
@@ -112,7 +113,9 @@ typedef struct {
     uint32_t flags;           /* BCM_* flags above */
     uint32_t blocks;          /* CTAs of the per-CTA kernel; 0 = all that fit on the GPU, at most
                                  one per wave of sources (ceil(n / lanes)).  Each holds a slot of
-                                 44 E lanes/64 bytes, E its table's entries (cta_table) */
+                                 44 E lanes/64 bytes, E its table's entries (cta_table); with the
+                                 one-source kernel (BCM_SPARSE) 8 ceil(n/32) + 16 Q bytes, Q =
+                                 min(n, 2^18) where an overflowing source can be deferred, else n */
     uint32_t threads;         /* threads per CTA of the per-CTA kernel: 256, 512 or 1024; 0 = 512
                                  (the one-source kernel, BCM_SPARSE: also 128; 0 = 256) */
     uint32_t heavy_words;     /* see above; 0 = default (4 per warp of the grid) */
