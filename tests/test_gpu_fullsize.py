@@ -3,7 +3,7 @@ defaults).
 
 Complete check: tests/golden/fullsize_<workload>_k<k>.json hold the exact
 top-k of chunglu1m and rmat20 (k = 1, 10, 100) and of the damaged-grid recipe
-at 512 x 512 (k = 10) as the oracle's sequential Algorithm 1 computed it
+at 512 x 512 and 1024 x 1024 (k = 10) as the oracle's sequential Algorithm 1 computed it
 (tests/golden/make_fullsize.py, which calls only the oracle); the GPU's ids,
 farness and reach must equal them element by element.
 
@@ -156,6 +156,18 @@ def test_grid512_topk10(B, gen, orc):
     _check_golden(gold, g, ids, far, reach)
     _check_golden(gold, g, *lanes[:3])
     _check_topk(orc, gen, g, ids, far, reach, n_top=64, n_rand=192)
+
+
+def test_grid1024_topk10(B, gen):
+    """The damaged-grid recipe at 1024 x 1024 (1,048,568 vertices, BFSs of up to
+    about 1,900 levels) against the oracle's complete answer (a golden: 3.4 hours
+    of the oracle's Algorithm 1 on one core); about 24 s on the GPU."""
+    g = gen.workload("grid1024")
+    gold = _golden("grid1024", 10)
+    with B.BcmGraph.from_graph(g) as h:
+        ids, far, reach, st = h.topk(10)
+    assert st["sparse"] == g.n and st["grid_waves"] == 0
+    _check_golden(gold, g, ids, far, reach)
 
 
 @pytest.mark.skipif(not __import__("os").environ.get("BCM_TEST_GRID2048"),
